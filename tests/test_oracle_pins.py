@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these tests touches the GPU library.  Each pin is chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign or index, a wrong
+norm, a missing rejection, k in place of k') fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import load_kat
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox ----
+def test_philox_known_answers():
+    """Published Philox4x32-10 known-answer vectors (Salmon et al., SC'11)."""
+    rows = load_kat(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = oracle.philox4x32_10(ctr, key)
+        assert [int(v) for v in got] == want
+
+
+def test_draw_index_power_of_two_is_top_bits():
+    """For n = 2^j the multiply-high mapping floor(u n / 2^64) keeps the top j
+    bits of u, and u is built from the first two output words."""
+    for j in (1, 5, 17, 30):
+        for t in range(50):
+            r = oracle.philox4x32_10([t, 7, 0, 0], [123, 0])
+            u = (int(r[1]) << 32) | int(r[0])
+            assert oracle.draw_index(123, 7, t, 1 << j) == u >> (64 - j)
+
+
+def test_draw_index_range_and_uniformity():
+    n = 10
+    counts = np.zeros(n)
+    for t in range(20000):
+        i = oracle.draw_index(5, 3, t, n)
+        assert 0 <= i < n
+        counts[i] += 1
+    chi2 = ((counts - 2000.0) ** 2 / 2000.0).sum()
+    assert chi2 < 40.0  # 9 dof; p ~ 1e-5
+    big = (1 << 31) - 1
+    assert all(0 <= oracle.draw_index(9, 1, t, big) < big for t in range(200))
+    assert all(oracle.draw_index(9, 1, t, 1) == 0 for t in range(20))
+
+
+def test_streams_are_distinct():
+    a = [oracle.draw_index(1, 0, t, 1 << 30) for t in range(64)]
+    b = [oracle.draw_index(1, 1, t, 1 << 30) for t in range(64)]
+    c = [oracle.draw_index(2, 0, t, 1 << 30) for t in range(64)]
+    d = [oracle.draw_index(1, 0, t, 1 << 30, stream=1) for t in range(64)]
+    assert len({tuple(a), tuple(b), tuple(c), tuple(d)}) == 4
+
+
+# ---------------------------------------------------------------- kernels ---
+def test_kernel_values_345_triangle():
+    """x - y = (3, 4): Euclidean distance 5, L1 distance 7."""
+    y = np.array([0.5, -1.0, 2.0], np.float32)
+    x = y + np.array([3.0, 4.0, 0.0], np.float32)
+    h = 2.0
+    assert math.isclose(oracle.kernel_value("gaussian", x, y, h), math.exp(-25 / 8), rel_tol=1e-12)
+    assert math.isclose(oracle.kernel_value("exponential", x, y, h), math.exp(-2.5), rel_tol=1e-12)
+    assert math.isclose(oracle.kernel_value("laplacian", x, y, h), math.exp(-3.5), rel_tol=1e-12)
+
+
+def _powerlaw_dataset(n, d, alpha, beta, seed=0):
+    """Points whose squared distances to y are alpha ((i+1)/n)^beta along random
+    directions (Lemma NN-contribution, Section 3.3)."""
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal(d)
+    dirs = rng.standard_normal((n, d))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    r = np.sqrt(alpha * ((np.arange(n) + 1.0) / n) ** beta)
+    X = y + r[:, None] * dirs
+    return X, y
+
+
+def test_exact_powerlaw_closed_form():
+    """With h^2 = (alpha/2) n^-beta the i-th nearest point contributes
+    exp(-(i+1)^beta) (proof of Lemma NN-contribution)."""
+    n, d, alpha, beta = 400, 6, 3.0, 0.5
+    X, y = _powerlaw_dataset(n, d, alpha, beta)
+    # keep everything in float64 -> float32 consistently: use the float32 points
+    X32, y32 = X.astype(np.float32), y.astype(np.float32)
+    h = math.sqrt(alpha / 2 * n ** (-beta))
+    got = oracle.exact(X32, y32[None], "gaussian", h)[0]
+    # distances of the float32 points, computed independently
+    d2 = ((X32.astype(np.float64) - y32.astype(np.float64)) ** 2).sum(1)
+    want_rounded = np.exp(-d2 / (2 * h * h)).mean()
+    want_closed = np.mean(np.exp(-((np.arange(n) + 1.0) ** beta)))
+    assert math.isclose(got, want_rounded, rel_tol=1e-12)
+    assert math.isclose(got, want_closed, rel_tol=1e-5)
+
+
+def test_exact_limits():
+    """h -> infinity: every summand -> 1; h -> 0: only points at distance 0."""
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((300, 5)).astype(np.float32)
+    Y = np.concatenate([X[:3], rng.standard_normal((2, 5)).astype(np.float32)])
+    for kern in ("gaussian", "exponential", "laplacian"):
+        big = oracle.exact(X, Y, kern, 1e9)
+        assert np.all(np.abs(big - 1.0) < 1e-7)
+        small = oracle.exact(X, Y, kern, 1e-4)
+        assert np.allclose(small[:3], 1.0 / 300, rtol=1e-12)
+        assert np.all(small[3:] < 1e-300)
+
+
+@pytest.mark.parametrize("kern,metric", [("gaussian", "euclidean"),
+                                         ("exponential", "euclidean"),
+                                         ("exponential", "manhattan")])
+def test_exact_matches_sklearn_kde_ratios(kern, metric):
+    """scikit-learn's KernelDensity (exact tree evaluation, zero tolerances)
+    agrees up to its normalising constant: compare ratios between queries."""
+    sk = pytest.importorskip("sklearn.neighbors")
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((500, 4)).astype(np.float32)
+    Y = rng.standard_normal((6, 4)).astype(np.float32)
+    h = 0.8
+    ours_kern = "laplacian" if metric == "manhattan" else kern
+    ours = oracle.exact(X, Y, ours_kern, h)
+    kde = sk.KernelDensity(kernel=kern, bandwidth=h, metric=metric, algorithm="kd_tree",
+                           atol=0.0, rtol=0.0).fit(X.astype(np.float64))
+    ls = kde.score_samples(Y.astype(np.float64))
+    assert np.allclose(np.log(ours) - np.log(ours[0]), ls - ls[0], atol=1e-9)
+
+
+def test_exact_values_in_unit_interval():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((200, 7)).astype(np.float32)
+    Y = rng.standard_normal((20, 7)).astype(np.float32) * 2
+    for kern in ("gaussian", "exponential", "laplacian"):
+        v = oracle.exact(X, Y, kern, 1.3)
+        assert np.all((v >= 0) & (v <= 1))
+
+
+# -------------------------------------------------------------- neighbours --
+def _cdist2(A, B):
+    from scipy.spatial.distance import cdist
+    return cdist(A.astype(np.float64), B.astype(np.float64), "sqeuclidean")
+
+
+def test_knn_matches_library_sort():
+    rng = np.random.default_rng(4)
+    X = rng.integers(-3, 4, size=(400, 3)).astype(np.float32)   # many exact ties
+    Y = rng.integers(-3, 4, size=(25, 3)).astype(np.float32)
+    k = 37
+    nbr, d2 = oracle.knn(X, Y, k)
+    D = _cdist2(Y, X)
+    for q in range(Y.shape[0]):
+        order = np.lexsort((np.arange(X.shape[0]), D[q]))[:k]
+        assert np.array_equal(nbr[q], order)
+        assert np.allclose(d2[q], D[q, order], rtol=0, atol=1e-9)
+
+
+def test_knn_pads_when_k_exceeds_n():
+    X = np.eye(3, dtype=np.float32)
+    nbr, d2 = oracle.knn(X, X[:1], 5)
+    assert list(nbr[0, 3:]) == [-1, -1] and np.all(np.isinf(d2[0, 3:]))
+
+
+def test_nearest_centroid_matches_library_argmin():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((500, 6)).astype(np.float32)
+    C = rng.standard_normal((17, 6)).astype(np.float32)
+    a, _ = oracle.nearest_centroid(X, C)
+    assert np.array_equal(a, np.argmin(_cdist2(X, C), axis=1))
+
+
+def test_ivf_full_probe_equals_brute_force():
+    """nprobe = nlist scans every list: the IVF search is the exact kNN."""
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((600, 5)).astype(np.float32)
+    C = rng.standard_normal((12, 5)).astype(np.float32)
+    assign, _ = oracle.nearest_centroid(X, C)
+    Y = rng.standard_normal((30, 5)).astype(np.float32)
+    _, nbr, d2 = oracle.ivf_search(X, C, assign, Y, 12, 20)
+    nb, db = oracle.knn(X, Y, 20)
+    assert np.array_equal(nbr, nb) and np.allclose(d2, db)
+
+
+def test_ivf_partial_probe_brute_force():
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((300, 4)).astype(np.float32)
+    C = rng.standard_normal((10, 4)).astype(np.float32)
+    assign = rng.integers(0, 10, size=300).astype(np.int32)   # any list layout
+    Y = rng.standard_normal((15, 4)).astype(np.float32)
+    P, k = 3, 25
+    probes, nbr, d2 = oracle.ivf_search(X, C, assign, Y, P, k)
+    DC, DX = _cdist2(Y, C), _cdist2(Y, X)
+    for q in range(15):
+        pq = np.lexsort((np.arange(10), DC[q]))[:P]
+        assert np.array_equal(probes[q], pq)
+        cand = np.flatnonzero(np.isin(assign, pq))
+        order = cand[np.lexsort((cand, DX[q, cand]))]
+        want = np.full(k, -1)
+        want[: min(k, order.size)] = order[:k]
+        assert np.array_equal(nbr[q], want)
+
+
+# --------------------------------------------------------------- DEANN -------
+def _small_problem(seed=8, n=150, d=3, nq=4):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = (0.5 * rng.standard_normal((nq, d))).astype(np.float32)
+    return X, Y
+
+
+def test_deann_full_neighbour_set_is_exact():
+    """k' = n: X_2 is empty and Algorithm 1 returns KDE_X(y) (Lemma
+    composition with B empty); duplicates and -1 padding do not count."""
+    X, Y = _small_problem()
+    n = X.shape[0]
+    rng = np.random.default_rng(0)
+    nbr = np.stack([np.concatenate([rng.permutation(n), [-1, 3, 3, -1]]) for _ in Y])
+    for kern in ("gaussian", "exponential", "laplacian"):
+        got = oracle.deann(X, Y, kern, 0.9, nbr, m=50, seed=1)
+        assert np.allclose(got, oracle.exact(X, Y, kern, 0.9), rtol=1e-13, atol=0)
+
+
+def test_deann_k0_is_rs():
+    """k = 0: Algorithm 1 falls back to random sampling (Section 3.2)."""
+    X, Y = _small_problem()
+    a, sa = oracle.deann(X, Y, "gaussian", 0.7, None, m=64, seed=11, return_samples=True)
+    b, sb = oracle.rs(X, Y, "gaussian", 0.7, m=64, seed=11, return_samples=True)
+    assert np.array_equal(sa, sb) and np.allclose(a, b, rtol=1e-14)
+
+
+def test_deann_m0_discards_far_points():
+    """m = 0: only the neighbours' exact contribution, divided by n."""
+    X, Y = _small_problem()
+    n = X.shape[0]
+    nbr, _ = oracle.knn(X, Y, 10)
+    got = oracle.deann(X, Y, "exponential", 0.6, nbr, m=0, seed=3)
+    for q in range(Y.shape[0]):
+        sub = oracle.exact(X[nbr[q]], Y[q:q + 1], "exponential", 0.6)[0]
+        assert math.isclose(got[q], sub * 10 / n, rel_tol=1e-13)
+
+
+def test_deann_samples_avoid_neighbours_and_are_in_range():
+    X, Y = _small_problem(n=60)
+    nbr, _ = oracle.knn(X, Y, 20)
+    _, S = oracle.deann(X, Y, "gaussian", 1.0, nbr, m=200, seed=5, return_samples=True)
+    for q in range(Y.shape[0]):
+        assert S[q].min() >= 0 and S[q].max() < 60
+        assert not np.isin(S[q], nbr[q]).any()
+        # accepted draws are the stream's draws with X_1 members removed, in order
+        draws = [oracle.draw_index(5, q, t, 60) for t in range(2000)]
+        kept = [i for i in draws if i not in set(nbr[q].tolist())][:200]
+        assert np.array_equal(S[q], kept)
+
+
+def test_deann_values_in_unit_interval():
+    X, Y = _small_problem(n=120, d=4, nq=30)
+    nbr, _ = oracle.knn(X, Y, 15)
+    for kern in ("gaussian", "exponential", "laplacian"):
+        v = oracle.deann(X, Y, kern, 0.5, nbr, m=40, seed=2)
+        assert np.all((v >= 0) & (v <= 1))
+
+
+def _unbiased_check(X, y, kern, h, nbr_row, m, mode=0, reps=10_000):
+    Yrep = np.repeat(y[None], reps, axis=0)
+    nbr = np.repeat(np.asarray(nbr_row, np.int32)[None], reps, axis=0)
+    est = oracle.deann(X, Yrep, kern, h, nbr, m=m, seed=77, mode=mode)
+    mu = oracle.exact(X, y[None], kern, h)[0]
+    se = est.std(ddof=1) / math.sqrt(reps)
+    return abs(est.mean() - mu), se, mu
+
+
+@pytest.mark.parametrize("which", ["good", "random", "adversarial", "duplicates"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_deann_unbiased_for_any_neighbour_set(which, mode):
+    """Corollary "unbiased": the mean over 10^4 independent streams is within
+    5 standard errors of the exact KDE, however poor the neighbour set."""
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((200, 3)).astype(np.float32)
+    y = np.zeros(3, np.float32)
+    d2 = ((X.astype(np.float64) - y) ** 2).sum(1)
+    k = 50
+    if which == "good":
+        row = np.argsort(d2)[:k]
+    elif which == "random":
+        row = rng.choice(200, k, replace=False)
+    elif which == "adversarial":
+        row = np.argsort(-d2)[:k]
+    else:
+        base = np.argsort(d2)[:30]
+        row = np.concatenate([base, base[:15], [-1] * 5])
+    err, se, mu = _unbiased_check(X, y, "gaussian", 0.8, row, m=8, mode=mode)
+    assert err < 5 * se + 1e-15, (err, se, mu)
+
+
+def test_missing_rejection_would_be_biased():
+    """Sanity of the unbiasedness test: a sampler that ignores X_1 (k' not
+    subtracted, draws from all of X) is detected as biased."""
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((200, 3)).astype(np.float32)
+    y = np.zeros(3, np.float32)
+    d2 = ((X.astype(np.float64) - y) ** 2).sum(1)
+    row = np.argsort(d2)[:50]
+    reps = 10_000
+    Yrep = np.repeat(y[None], reps, axis=0)
+    nbr = np.repeat(row[None].astype(np.int32), reps, axis=0)
+    s1 = oracle.exact(X[row], y[None], "gaussian", 0.8)[0] * 50
+    rs = oracle.rs(X, Yrep, "gaussian", 0.8, m=8, seed=77)
+    wrong = (s1 + 150 * rs) / 200          # RS over all of X, scaled as if over X_2
+    mu = oracle.exact(X, y[None], "gaussian", 0.8)[0]
+    se = wrong.std(ddof=1) / math.sqrt(reps)
+    assert abs(wrong.mean() - mu) > 5 * se
+    good = oracle.deann(X, Yrep, "gaussian", 0.8, nbr, m=8, seed=77)
+    assert abs(good.mean() - mu) < 5 * good.std(ddof=1) / math.sqrt(reps)
+
+
+def test_deann_draw_cap():
+    """k' = n - 1 of n = 1000 with m = 10 needs ~10^4 draws, above the cap
+    64 m + 4096: the oracle reports the cap instead of looping."""
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((1000, 2)).astype(np.float32)
+    nbr = np.arange(999, dtype=np.int32)[None]
+    with pytest.raises(oracle.OracleError, match="cap"):
+        oracle.deann(X, X[:1], "gaussian", 1.0, nbr, m=10, seed=0)
+
+
+def test_deann_rejects_out_of_range_neighbour():
+    X, Y = _small_problem()
+    with pytest.raises(oracle.OracleError):
+        oracle.deann(X, Y[:1], "gaussian", 1.0, np.array([[0, 150]]), m=4, seed=0)
+
+
+def test_rs_chernoff_bound_on_worst_case_input():
+    """Lemma RS proof: Pr[Z > (1+eps) mu] <= exp(-eps^2 m tau / 3).  Worst-case
+    input (the tightness example after the proof): a tau fraction of X sits on
+    y (kernel value 1), the rest far away (kernel value ~0)."""
+    n, tau, m, eps = 1000, 0.05, 400, 0.5
+    X = np.full((n, 2), 1e3, np.float32)
+    X[: int(tau * n)] = 0.0
+    reps = 4000
+    Y = np.zeros((reps, 2), np.float32)
+    est = oracle.rs(X, Y, "gaussian", 1.0, m=m, seed=21)
+    mu = tau
+    assert abs(est.mean() - mu) < 5 * est.std(ddof=1) / math.sqrt(reps)
+    fail_hi = np.mean(est > (1 + eps) * mu)
+    fail_lo = np.mean(est < (1 - eps) * mu)
+    assert fail_hi <= math.exp(-eps * eps * m * tau / 3)
+    assert fail_lo <= math.exp(-eps * eps * m * tau / 2)
+
+
+# ------------------------------------------------------------- gradients ----
+@pytest.mark.parametrize("kern", ["gaussian", "exponential", "laplacian"])
+def test_gradient_matches_central_differences(kern):
+    """Pathwise derivative with X_1 and S held fixed vs FP64 central finite
+    differences of the same estimator (step 1e-3 h)."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((300, 4)).astype(np.float32)
+    Y = (0.3 * rng.standard_normal((3, 4))).astype(np.float32)
+    h = 0.9
+    nbr, _ = oracle.knn(X, Y, 20)
+    out, dY, dl = oracle.deann_grad(X, Y, kern, h, nbr, m=30, seed=4)
+    assert np.allclose(out, oracle.deann(X, Y, kern, h, nbr, m=30, seed=4), rtol=1e-13)
+    # step 1e-3 h; the Laplacian kernel has kinks where x_j = y_j, so it takes a
+    # step small enough not to cross one
+    step = 1e-3 * h if kern != "laplacian" else 1e-7 * h
+    # derivative in y along each axis; the query is float32, so difference the
+    # estimator through a float64 shift of the data instead (translation
+    # invariance: K(x, y + e) = K(x - e, y)).
+    for j in range(4):
+        e = np.zeros(4)
+        e[j] = step
+        fp = _deann64(X, Y, kern, h, nbr, 30, 4, shift=e)
+        fm = _deann64(X, Y, kern, h, nbr, 30, 4, shift=-e)
+        fd = (fp - fm) / (2 * step)
+        assert np.allclose(dY[:, j], fd, rtol=1e-3, atol=1e-6 * np.abs(dY).max())
+    fp = _deann64(X, Y, kern, h * math.exp(1e-3), nbr, 30, 4)
+    fm = _deann64(X, Y, kern, h * math.exp(-1e-3), nbr, 30, 4)
+    assert np.allclose(dl, (fp - fm) / 2e-3, rtol=1e-3)
+
+
+def _deann64(X, Y, kern, h, nbr, m, seed, shift=None):
+    """The estimator in float64 for finite differences: same neighbour set and
+    sample indices (taken from the oracle), values from numpy."""
+    _, S = oracle.deann(X, Y, kern, h, nbr, m=m, seed=seed, return_samples=True)
+    n = X.shape[0]
+    out = np.zeros(Y.shape[0])
+    for q in range(Y.shape[0]):
+        y = Y[q].astype(np.float64) + (0 if shift is None else shift)
+        def K(idx):
+            diff = X[idx].astype(np.float64) - y
+            if kern == "gaussian":
+                return np.exp(-(diff ** 2).sum(1) / (2 * h * h))
+            if kern == "exponential":
+                return np.exp(-np.sqrt((diff ** 2).sum(1)) / h)
+            return np.exp(-np.abs(diff).sum(1) / h)
+        nb = np.unique(nbr[q][nbr[q] >= 0])
+        out[q] = (K(nb).sum() + (n - nb.size) / m * K(S[q]).sum()) / n
+    return out
+
+
+def test_exact_gradient_symmetry_and_fd():
+    """Symmetric dataset {+a, -a}: the density gradient vanishes at 0; and the
+    exact gradient matches central differences elsewhere."""
+    a = np.array([[1.0, 2.0, -0.5]], np.float32)
+    X = np.concatenate([a, -a])
+    g, _ = oracle.exact_grad(X, np.zeros((1, 3), np.float32), "gaussian", 1.1)
+    assert np.allclose(g, 0, atol=1e-15)
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((100, 3)).astype(np.float32)
+    y = np.array([[0.2, -0.1, 0.4]], np.float32)
+    g, dl = oracle.exact_grad(X, y, "gaussian", 0.7)
+    step = 1e-4
+    for j in range(3):
+        e = np.zeros(3, np.float32)
+        e[j] = 1
+        Xp = (X.astype(np.float64) - step * e).astype(np.float64)
+        Xm = (X.astype(np.float64) + step * e).astype(np.float64)
+        f = lambda Z: np.exp(-((Z - y.astype(np.float64)) ** 2).sum(1) / (2 * 0.49)).mean()
+        assert math.isclose(g[0, j], (f(Xp) - f(Xm)) / (2 * step), rel_tol=1e-6)
+
+
+# ----------------------------------------------------------- DEANNP / RSP ---
+def test_deannp_full_window_is_exact():
+    """m = n - k': the window covers X \\ X_1 exactly once, so DEANNP returns
+    the exact KDE for any permutation and starting index."""
+    X, Y = _small_problem(n=90)
+    nbr, _ = oracle.knn(X, Y, 12)
+    perm = np.random.default_rng(1).permutation(90).astype(np.int32)
+    out, _ = oracle.deannp(X, Y, "gaussian", 0.8, perm, nbr, m=90 - 12, ell0=37)
+    assert np.allclose(out, oracle.exact(X, Y, "gaussian", 0.8), rtol=1e-13)
+
+
+def test_rsp_consecutive_windows_cover_dataset():
+    """RSP (Algorithm 2) with m | n: n/m consecutive calls for the same query
+    read disjoint windows covering X, so their mean is the exact KDE, and the
+    running index returns to its start."""
+    X, Y = _small_problem(n=120, nq=1)
+    perm = np.random.default_rng(2).permutation(120).astype(np.int32)
+    Yrep = np.repeat(Y, 6, axis=0)
+    out, ell = oracle.deannp(X, Yrep, "exponential", 0.5, perm, None, m=20, ell0=7)
+    assert ell == 7
+    assert math.isclose(out.mean(), oracle.exact(X, Y, "exponential", 0.5)[0], rel_tol=1e-13)
