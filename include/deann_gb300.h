@@ -1,0 +1,228 @@
+/*
+ * deann_gb300.h -- C-ABI of the GB300 (sm_103a) kernel-density estimation
+ * library implementing DEANN: Karppa, Aumueller, Pagh, "DEANN: Speeding up
+ * Kernel-Density Estimation using Approximate Nearest Neighbor Search"
+ * (arXiv 2107.02736).
+ *
+ * Problem statement (Section 2, Definition "Kernel Density Estimate"): for a
+ * dataset X = {x_0, ..., x_{n-1}} in R^d, a kernel K_h with values in [0, 1]
+ * and a query y, KDE_X(y) = (1/n) sum_i K_h(x_i, y).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are row-major FP32 with rows of d contiguous floats (no padding).
+ *  - Pointer spaces: the array arguments of one call are either all host
+ *    pointers or all device pointers of the index's GPU; the space of Y (X for
+ *    kde_build) decides, and outputs are written in that same space.
+ *    Host-pointer calls copy in, compute, copy out and synchronise the stream
+ *    before returning.  Device-pointer calls only enqueue work on the stream
+ *    and return KDE_OK once it is enqueued; an error a kernel detects while
+ *    running (the draw cap, an out-of-range neighbour id) writes NaN into the
+ *    affected outputs and is reported by the next kde_sync().
+ *  - Ownership: the caller keeps every array it passes.  kde_build copies X;
+ *    the index owns all device memory it allocates until kde_free.  Scratch
+ *    memory is owned by the index and reused by its calls, so calls on one
+ *    index must be ordered on one stream (or synchronised by the caller).
+ *  - Streams: kde_opts.stream is a cudaStream_t (NULL: the legacy default
+ *    stream).  A NULL kde_opts pointer means all-default options.
+ *  - Errors: every entry point returns a kde_status; no call aborts or throws.
+ *    kde_last_error() gives a message for the calling thread's last failure.
+ *  - Random numbers: the sample S of a query is drawn from Philox4x32-10
+ *    (Salmon et al., SC'11) with key (lo32(seed), hi32(seed)) and counter
+ *    (t, lo32(qid), hi32(qid), 0), where qid = opts.query_id_offset + row and
+ *    t = 0, 1, 2, ... is the draw number; index = floor(u n / 2^64) with
+ *    u = (r1 << 32) | r0.  The same (X, Y, neighbours, seed, qid) always gives
+ *    the same sample.
+ */
+#ifndef DEANN_GB300_H
+#define DEANN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kde_index kde_index;
+
+/* Kernels (Section 1): Gaussian exp(-|x-y|_2^2 / (2h^2)), exponential
+ * exp(-|x-y|_2 / h), Laplacian exp(-|x-y|_1 / h).  No normalising constant. */
+typedef enum {
+  KDE_GAUSSIAN = 0,
+  KDE_EXPONENTIAL = 1,
+  KDE_LAPLACIAN = 2
+} kde_kernel;
+
+typedef enum {
+  KDE_OK = 0,
+  KDE_EINVAL = 1, /* invalid argument (message in kde_last_error) */
+  KDE_ENOMEM = 2, /* device allocation failed */
+  KDE_ECUDA = 3,  /* a CUDA runtime call failed */
+  KDE_ELIMIT = 4, /* a query needed more than 64 m + 4096 draws */
+  KDE_ESTATE = 5  /* wrong device, or an earlier asynchronous error pending */
+} kde_status;
+
+/* Precision of the IVF scan's distance tiles.  Selected neighbours are always
+ * rescored with FP32 difference-form distances, so the returned neighbour
+ * distances and estimates are FP32 whatever the scan used. */
+typedef enum {
+  KDE_PREC_FP32 = 0, /* FP32 operands */
+  KDE_PREC_BF16 = 1  /* BF16 operands, FP32 accumulation, FP32 rescoring */
+} kde_precision;
+
+typedef struct {
+  int32_t precision;        /* kde_precision of the scan (kde_query, kde_search) */
+  int32_t sample_mode;      /* 0: reject draws in X_1 (default); 1: "drop" */
+  int32_t kmeans_iters;     /* kde_build: Lloyd iterations (0 = 20) */
+  int32_t reserved;         /* must be 0 */
+  uint64_t query_id_offset; /* qid of row r is query_id_offset + r */
+  void* stream;             /* cudaStream_t, NULL = legacy default stream */
+} kde_opts;
+
+/* kde_build -- build an index over X (Section 4: FAISS-style inverted file).
+ *   X       n x d, host or device.  Copied; the caller keeps X.
+ *   n >= 1, 1 <= d <= 4096.
+ *   kernel  kde_kernel; h > 0 and finite is the bandwidth.
+ *   nlist   number of IVF lists, 1 <= nlist <= min(n, 8192).  nlist = 1 makes
+ *           every query scan all n points (brute-force kNN as the ANN).
+ *           Otherwise k-means with nlist centroids (initial centroids: distinct
+ *           points drawn from Philox stream 1 of `seed`; opts.kmeans_iters
+ *           Lloyd iterations; empty lists reseeded with the point farthest from
+ *           its centroid), then every point goes to the list of its nearest
+ *           centroid, lists stored contiguously.
+ *   out     receives the new index (NULL on failure).
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, float h,
+                     int32_t nlist, uint64_t seed, const kde_opts* opts, kde_index** out);
+
+/* kde_free -- release the index and all device memory it owns (NULL is a
+ * no-op).  Synchronises the device first. */
+void kde_free(kde_index* index);
+
+/* kde_set_bandwidth -- replace h (> 0, finite).  The IVF does not depend on h. */
+kde_status kde_set_bandwidth(kde_index* index, float h);
+
+/* kde_index_info -- any output pointer may be NULL. */
+kde_status kde_index_info(const kde_index* index, int64_t* n, int32_t* d, int32_t* nlist,
+                          int32_t* kernel, float* h, int64_t* max_list);
+
+/* kde_export_ivf -- copy the IVF state to HOST memory so that the search can
+ * be re-run elsewhere: centroids (nlist x d FP32), assign (n int32: the list
+ * of each point, in the original point order).  Either may be NULL. */
+kde_status kde_export_ivf(kde_index* index, float* centroids, int32_t* assign);
+
+/* kde_search -- the ANN subroutine of Algorithm 1, line 2: the k nearest
+ * points (Euclidean) among the lists of the nprobe nearest centroids.
+ *   Y      nq x d queries; nq >= 0.
+ *   k      1 <= k <= 1024; 1 <= nprobe <= min(nlist, 256).
+ *   nbr    nq x k original point ids sorted by (distance, id); -1 pads rows
+ *          with fewer than k candidates.
+ *   d2     nq x k squared distances (FP32, difference form) or NULL; +inf pads.
+ * Candidates are ranked first by approximate distances from the scan (see
+ * opts.precision) and the best k + margin are rescored exactly. */
+kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t nprobe,
+                      int32_t* nbr, float* d2, const kde_opts* opts);
+
+/* kde_query -- DEANN (Algorithm 1): X_1 = kde_search(y, k, nprobe); the
+ * neighbours' contribution is summed exactly; S = m draws uniform on X \ X_1
+ * (with repetition, by rejection of draws in X_1; or opts.sample_mode = 1);
+ * out = (1/n) [ sum_{X_1} K + ((n - k')/m) sum_S K ] with k' = |X_1|.
+ *   k      0 <= k <= min(n, 1024) (k = 0 is plain random sampling);
+ *   m      >= 0 (m = 0 keeps only the neighbours' exact contribution);
+ *   nprobe 1 <= nprobe <= min(nlist, 256) (ignored when k = 0).
+ *   out    nq estimates (FP32).
+ *   nbr    NULL, or nq x k receiving the neighbour ids that were used. */
+kde_status kde_query(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t m,
+                     int32_t nprobe, uint64_t seed, float* out, int32_t* nbr,
+                     const kde_opts* opts);
+
+/* kde_query_with_neighbors -- Algorithm 1 lines 3-7 with a caller-supplied
+ * neighbour set per query (nq x k ids; negative entries are padding,
+ * duplicates count once; an id >= n is an error).  Same estimate as
+ * kde_query. */
+kde_status kde_query_with_neighbors(kde_index* index, const float* Y, int64_t nq,
+                                    const int32_t* nbr, int32_t k, int32_t m, uint64_t seed,
+                                    float* out, const kde_opts* opts);
+
+/* kde_query_rs -- random sampling (Lemma RS): m >= 1 draws uniform on X with
+ * repetition (the first m draws of each query's stream), out = mean kernel
+ * value. */
+kde_status kde_query_rs(kde_index* index, const float* Y, int64_t nq, int32_t m, uint64_t seed,
+                        float* out, const kde_opts* opts);
+
+/* kde_exact -- the exact KDE (Section 2 definition; the "Naive" evaluation of
+ * Appendix D), out[q] = (1/n) sum_i K_h(x_i, y_q), FP32 difference-form
+ * distances, FP64 accumulation across the dataset. */
+kde_status kde_exact(kde_index* index, const float* Y, int64_t nq, float* out,
+                     const kde_opts* opts);
+
+/* kde_sample_indices -- the sample S that kde_query_with_neighbors uses for
+ * each query (nq x m original ids): the accepted draws in draw order
+ * (sample_mode 0) or the raw draws (sample_mode 1).  Rows with no sampling
+ * (k' = n or m = 0) are filled with -1. */
+kde_status kde_sample_indices(kde_index* index, int64_t nq, const int32_t* nbr, int32_t k,
+                              int32_t m, uint64_t seed, int32_t* samples, const kde_opts* opts);
+
+/* kde_grad_with_neighbors -- adjoint of kde_query_with_neighbors with X_1 and
+ * S held fixed (the pathwise derivative; the paper defines no gradient):
+ *   out[q]   the estimate (as kde_query_with_neighbors), or NULL;
+ *   dY[q]    gout[q] * d out[q] / d y_q (nq x d);
+ *   dlogh[q] gout[q] * d out[q] / d log h, or NULL.
+ * gout may be NULL (all ones).  Kernel values are recomputed from the
+ * neighbour ids and the regenerated sample, never stored.  d <= 1024. */
+kde_status kde_grad_with_neighbors(kde_index* index, const float* Y, int64_t nq,
+                                   const int32_t* nbr, int32_t k, int32_t m, uint64_t seed,
+                                   const float* gout, float* out, float* dY, float* dlogh,
+                                   const kde_opts* opts);
+
+/* kde_sync -- wait for the index's work on opts->stream and report (then
+ * clear) errors raised by kernels of earlier device-pointer calls:
+ * KDE_ELIMIT (draw cap), KDE_EINVAL (neighbour id >= n). */
+kde_status kde_sync(kde_index* index, const kde_opts* opts);
+
+/* kde_stats -- counters kept since the index was built: margin_failures =
+ * queries whose rescored top-k could not be certified against the scan's
+ * error bound (the neighbours returned are still valid points, possibly not
+ * the exact top k).  Synchronises opts->stream. */
+kde_status kde_stats(kde_index* index, int64_t* margin_failures, const kde_opts* opts);
+
+/* kde_reserve -- pre-allocate scratch for calls with up to nq queries and the
+ * given k, m, nprobe, so that later calls allocate nothing (required before
+ * capturing calls into a CUDA graph). */
+kde_status kde_reserve(kde_index* index, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
+                       const kde_opts* opts);
+
+/* Per-stage device timing of an index's calls.  Stages: 0 query staging
+ * (padding, norms), 1 coarse quantiser (probe selection), 2 scan work plan,
+ * 3 IVF list scan, 4 candidate selection and rescoring, 5 estimator (sample
+ * draws, gathers, combination), 6 exact KDE, 7 adjoint.  launches counts the
+ * kernels each stage launched (always on); ms / timed are filled from CUDA
+ * events recorded on the call's stream around every stage while profiling is
+ * enabled. */
+#define KDE_NUM_STAGES 8
+typedef struct {
+  double ms[KDE_NUM_STAGES];      /* total device time per stage */
+  int64_t timed[KDE_NUM_STAGES];  /* timed stage executions */
+  int64_t calls[KDE_NUM_STAGES];  /* stage executions */
+  int64_t launches[KDE_NUM_STAGES];
+} kde_profile;
+
+/* kde_profile_enable -- on != 0 starts recording events for later calls. */
+kde_status kde_profile_enable(kde_index* index, int32_t on);
+
+/* kde_profile_read -- synchronises, sums the recorded times into *out and,
+ * when reset != 0, clears the counters and events. */
+kde_status kde_profile_read(kde_index* index, kde_profile* out, int32_t reset,
+                            const kde_opts* opts);
+
+/* kde_strerror -- static description of a status. */
+const char* kde_strerror(kde_status status);
+
+/* kde_last_error -- message of the calling thread's last failed call. */
+const char* kde_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEANN_GB300_H */

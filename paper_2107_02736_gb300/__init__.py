@@ -1,0 +1,364 @@
+"""DEANN kernel-density estimation on GB300 (sm_103a).
+
+Thin Python binding of the C-ABI library ``libdeann_gb300.so``
+(``include/deann_gb300.h``).  This module only marshals arguments: every step
+of the estimator runs in the library's CUDA kernels.  Importing it never
+falls back to a CPU path; when the library is missing it raises.
+
+Paper: Karppa, Aumueller, Pagh, "DEANN: Speeding up Kernel-Density Estimation
+using Approximate Nearest Neighbor Search" (arXiv 2107.02736).
+
+Arrays are torch tensors (float32 / int32, C-contiguous).  CUDA tensors are
+passed as device pointers and the work is enqueued on torch's current stream;
+CPU tensors go through the library's host-pointer path (copy in, compute,
+copy out, synchronise).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build_mod
+
+__all__ = ["KDEIndex", "DeannKDE", "KDEError", "library_path", "load_library",
+           "GAUSSIAN", "EXPONENTIAL", "LAPLACIAN"]
+
+GAUSSIAN, EXPONENTIAL, LAPLACIAN = 0, 1, 2
+_KERNELS = {"gaussian": GAUSSIAN, "exponential": EXPONENTIAL, "laplacian": LAPLACIAN}
+_STATUS = {0: "KDE_OK", 1: "KDE_EINVAL", 2: "KDE_ENOMEM", 3: "KDE_ECUDA", 4: "KDE_ELIMIT",
+           5: "KDE_ESTATE"}
+
+_lib = None
+
+
+class KDEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
+                ("kmeans_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("query_id_offset", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+STAGES = ["stage", "coarse", "plan", "scan", "select", "estimate", "exact", "grad"]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("timed", ctypes.c_int64 * 8),
+                ("calls", ctypes.c_int64 * 8), ("launches", ctypes.c_int64 * 8)]
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+def load_library():
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"DEANN CUDA library not found at {path}; build it with "
+            "`python -m paper_2107_02736_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, i64, i32, u64, f32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                             ctypes.c_uint64, ctypes.c_float)
+    O = ctypes.POINTER(_Opts)
+    sig = {
+        "kde_build": [P, i64, i32, i32, f32, i32, u64, O, ctypes.POINTER(ctypes.c_void_p)],
+        "kde_set_bandwidth": [P, f32],
+        "kde_index_info": [P, P, P, P, P, P, P],
+        "kde_export_ivf": [P, P, P],
+        "kde_search": [P, P, i64, i32, i32, P, P, O],
+        "kde_query": [P, P, i64, i32, i32, i32, u64, P, P, O],
+        "kde_query_with_neighbors": [P, P, i64, P, i32, i32, u64, P, O],
+        "kde_query_rs": [P, P, i64, i32, u64, P, O],
+        "kde_exact": [P, P, i64, P, O],
+        "kde_sample_indices": [P, i64, P, i32, i32, u64, P, O],
+        "kde_grad_with_neighbors": [P, P, i64, P, i32, i32, u64, P, P, P, P, O],
+        "kde_sync": [P, O],
+        "kde_stats": [P, P, O],
+        "kde_reserve": [P, i64, i32, i32, i32, O],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.kde_profile_enable.argtypes = [P, i32]
+    lib.kde_profile_enable.restype = ctypes.c_int
+    lib.kde_profile_read.argtypes = [P, ctypes.POINTER(_Profile), i32, O]
+    lib.kde_profile_read.restype = ctypes.c_int
+    lib.kde_free.argtypes = [P]
+    lib.kde_free.restype = None
+    lib.kde_strerror.argtypes = [ctypes.c_int]
+    lib.kde_strerror.restype = ctypes.c_char_p
+    lib.kde_last_error.argtypes = []
+    lib.kde_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = _lib.kde_last_error().decode(errors="replace")
+        raise KDEError(status, msg)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, device=None):
+    t = torch.as_tensor(t, dtype=torch.float32, device=device)
+    return t.contiguous()
+
+
+def _i32(t, device=None):
+    t = torch.as_tensor(t, dtype=torch.int32, device=device)
+    return t.contiguous()
+
+
+class KDEIndex:
+    """An index over a dataset X (n x d) for one kernel and bandwidth.
+
+    ``nlist = 1`` makes every query scan all points (brute-force kNN as the
+    ANN); ``nlist > 1`` builds an IVF-flat index with GPU k-means.
+    """
+
+    def __init__(self, X, kernel="gaussian", h=1.0, nlist=1, seed=0, kmeans_iters=20,
+                 device=None):
+        lib = load_library()
+        X = _f32(X, device=device)
+        if X.dim() != 2:
+            raise ValueError("X must be n x d")
+        self._device = X.device if X.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        kern = _KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        opts = self._opts(kmeans_iters=kmeans_iters)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self._device):
+            _check(lib.kde_build(_ptr(X), X.shape[0], X.shape[1], kern, float(h), int(nlist),
+                                 int(seed) & (2**64 - 1), ctypes.byref(opts),
+                                 ctypes.byref(handle)))
+        self._h = handle
+        self.n, self.d = X.shape
+        self.kernel = kern
+        self.nlist = int(nlist)
+
+    # -- plumbing ----------------------------------------------------------
+    def _opts(self, precision=0, sample_mode=0, qid_offset=0, kmeans_iters=0, host=False):
+        o = _Opts()
+        o.precision = int(precision)
+        o.sample_mode = int(sample_mode)
+        o.kmeans_iters = int(kmeans_iters)
+        o.reserved = 0
+        o.query_id_offset = int(qid_offset)
+        o.stream = None if host else torch.cuda.current_stream().cuda_stream
+        return o
+
+    def _prep(self, Y):
+        Y = _f32(Y)
+        if Y.dim() != 2 or Y.shape[1] != self.d:
+            raise ValueError(f"Y must be nq x {self.d}")
+        return Y
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.kde_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device(self):
+        return self._device
+
+    @property
+    def h(self) -> float:
+        h = ctypes.c_float()
+        _check(_lib.kde_index_info(self._h, None, None, None, None, ctypes.byref(h), None))
+        return h.value
+
+    @property
+    def max_list(self) -> int:
+        v = ctypes.c_int64()
+        _check(_lib.kde_index_info(self._h, None, None, None, None, None, ctypes.byref(v)))
+        return v.value
+
+    def set_bandwidth(self, h: float):
+        _check(_lib.kde_set_bandwidth(self._h, float(h)))
+
+    def export_ivf(self):
+        """(centroids nlist x d float32, assign n int32) as CPU tensors."""
+        C = torch.empty((self.nlist, self.d), dtype=torch.float32)
+        a = torch.empty(self.n, dtype=torch.int32)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_export_ivf(self._h, _ptr(C), _ptr(a)))
+        return C, a
+
+    def sync(self):
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_sync(self._h, ctypes.byref(self._opts())))
+
+    def margin_failures(self) -> int:
+        v = ctypes.c_int64()
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_stats(self._h, ctypes.byref(v), ctypes.byref(self._opts())))
+        return v.value
+
+    def profile(self, on: bool = True):
+        _check(_lib.kde_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{stage: {ms, timed, calls, launches}} since the last reset."""
+        p = _Profile()
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_profile_read(self._h, ctypes.byref(p), 1 if reset else 0,
+                                         ctypes.byref(self._opts())))
+        return {name: dict(ms=p.ms[i], timed=p.timed[i], calls=p.calls[i],
+                           launches=p.launches[i]) for i, name in enumerate(STAGES)}
+
+    def reserve(self, nq, k=0, m=0, nprobe=1):
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_reserve(self._h, int(nq), int(k), int(m), int(nprobe),
+                                    ctypes.byref(self._opts())))
+
+    # -- the path ------------------------------------------------------------
+    def search(self, Y, k, nprobe=1, precision=0):
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        nbr = torch.empty((nq, k), dtype=torch.int32, device=Y.device)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_search(self._h, _ptr(Y), nq, int(k), int(nprobe), _ptr(nbr),
+                                   _ptr(d2), ctypes.byref(self._opts(precision,
+                                                                     host=not Y.is_cuda))))
+        return nbr, d2
+
+    def query(self, Y, k, m, nprobe=1, seed=0, precision=0, sample_mode=0, qid_offset=0,
+              return_neighbors=False):
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        nbr = (torch.empty((nq, k), dtype=torch.int32, device=Y.device)
+               if return_neighbors and k > 0 else None)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_query(self._h, _ptr(Y), nq, int(k), int(m), int(nprobe),
+                                  int(seed) & (2**64 - 1), _ptr(out), _ptr(nbr),
+                                  ctypes.byref(self._opts(precision, sample_mode, qid_offset,
+                                                          host=not Y.is_cuda))))
+        return (out, nbr) if return_neighbors else out
+
+    def query_with_neighbors(self, Y, nbr, m, seed=0, sample_mode=0, qid_offset=0):
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        nbr = _i32(nbr, device=Y.device).reshape(nq, -1)
+        k = nbr.shape[1]
+        out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_query_with_neighbors(
+                self._h, _ptr(Y), nq, _ptr(nbr) if k > 0 else None, k, int(m),
+                int(seed) & (2**64 - 1), _ptr(out),
+                ctypes.byref(self._opts(0, sample_mode, qid_offset, host=not Y.is_cuda))))
+        return out
+
+    def query_rs(self, Y, m, seed=0, qid_offset=0):
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_query_rs(self._h, _ptr(Y), nq, int(m), int(seed) & (2**64 - 1),
+                                     _ptr(out), ctypes.byref(self._opts(
+                                         0, 0, qid_offset, host=not Y.is_cuda))))
+        return out
+
+    def exact(self, Y):
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_exact(self._h, _ptr(Y), nq, _ptr(out),
+                                  ctypes.byref(self._opts(host=not Y.is_cuda))))
+        return out
+
+    def sample_indices(self, nbr, m, seed=0, nq=None, sample_mode=0, qid_offset=0,
+                       device=None):
+        if nbr is None:
+            if nq is None:
+                raise ValueError("nq is required without nbr")
+            dev = device if device is not None else self._device
+            k = 0
+            nbr_t = None
+        else:
+            nbr_t = _i32(nbr, device=device)
+            nq = nbr_t.shape[0]
+            nbr_t = nbr_t.reshape(nq, -1)
+            k = nbr_t.shape[1]
+            dev = nbr_t.device
+        S = torch.empty((nq, m), dtype=torch.int32, device=dev)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_sample_indices(
+                self._h, int(nq), _ptr(nbr_t) if k > 0 else None, k, int(m),
+                int(seed) & (2**64 - 1), _ptr(S),
+                ctypes.byref(self._opts(0, sample_mode, qid_offset,
+                                        host=S.device.type == "cpu"))))
+        return S
+
+    def grad_with_neighbors(self, Y, nbr, m, seed=0, gout=None, sample_mode=0, qid_offset=0):
+        """(out, dY, dlogh_per_query) of the estimate with X_1 and S fixed."""
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        if nbr is None:
+            nbr_t, k = None, 0
+        else:
+            nbr_t = _i32(nbr, device=Y.device).reshape(nq, -1)
+            k = nbr_t.shape[1]
+        g = None if gout is None else _f32(gout, device=Y.device)
+        out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        dY = torch.empty((nq, self.d), dtype=torch.float32, device=Y.device)
+        dl = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_grad_with_neighbors(
+                self._h, _ptr(Y), nq, _ptr(nbr_t) if k > 0 else None, k, int(m),
+                int(seed) & (2**64 - 1), _ptr(g), _ptr(out), _ptr(dY), _ptr(dl),
+                ctypes.byref(self._opts(0, sample_mode, qid_offset, host=not Y.is_cuda))))
+        return out, dY, dl
+
+
+class DeannKDE(torch.autograd.Function):
+    """out = DEANN estimate of KDE(Y) with bandwidth exp(log_h).
+
+    Forward runs the IVF search and the estimator; backward recomputes kernel
+    values from the saved neighbour ids and the regenerated sample (the same
+    Philox stream) and returns d/dY and d/dlog h of the estimate with the
+    neighbour set and the sample held fixed.
+    """
+
+    @staticmethod
+    def forward(ctx, Y, log_h, index: KDEIndex, k: int, m: int, nprobe: int, seed: int,
+                precision: int = 0):
+        index.set_bandwidth(float(torch.exp(log_h.detach()).item()))
+        out, nbr = index.query(Y.detach(), k, m, nprobe=nprobe, seed=seed, precision=precision,
+                               return_neighbors=True)
+        ctx.index, ctx.m, ctx.seed = index, m, seed
+        ctx.save_for_backward(Y.detach(), nbr if nbr is not None else torch.empty(0))
+        ctx.k = k
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        Y, nbr = ctx.saved_tensors
+        nb = nbr if ctx.k > 0 else None
+        _, dY, dl = ctx.index.grad_with_neighbors(Y, nb, ctx.m, seed=ctx.seed,
+                                                  gout=gout.contiguous())
+        return dY, dl.sum().reshape(()), None, None, None, None, None, None

@@ -1,0 +1,994 @@
+// C-ABI entry points (include/deann_gb300.h): argument checks, pointer-space
+// handling, scratch layout and the launch sequence of each call.  All
+// arithmetic runs in the kernels of build.cu, tiles.cu, select.cu and
+// sample.cu; this file only moves bytes and orders launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "deann_gb300.h"
+#include "internal.h"
+
+using namespace deann;
+
+namespace {
+
+thread_local std::string g_err;
+
+kde_status fail(kde_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(KDE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    kde_status s_ = (expr);        \
+    if (s_ != KDE_OK) return s_;   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+enum Space { SPACE_HOST = 0, SPACE_DEVICE = 1, SPACE_FOREIGN = 2 };
+
+Space space_of(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return SPACE_HOST;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+    return a.device == device ? SPACE_DEVICE : SPACE_FOREIGN;
+  return SPACE_HOST;
+}
+
+cudaStream_t stream_of(const kde_opts* o) {
+  return (o != nullptr && o->stream != nullptr) ? reinterpret_cast<cudaStream_t>(o->stream)
+                                                : cudaStream_t(0);
+}
+
+const kde_opts kDefaultOpts = {0, 0, 0, 0, 0, nullptr};
+
+// Bump layout over the index's scratch buffer; with base == nullptr it only
+// counts bytes, so the same carve code sizes and places the buffers.
+struct Bump {
+  char* base = nullptr;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += bytes;
+    return p;
+  }
+};
+
+kde_status ensure_scratch(kde_index* ix, size_t bytes) {
+  if (bytes <= ix->scratch.cap) return KDE_OK;
+  if (bytes > ix->scratch_limit)
+    return fail(KDE_ENOMEM, "call needs %zu bytes of scratch, above the limit %zu", bytes,
+                ix->scratch_limit);
+  CK(cudaDeviceSynchronize());
+  if (ix->scratch.base) cudaFree(ix->scratch.base);
+  ix->scratch.base = nullptr;
+  ix->scratch.cap = 0;
+  const size_t cap = std::max(bytes, size_t(64) << 20);
+  if (cudaMalloc(&ix->scratch.base, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(KDE_ENOMEM, "cudaMalloc of %zu scratch bytes failed", cap);
+  }
+  ix->scratch.cap = cap;
+  return KDE_OK;
+}
+
+template <class T>
+kde_status dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(KDE_ENOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+  }
+  return KDE_OK;
+}
+
+// Reads and clears the device error words; maps them to a status.
+kde_status collect_errors(kde_index* ix, cudaStream_t st, int64_t* margin_out) {
+  uint32_t h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ix->err, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemsetAsync(ix->err, 0, 2 * sizeof(uint32_t), st));
+  if (margin_out) *margin_out = h[1];
+  if (h[0] & KDE_ERRBIT_DRAWCAP)
+    return fail(KDE_ELIMIT, "a query needed more than 64 m + 4096 draws (k' close to n)");
+  if (h[0] & KDE_ERRBIT_BADNBR) return fail(KDE_EINVAL, "a neighbour id was >= n");
+  return KDE_OK;
+}
+
+void ix_margin_accumulate(kde_index* ix, int64_t m) { ix->margin_failures += m; }
+
+// Stages of a call, for kde_profile_read.
+enum { ST_STAGE = 0, ST_COARSE, ST_PLAN, ST_SCAN, ST_SELECT, ST_ESTIMATE, ST_EXACT, ST_GRAD };
+
+// Counts the kernels a stage launches and, when profiling is on, brackets
+// the stage with CUDA events on the call's stream.
+struct StageTimer {
+  kde_index* ix;
+  cudaStream_t st;
+  int stage;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageTimer(kde_index* ix_, int stage_, cudaStream_t st_, int nlaunch)
+      : ix(ix_), st(st_), stage(stage_) {
+    ix->launches[stage] += nlaunch;
+    ix->calls[stage] += 1;
+    if (ix->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, st);
+  }
+  ~StageTimer() {
+    if (a != nullptr && b != nullptr) {
+      cudaEventRecord(b, st);
+      ix->events.push_back({a, b, stage});
+    }
+  }
+};
+
+int select_margin(int k, int precision) { return precision == 0 ? k / 4 + 16 : k + 32; }
+
+float scan_err_scale(int dp, int precision) {
+  const float u = 1.0f / 16777216.0f;  // 2^-24
+  if (precision == 0) return 2.0f * ((float)dp / 32.0f + 40.0f) * u;
+  // BF16 operands: each rounded to 8 significant bits
+  return 2.0f * (1.0f / 128.0f + ((float)dp / 32.0f + 40.0f) * u);
+}
+
+// ---- query scratch ---------------------------------------------------------
+struct SearchBufs {
+  int64_t qc = 0;  // queries per chunk
+  float* D = nullptr;
+  int32_t* probes = nullptr;
+  int64_t *q_count = nullptr, *q_off = nullptr, *seg_off = nullptr;
+  int64_t *list_cnt = nullptr, *bucket_off = nullptr, *bucket_fill = nullptr;
+  int64_t *tile_cnt = nullptr, *tile_off = nullptr;
+  int32_t* pair_q = nullptr;
+  int64_t* pair_dst = nullptr;
+  float* cand = nullptr;
+};
+
+constexpr size_t kCandCap = size_t(2) << 30;
+
+void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
+  const int L = ix->nlist;
+  const size_t per_q = (size_t)P * (size_t)std::max<int64_t>(ix->max_list, 1) * sizeof(float);
+  int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
+  qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
+  s.qc = qc;
+  if (L > 1) s.D = b.take<float>((size_t)qc * L);
+  s.probes = b.take<int32_t>((size_t)qc * P);
+  s.q_count = b.take<int64_t>(qc);
+  s.q_off = b.take<int64_t>(qc + 1);
+  s.seg_off = b.take<int64_t>((size_t)qc * P);
+  s.list_cnt = b.take<int64_t>(L);
+  s.bucket_off = b.take<int64_t>(L + 1);
+  s.bucket_fill = b.take<int64_t>(L);
+  s.tile_cnt = b.take<int64_t>(L);
+  s.tile_off = b.take<int64_t>(L + 1);
+  s.pair_q = b.take<int32_t>((size_t)qc * P);
+  s.pair_dst = b.take<int64_t>((size_t)qc * P);
+  s.cand = b.take<float>((size_t)qc * P * std::max<int64_t>(ix->max_list, 1));
+}
+
+struct CallBufs {
+  float* Yp = nullptr;     // nq x dp padded queries
+  float* Yn = nullptr;     // nq norms
+  float* out = nullptr;    // nq
+  int32_t* nbr = nullptr;  // nq x k
+  float* nd2 = nullptr;    // nq x k
+  float* s1 = nullptr;     // nq
+  int32_t* samples = nullptr;
+  float* gout = nullptr;
+  float* dY = nullptr;
+  float* dlogh = nullptr;
+  double* acc = nullptr;
+  SearchBufs search;
+};
+
+struct CallShape {
+  int64_t nq = 0;
+  int k = 0, m = 0, P = 0;
+  bool search = false;     // runs the IVF search
+  bool host = false;       // host-pointer call (needs device copies of outputs)
+  bool need_nbr = false;   // neighbour ids on the device
+  bool need_nd2 = false;
+  bool need_out = false;
+  bool need_s1 = false;
+  bool need_samples = false;
+  bool grad = false;
+  bool exact = false;
+};
+
+void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
+  const int64_t nq = std::max<int64_t>(c.nq, 1);
+  cb.Yp = b.take<float>((size_t)nq * ix->dp);
+  cb.Yn = b.take<float>(nq);
+  if (c.need_out) cb.out = b.take<float>(nq);
+  if (c.need_nbr) cb.nbr = b.take<int32_t>((size_t)nq * std::max(c.k, 1));
+  if (c.need_nd2) cb.nd2 = b.take<float>((size_t)nq * std::max(c.k, 1));
+  if (c.need_s1) cb.s1 = b.take<float>(nq);
+  if (c.need_samples) cb.samples = b.take<int32_t>((size_t)nq * std::max(c.m, 1));
+  if (c.grad) {
+    cb.gout = b.take<float>(nq);
+    cb.dY = b.take<float>((size_t)nq * ix->d);
+    cb.dlogh = b.take<float>(nq);
+  }
+  if (c.exact) cb.acc = b.take<double>(nq);
+  if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
+}
+
+kde_status prepare_call(kde_index* ix, const CallShape& c, CallBufs& cb) {
+  Bump count;
+  CallBufs dummy;
+  carve_call(count, ix, c, dummy);
+  TRY(ensure_scratch(ix, count.used));
+  Bump real;
+  real.base = ix->scratch.base;
+  carve_call(real, ix, c, cb);
+  return KDE_OK;
+}
+
+// Pads queries (nq x d, host or device) into cb.Yp (nq x dp) and computes norms.
+kde_status stage_queries(kde_index* ix, const float* Y, int64_t nq, bool host, CallBufs& cb,
+                         cudaStream_t st) {
+  if (nq == 0) return KDE_OK;
+  if (ix->dp != ix->d) CK(cudaMemsetAsync(cb.Yp, 0, sizeof(float) * nq * ix->dp, st));
+  CK(cudaMemcpy2DAsync(cb.Yp, sizeof(float) * ix->dp, Y, sizeof(float) * ix->d,
+                       sizeof(float) * ix->d, (size_t)nq,
+                       host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  StageTimer t(ix, ST_STAGE, st, 1);
+  launch_query_norms(cb.Yp, nq, ix->dp, cb.Yn, st);
+  return KDE_OK;
+}
+
+// IVF search on staged queries: neighbours, optional squared distances and s1.
+kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int P, int precision,
+                      int32_t* nbr, float* nd2, float* s1, cudaStream_t st) {
+  const SearchBufs& s = cb.search;
+  const int L = ix->nlist;
+  const int margin = select_margin(k, precision);
+  const int kprime = std::min(kSelectCap, k + margin);
+  for (int64_t q0 = 0; q0 < nq; q0 += s.qc) {
+    const int64_t nc = std::min<int64_t>(s.qc, nq - q0);
+    const float* Yc = cb.Yp + q0 * ix->dp;
+    const float* Ync = cb.Yn + q0;
+    {
+      StageTimer t(ix, ST_COARSE, st, L > 1 ? 2 : 1);
+      if (L > 1) {
+        launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, st);
+        launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
+                             s.probes, st);
+      } else {
+        launch_fill_i32(s.probes, nc * P, 0, st);
+      }
+    }
+    {
+      StageTimer t(ix, ST_PLAN, st, 6);
+      launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_off, s.seg_off,
+                        s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
+                        s.tile_cnt, s.tile_off, kTile, st);
+    }
+    ScanPlan plan;
+    plan.pair_q = s.pair_q;
+    plan.pair_dst = s.pair_dst;
+    plan.bucket_off = s.bucket_off;
+    plan.tile_off = s.tile_off;
+    plan.max_tiles = (nc * P + kTile - 1) / kTile + L;
+    {
+      StageTimer t(ix, ST_SCAN, st, 1);
+      launch_scan_simt(Yc, Ync, ix->XL, ix->XLn, ix->list_off, L, ix->dp, plan, s.cand, st);
+    }
+    StageTimer tsel(ix, ST_SELECT, st, 1);
+    SelectArgs a;
+    a.cand = s.cand;
+    a.q_off = s.q_off;
+    a.q_count = s.q_count;
+    a.seg_off = s.seg_off;
+    a.probes = s.probes;
+    a.P = P;
+    a.list_off = ix->list_off;
+    a.XL = ix->XL;
+    a.XLn = ix->XLn;
+    a.perm = ix->perm;
+    a.X = ix->X;
+    a.xmax = ix->xmax;
+    a.Y = Yc;
+    a.Yn = Ync;
+    a.nq = nc;
+    a.d = ix->d;
+    a.dp = ix->dp;
+    a.k = k;
+    a.kprime = kprime;
+    a.kern = ix->kern;
+    a.h = ix->h;
+    a.err_scale = scan_err_scale(ix->dp, precision);
+    a.nbr = nbr + q0 * k;
+    a.nd2 = nd2 ? nd2 + q0 * k : nullptr;
+    a.s1 = s1 ? s1 + q0 : nullptr;
+    a.kcount = nullptr;
+    a.err = ix->err;
+    launch_select_neighbors(a, st);
+  }
+  CK(cudaGetLastError());
+  return KDE_OK;
+}
+
+SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int32_t* nbr, int k,
+                       int m, uint64_t seed, const kde_opts* o) {
+  SampleArgs a;
+  a.X = ix->X;
+  a.n = ix->n;
+  a.d = ix->d;
+  a.dp = ix->dp;
+  a.kern = ix->kern;
+  a.h = ix->h;
+  a.Y = cb.Yp;
+  a.nq = nq;
+  a.nbr = nbr;
+  a.k = k;
+  a.m = m;
+  a.seed = seed;
+  a.qid_offset = o->query_id_offset;
+  a.mode = o->sample_mode;
+  a.s1_in = nullptr;
+  a.kcount_in = nullptr;
+  a.out = nullptr;
+  a.samples = nullptr;
+  a.rs = 0;
+  a.gout = nullptr;
+  a.dY = nullptr;
+  a.dlogh = nullptr;
+  a.err = ix->err;
+  return a;
+}
+
+kde_status check_index(const kde_index* ix) {
+  if (ix == nullptr) return fail(KDE_EINVAL, "index is NULL");
+  return KDE_OK;
+}
+
+kde_status check_opts(const kde_opts* o) {
+  if (o->precision != KDE_PREC_FP32 && o->precision != KDE_PREC_BF16)
+    return fail(KDE_EINVAL, "precision must be 0 (FP32) or 1 (BF16)");
+  if (o->sample_mode != 0 && o->sample_mode != 1)
+    return fail(KDE_EINVAL, "sample_mode must be 0 or 1");
+  if (o->reserved != 0) return fail(KDE_EINVAL, "kde_opts.reserved must be 0");
+  return KDE_OK;
+}
+
+// Decides the space of a call from Y and checks the other arrays agree.
+kde_status call_space(const kde_index* ix, const void* Y, std::initializer_list<const void*> others,
+                      bool* host) {
+  const Space s = space_of(Y, ix->device);
+  if (s == SPACE_FOREIGN) return fail(KDE_ESTATE, "Y lives on another device than the index");
+  for (const void* p : others) {
+    if (p == nullptr) continue;
+    if (space_of(p, ix->device) != s)
+      return fail(KDE_EINVAL, "all arrays of a call must be host or all device pointers");
+  }
+  *host = (s == SPACE_HOST);
+  return KDE_OK;
+}
+
+kde_status copy_out(void* dst, const void* src, size_t bytes, bool host, cudaStream_t st) {
+  if (bytes == 0) return KDE_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     st));
+  return KDE_OK;
+}
+
+kde_status finish_call(kde_index* ix, bool host, cudaStream_t st) {
+  CK(cudaGetLastError());
+  if (!host) return KDE_OK;
+  int64_t margin = 0;
+  kde_status s = collect_errors(ix, st, &margin);
+  ix_margin_accumulate(ix, margin);
+  return s;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* kde_strerror(kde_status s) {
+  switch (s) {
+    case KDE_OK: return "success";
+    case KDE_EINVAL: return "invalid argument";
+    case KDE_ENOMEM: return "out of device memory";
+    case KDE_ECUDA: return "CUDA runtime error";
+    case KDE_ELIMIT: return "draw cap reached";
+    case KDE_ESTATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* kde_last_error(void) { return g_err.c_str(); }
+
+kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, float h,
+                     int32_t nlist, uint64_t seed, const kde_opts* opts, kde_index** out) {
+  if (out == nullptr) return fail(KDE_EINVAL, "out is NULL");
+  *out = nullptr;
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  if (X == nullptr) return fail(KDE_EINVAL, "X is NULL");
+  if (n < 1 || n > INT32_MAX) return fail(KDE_EINVAL, "n must be in [1, 2^31 - 1]");
+  if (d < 1 || d > kMaxDim) return fail(KDE_EINVAL, "d must be in [1, %d]", kMaxDim);
+  if (!(h > 0.f) || !std::isfinite(h)) return fail(KDE_EINVAL, "h must be positive and finite");
+  if (kernel != KDE_GAUSSIAN && kernel != KDE_EXPONENTIAL && kernel != KDE_LAPLACIAN)
+    return fail(KDE_EINVAL, "unknown kernel");
+  if (nlist < 1 || (int64_t)nlist > n || nlist > 8192)
+    return fail(KDE_EINVAL, "nlist must be in [1, min(n, 8192)]");
+  const int iters = o->kmeans_iters > 0 ? o->kmeans_iters : 20;
+  cudaStream_t st = stream_of(o);
+
+  kde_index* ix = new kde_index();
+  CK(cudaGetDevice(&ix->device));
+  const Space xs = space_of(X, ix->device);
+  if (xs == SPACE_FOREIGN) {
+    delete ix;
+    return fail(KDE_ESTATE, "X lives on another device");
+  }
+  ix->n = n;
+  ix->d = d;
+  ix->dp = padded_dim(d);
+  ix->dpb = (d + 63) & ~63;
+  ix->nlist = nlist;
+  ix->kern = (int)kernel;
+  ix->h = h;
+  ix->seed = seed;
+  const int64_t L = nlist;
+  kde_status s = KDE_OK;
+  auto bail = [&](kde_status st2) {
+    kde_free(ix);
+    return st2;
+  };
+#define BTRY(expr)                      \
+  do {                                  \
+    kde_status s2_ = (expr);            \
+    if (s2_ != KDE_OK) return bail(s2_); \
+  } while (0)
+#define BCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return bail(fail(KDE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));    \
+  } while (0)
+
+  BTRY(dev_alloc(&ix->X, (size_t)n * ix->dp));
+  BTRY(dev_alloc(&ix->Xn, (size_t)n));
+  BTRY(dev_alloc(&ix->XL, (size_t)n * ix->dp));
+  BTRY(dev_alloc(&ix->XLn, (size_t)n));
+  BTRY(dev_alloc(&ix->perm, (size_t)n));
+  BTRY(dev_alloc(&ix->assign, (size_t)n));
+  BTRY(dev_alloc(&ix->list_off, (size_t)L + 1));
+  BTRY(dev_alloc(&ix->C, (size_t)L * ix->dp));
+  BTRY(dev_alloc(&ix->Cn, (size_t)L));
+  BTRY(dev_alloc(&ix->err, 4));
+  BTRY(dev_alloc(&ix->xmax_d, 1));
+  {
+    uint16_t* b = nullptr;
+    BTRY(dev_alloc(&b, (size_t)n * ix->dpb));
+    ix->XLb = b;
+  }
+  BCK(cudaMemsetAsync(ix->err, 0, 4 * sizeof(uint32_t), st));
+
+  // build scratch
+  const int64_t nchunks = (n + 2047) / 2048;
+  Bump cnt;
+  cnt.take<float>((size_t)n * d);  // staging copy of a host X
+  cnt.take<float>(n);              // best_d2
+  cnt.take<float>(n);              // tmp_d2
+  cnt.take<int64_t>((size_t)L * nchunks);
+  cnt.take<int32_t>(L);            // empty flags
+  cnt.take<uint32_t>((n + 31) / 32 + 1);
+  cnt.take<int32_t>(L);            // chosen
+  cnt.take<int64_t>(L);            // counts
+  BTRY(ensure_scratch(ix, cnt.used));
+  Bump b;
+  b.base = ix->scratch.base;
+  float* stage = b.take<float>((size_t)n * d);
+  float* best_d2 = b.take<float>(n);
+  float* tmp_d2 = b.take<float>(n);
+  int64_t* chunk_hist = b.take<int64_t>((size_t)L * nchunks);
+  int32_t* empty = b.take<int32_t>(L);
+  uint32_t* bitmap = b.take<uint32_t>((n + 31) / 32 + 1);
+  int32_t* chosen = b.take<int32_t>(L);
+  int64_t* counts = b.take<int64_t>(L);
+
+  const float* src = X;
+  if (xs == SPACE_HOST) {
+    BCK(cudaMemcpyAsync(stage, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, st));
+    src = stage;
+  }
+  launch_pad_rows(src, n, d, ix->X, ix->dp, st);
+  launch_row_norms(ix->X, n, ix->dp, ix->Xn, st);
+  launch_max_f32(ix->Xn, n, ix->xmax_d, st);
+
+  if (L == 1) {
+    launch_fill_i32(ix->assign, n, 0, st);
+  } else {
+    launch_kmeans_init(ix->X, n, ix->dp, (int)L, seed, bitmap, chosen, ix->C, ix->err, st);
+    for (int it = 0; it < iters; ++it) {
+      launch_assign_simt(ix->X, n, ix->C, (int)L, d, ix->dp, ix->assign, best_d2, st);
+      launch_list_hist(ix->assign, n, (int)L, counts, st);
+      launch_exclusive_scan_i64(counts, L, ix->list_off, st);
+      launch_stable_scatter(ix->assign, n, (int)L, ix->list_off, chunk_hist, ix->perm, st);
+      launch_centroid_update(ix->X, ix->dp, ix->perm, ix->list_off, (int)L, ix->C, empty, st);
+      launch_reseed_empty(ix->X, n, ix->dp, best_d2, empty, (int)L, ix->C, tmp_d2, st);
+    }
+    launch_assign_simt(ix->X, n, ix->C, (int)L, d, ix->dp, ix->assign, best_d2, st);
+  }
+  launch_list_hist(ix->assign, n, (int)L, counts, st);
+  launch_exclusive_scan_i64(counts, L, ix->list_off, st);
+  launch_stable_scatter(ix->assign, n, (int)L, ix->list_off, chunk_hist, ix->perm, st);
+  if (L == 1) launch_centroid_update(ix->X, ix->dp, ix->perm, ix->list_off, 1, ix->C, empty, st);
+  launch_row_norms(ix->C, L, ix->dp, ix->Cn, st);
+  launch_gather_rows(ix->X, ix->dp, ix->perm, n, ix->XL, st);
+  launch_gather_f32(ix->Xn, ix->perm, n, ix->XLn, st);
+  launch_to_bf16(ix->XL, n, ix->dp, ix->XLb, ix->dpb, st);
+  BCK(cudaGetLastError());
+
+  ix->h_list_off = new int64_t[L + 1];
+  BCK(cudaMemcpyAsync(ix->h_list_off, ix->list_off, sizeof(int64_t) * (L + 1),
+                      cudaMemcpyDeviceToHost, st));
+  float xmax2 = 0.f;
+  BCK(cudaMemcpyAsync(&xmax2, ix->xmax_d, sizeof(float), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  ix->xmax = std::sqrt(xmax2);
+  ix->max_list = 0;
+  for (int64_t l = 0; l < L; ++l)
+    ix->max_list = std::max(ix->max_list, ix->h_list_off[l + 1] - ix->h_list_off[l]);
+  int64_t margin = 0;
+  s = collect_errors(ix, st, &margin);
+  if (s == KDE_ELIMIT) s = KDE_OK;  // k-means init fell back to fixed points
+  if (s != KDE_OK) return bail(s);
+#undef BTRY
+#undef BCK
+  *out = ix;
+  return KDE_OK;
+}
+
+void kde_free(kde_index* ix) {
+  if (ix == nullptr) return;
+  DeviceGuard g(ix->device);
+  cudaDeviceSynchronize();
+  cudaFree(ix->X);
+  cudaFree(ix->Xn);
+  cudaFree(ix->XL);
+  cudaFree(ix->XLn);
+  cudaFree(ix->XLb);
+  cudaFree(ix->perm);
+  cudaFree(ix->assign);
+  cudaFree(ix->list_off);
+  cudaFree(ix->C);
+  cudaFree(ix->Cn);
+  cudaFree(ix->err);
+  cudaFree(ix->xmax_d);
+  if (ix->scratch.base) cudaFree(ix->scratch.base);
+  for (const auto& e : ix->events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete[] ix->h_list_off;
+  delete ix;
+}
+
+kde_status kde_set_bandwidth(kde_index* ix, float h) {
+  TRY(check_index(ix));
+  if (!(h > 0.f) || !std::isfinite(h)) return fail(KDE_EINVAL, "h must be positive and finite");
+  ix->h = h;
+  return KDE_OK;
+}
+
+kde_status kde_index_info(const kde_index* ix, int64_t* n, int32_t* d, int32_t* nlist,
+                          int32_t* kernel, float* h, int64_t* max_list) {
+  TRY(check_index(ix));
+  if (n) *n = ix->n;
+  if (d) *d = ix->d;
+  if (nlist) *nlist = ix->nlist;
+  if (kernel) *kernel = ix->kern;
+  if (h) *h = ix->h;
+  if (max_list) *max_list = ix->max_list;
+  return KDE_OK;
+}
+
+kde_status kde_export_ivf(kde_index* ix, float* centroids, int32_t* assign) {
+  TRY(check_index(ix));
+  DeviceGuard g(ix->device);
+  if (centroids)
+    CK(cudaMemcpy2D(centroids, sizeof(float) * ix->d, ix->C, sizeof(float) * ix->dp,
+                    sizeof(float) * ix->d, (size_t)ix->nlist, cudaMemcpyDeviceToHost));
+  if (assign)
+    CK(cudaMemcpy(assign, ix->assign, sizeof(int32_t) * ix->n, cudaMemcpyDeviceToHost));
+  return KDE_OK;
+}
+
+static kde_status check_search_args(const kde_index* ix, int64_t nq, int32_t k, int32_t nprobe) {
+  if (nq < 0 || nq > INT32_MAX) return fail(KDE_EINVAL, "nq must be in [0, 2^31 - 1]");
+  if (k < 1 || k > kMaxK || (int64_t)k > ix->n)
+    return fail(KDE_EINVAL, "k must be in [1, min(n, %d)]", kMaxK);
+  if (nprobe < 1 || nprobe > ix->nlist || nprobe > kMaxProbe)
+    return fail(KDE_EINVAL, "nprobe must be in [1, min(nlist, %d)]", kMaxProbe);
+  return KDE_OK;
+}
+
+kde_status kde_search(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32_t nprobe,
+                      int32_t* nbr, float* d2, const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_search_args(ix, nq, k, nprobe));
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr || nbr == nullptr) return fail(KDE_EINVAL, "Y and nbr must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {nbr, d2}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.P = nprobe;
+  c.search = true;
+  c.host = host;
+  c.need_nbr = host;
+  c.need_nd2 = host && d2 != nullptr;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  int32_t* nb = host ? cb.nbr : nbr;
+  float* dd = host ? cb.nd2 : d2;
+  TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, dd, nullptr, st));
+  if (host) {
+    TRY(copy_out(nbr, nb, sizeof(int32_t) * nq * k, true, st));
+    if (d2) TRY(copy_out(d2, dd, sizeof(float) * nq * k, true, st));
+  }
+  return finish_call(ix, host, st);
+}
+
+static kde_status check_est_args(const kde_index* ix, int64_t nq, int32_t k, int32_t m) {
+  if (nq < 0 || nq > INT32_MAX) return fail(KDE_EINVAL, "nq must be in [0, 2^31 - 1]");
+  if (k < 0 || k > kMaxK) return fail(KDE_EINVAL, "k must be in [0, %d]", kMaxK);
+  if (m < 0) return fail(KDE_EINVAL, "m must be >= 0");
+  if ((int64_t)m * 64 + 4096 > INT32_MAX) return fail(KDE_EINVAL, "m too large");
+  return KDE_OK;
+}
+
+kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32_t m,
+                     int32_t nprobe, uint64_t seed, float* out, int32_t* nbr,
+                     const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m));
+  if (k > 0) {
+    TRY(check_search_args(ix, nq, k, nprobe));
+  } else if (m < 1) {
+    return fail(KDE_EINVAL, "k = 0 needs m >= 1");
+  }
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr || out == nullptr) return fail(KDE_EINVAL, "Y and out must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {out, nbr}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.P = nprobe;
+  c.search = k > 0;
+  c.host = host;
+  c.need_out = host;
+  c.need_nbr = k > 0 && (host || nbr == nullptr);
+  c.need_s1 = k > 0;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  int32_t* nb = (k > 0) ? ((host || nbr == nullptr) ? cb.nbr : nbr) : nullptr;
+  if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st));
+  SampleArgs a = sample_args(ix, cb, nq, nb, k, m, seed, o);
+  a.s1_in = k > 0 ? cb.s1 : nullptr;
+  a.out = host ? cb.out : out;
+  a.rs = k == 0 ? 1 : 0;
+  {
+    StageTimer t(ix, ST_ESTIMATE, st, 1);
+    launch_estimate(a, st);
+  }
+  if (host) {
+    TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
+    if (nbr && k > 0) TRY(copy_out(nbr, nb, sizeof(int32_t) * nq * k, true, st));
+  }
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_query_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
+                                    const int32_t* nbr, int32_t k, int32_t m, uint64_t seed,
+                                    float* out, const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m));
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr || out == nullptr || (k > 0 && nbr == nullptr))
+    return fail(KDE_EINVAL, "Y, out (and nbr when k > 0) must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {out, k > 0 ? nbr : nullptr}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.host = host;
+  c.need_out = host;
+  c.need_nbr = host && k > 0;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  const int32_t* nb = nbr;
+  if (host && k > 0) {
+    CK(cudaMemcpyAsync(cb.nbr, nbr, sizeof(int32_t) * nq * k, cudaMemcpyHostToDevice, st));
+    nb = cb.nbr;
+  }
+  SampleArgs a = sample_args(ix, cb, nq, k > 0 ? nb : nullptr, k, m, seed, o);
+  a.out = host ? cb.out : out;
+  {
+    StageTimer t(ix, ST_ESTIMATE, st, 1);
+    launch_estimate(a, st);
+  }
+  if (host) TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_query_rs(kde_index* ix, const float* Y, int64_t nq, int32_t m, uint64_t seed,
+                        float* out, const kde_opts* opts) {
+  TRY(check_index(ix));
+  if (m < 1) return fail(KDE_EINVAL, "m must be >= 1");
+  kde_opts o2 = opts ? *opts : kDefaultOpts;
+  o2.sample_mode = 0;
+  return kde_query_with_neighbors(ix, Y, nq, nullptr, 0, m, seed, out, &o2);
+}
+
+kde_status kde_exact(kde_index* ix, const float* Y, int64_t nq, float* out,
+                     const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  if (nq < 0 || nq > INT32_MAX) return fail(KDE_EINVAL, "nq must be in [0, 2^31 - 1]");
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr || out == nullptr) return fail(KDE_EINVAL, "Y and out must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {out}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.host = host;
+  c.need_out = host;
+  c.exact = true;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  float* o_d = host ? cb.out : out;
+  {
+    StageTimer t(ix, ST_EXACT, st, 2);
+    launch_exact_simt(cb.Yp, cb.Yn, nq, ix->X, ix->Xn, ix->n, ix->d, ix->dp, ix->kern, ix->h,
+                      cb.acc, o_d, st);
+  }
+  if (host) TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_sample_indices(kde_index* ix, int64_t nq, const int32_t* nbr, int32_t k,
+                              int32_t m, uint64_t seed, int32_t* samples, const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m));
+  if (nq == 0 || m == 0) return KDE_OK;
+  if (samples == nullptr || (k > 0 && nbr == nullptr))
+    return fail(KDE_EINVAL, "samples (and nbr when k > 0) must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, samples, {k > 0 ? nbr : nullptr}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.host = host;
+  c.need_nbr = host && k > 0;
+  c.need_samples = host;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  const int32_t* nb = nbr;
+  if (host && k > 0) {
+    CK(cudaMemcpyAsync(cb.nbr, nbr, sizeof(int32_t) * nq * k, cudaMemcpyHostToDevice, st));
+    nb = cb.nbr;
+  }
+  // the estimator kernel stages a query row; give it zeros
+  CK(cudaMemsetAsync(cb.Yp, 0, sizeof(float) * nq * ix->dp, st));
+  SampleArgs a = sample_args(ix, cb, nq, k > 0 ? nb : nullptr, k, m, seed, o);
+  a.samples = host ? cb.samples : samples;
+  {
+    StageTimer t(ix, ST_ESTIMATE, st, 1);
+    launch_estimate(a, st);
+  }
+  if (host) TRY(copy_out(samples, cb.samples, sizeof(int32_t) * nq * m, true, st));
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_grad_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
+                                   const int32_t* nbr, int32_t k, int32_t m, uint64_t seed,
+                                   const float* gout, float* out, float* dY, float* dlogh,
+                                   const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m));
+  if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr || dY == nullptr || (k > 0 && nbr == nullptr))
+    return fail(KDE_EINVAL, "Y, dY (and nbr when k > 0) must not be NULL");
+  if (k == 0 && m == 0) return fail(KDE_EINVAL, "k = 0 needs m >= 1");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {k > 0 ? nbr : nullptr, gout, out, dY, dlogh}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.host = host;
+  c.need_out = host && out != nullptr;
+  c.need_nbr = host && k > 0;
+  c.grad = host;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  const int32_t* nb = nbr;
+  const float* go = gout;
+  if (host) {
+    if (k > 0) {
+      CK(cudaMemcpyAsync(cb.nbr, nbr, sizeof(int32_t) * nq * k, cudaMemcpyHostToDevice, st));
+      nb = cb.nbr;
+    }
+    if (gout) {
+      CK(cudaMemcpyAsync(cb.gout, gout, sizeof(float) * nq, cudaMemcpyHostToDevice, st));
+      go = cb.gout;
+    }
+  }
+  SampleArgs a = sample_args(ix, cb, nq, k > 0 ? nb : nullptr, k, m, seed, o);
+  a.gout = go;
+  a.out = host ? (out ? cb.out : nullptr) : out;
+  a.dY = host ? cb.dY : dY;
+  a.dlogh = host ? (dlogh ? cb.dlogh : nullptr) : dlogh;
+  {
+    StageTimer t(ix, ST_GRAD, st, 1);
+    launch_estimate_grad(a, st);
+  }
+  if (host) {
+    TRY(copy_out(dY, cb.dY, sizeof(float) * nq * ix->d, true, st));
+    if (out) TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
+    if (dlogh) TRY(copy_out(dlogh, cb.dlogh, sizeof(float) * nq, true, st));
+  }
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_sync(kde_index* ix, const kde_opts* opts) {
+  TRY(check_index(ix));
+  DeviceGuard g(ix->device);
+  int64_t margin = 0;
+  kde_status s = collect_errors(ix, stream_of(opts), &margin);
+  ix_margin_accumulate(ix, margin);
+  return s;
+}
+
+kde_status kde_stats(kde_index* ix, int64_t* margin_failures, const kde_opts* opts) {
+  TRY(check_index(ix));
+  DeviceGuard g(ix->device);
+  int64_t margin = 0;
+  kde_status s = collect_errors(ix, stream_of(opts), &margin);
+  ix_margin_accumulate(ix, margin);
+  if (margin_failures) *margin_failures = ix->margin_failures;
+  return s;
+}
+
+kde_status kde_profile_enable(kde_index* ix, int32_t on) {
+  TRY(check_index(ix));
+  ix->prof = on != 0;
+  return KDE_OK;
+}
+
+kde_status kde_profile_read(kde_index* ix, kde_profile* out, int32_t reset,
+                            const kde_opts* opts) {
+  TRY(check_index(ix));
+  if (out == nullptr) return fail(KDE_EINVAL, "out is NULL");
+  DeviceGuard g(ix->device);
+  CK(cudaStreamSynchronize(stream_of(opts)));
+  CK(cudaDeviceSynchronize());
+  for (int s = 0; s < KDE_NUM_STAGES; ++s) {
+    out->ms[s] = 0.0;
+    out->timed[s] = 0;
+    out->calls[s] = ix->calls[s];
+    out->launches[s] = ix->launches[s];
+  }
+  for (const auto& e : ix->events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      out->ms[e.stage] += ms;
+      out->timed[e.stage] += 1;
+    }
+  }
+  if (reset) {
+    for (const auto& e : ix->events) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    ix->events.clear();
+    for (int s = 0; s < KDE_NUM_STAGES; ++s) ix->calls[s] = ix->launches[s] = 0;
+  }
+  return KDE_OK;
+}
+
+kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
+                       const kde_opts* opts) {
+  TRY(check_index(ix));
+  (void)opts;
+  DeviceGuard g(ix->device);
+  size_t need = 0;
+  for (int variant = 0; variant < 4; ++variant) {
+    CallShape c;
+    c.nq = nq;
+    c.k = k;
+    c.m = m;
+    c.P = std::max(1, nprobe);
+    c.search = k > 0;
+    c.host = true;
+    c.need_out = c.need_s1 = true;
+    c.need_nbr = c.need_nd2 = k > 0;
+    c.need_samples = variant == 1;
+    c.grad = variant == 2;
+    c.exact = variant == 3;
+    Bump cnt;
+    CallBufs dummy;
+    carve_call(cnt, ix, c, dummy);
+    need = std::max(need, cnt.used);
+  }
+  return ensure_scratch(ix, need);
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations of the DEANN GB300 library: the index layout in HBM
+// and the launchers each translation unit provides.  Not part of the C-ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#define KDE_KERN_GAUSSIAN 0
+#define KDE_KERN_EXPONENTIAL 1
+#define KDE_KERN_LAPLACIAN 2
+
+// Device error word bits (index->err[0]); index->err[1] counts queries whose
+// candidate margin could not be certified.
+#define KDE_ERRBIT_DRAWCAP 1u
+#define KDE_ERRBIT_BADNBR 2u
+#define KDE_ERRBIT_MARGIN 4u
+#define KDE_ERRBIT_TMA 8u
+
+namespace deann {
+
+constexpr int kMaxDim = 4096;        // largest supported d
+constexpr int kMaxK = 1024;          // largest neighbour count k
+constexpr int kMaxProbe = 256;       // largest nprobe
+constexpr int kSelectCap = 2048;     // largest candidate count kept for rescoring
+constexpr int kTile = 64;            // SIMT distance tile edge
+
+// Row stride (in floats) of every FP32 row-major matrix: d rounded up to a
+// multiple of 4 so rows start on 16-byte boundaries; padding is zero.
+inline int padded_dim(int d) { return (d + 3) & ~3; }
+
+// Bump allocator over one device buffer owned by an index.  Calls on one
+// index are stream-ordered, so scratch is reused call after call.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  void reset() { used = 0; }
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (used + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+}  // namespace deann
+
+struct kde_index {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0;
+  int dp = 0;                 // padded row stride (floats)
+  int dpb = 0;                // padded row stride of the BF16 copy (elements)
+  int nlist = 1;
+  int kern = 0;
+  float h = 1.f;
+  uint64_t seed = 0;
+  // dataset, original order: X[n x dp] FP32 and squared norms
+  float* X = nullptr;
+  float* Xn = nullptr;
+  // dataset, IVF list order (list-contiguous): FP32, BF16 and norms
+  float* XL = nullptr;
+  float* XLn = nullptr;
+  void* XLb = nullptr;        // __nv_bfloat16 [n x dpb]
+  int32_t* perm = nullptr;    // list position -> original id
+  int32_t* assign = nullptr;  // original id -> list id
+  int64_t* list_off = nullptr;  // [nlist + 1] device
+  int64_t* h_list_off = nullptr;  // host copy
+  int64_t max_list = 0;
+  float* C = nullptr;         // centroids [nlist x dp]
+  float* Cn = nullptr;
+  uint32_t* err = nullptr;    // device error words [4]
+  float* xmax_d = nullptr;    // device max |x|^2
+  float xmax = 0.f;           // max |x| over the dataset
+  int64_t margin_failures = 0;
+  deann::Arena scratch;
+  size_t scratch_limit = size_t(16) << 30;
+  // per-stage profiling (CUDA events on the call's stream) and launch counts
+  static constexpr int kStages = 8;
+  bool prof = false;
+  struct EvPair {
+    cudaEvent_t a, b;
+    int stage;
+  };
+  std::vector<EvPair> events;
+  int64_t launches[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t calls[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace deann {
+
+// ---- build.cu -------------------------------------------------------------
+void launch_row_norms(const float* X, int64_t n, int dp, float* out, cudaStream_t s);
+void launch_pad_rows(const float* src, int64_t n, int d, float* dst, int dp, cudaStream_t s);
+void launch_kmeans_init(const float* X, int64_t n, int dp, int L, uint64_t seed,
+                        uint32_t* bitmap, int32_t* chosen, float* C, uint32_t* err, cudaStream_t s);
+void launch_max_f32(const float* v, int64_t n, float* out, cudaStream_t s);
+void launch_list_hist(const int32_t* assign, int64_t n, int L, int64_t* counts, cudaStream_t s);
+void launch_exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, cudaStream_t s);
+void launch_stable_scatter(const int32_t* assign, int64_t n, int L, const int64_t* list_off,
+                           int64_t* chunk_hist, int32_t* perm, cudaStream_t s);
+void launch_centroid_update(const float* X, int dp, const int32_t* perm, const int64_t* list_off,
+                            int L, float* C, int32_t* empty_flags, cudaStream_t s);
+void launch_reseed_empty(const float* X, int64_t n, int dp, const float* best_d2,
+                         int32_t* empty_flags, int L, float* C, float* tmp_d2, cudaStream_t s);
+void launch_gather_rows(const float* X, int dp, const int32_t* ids, int64_t count, float* dst,
+                        cudaStream_t s);
+void launch_gather_f32(const float* v, const int32_t* ids, int64_t count, float* dst,
+                       cudaStream_t s);
+void launch_to_bf16(const float* X, int64_t n, int dp, void* dst, int dpb, cudaStream_t s);
+void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s);
+
+// ---- tiles.cu (SIMT distance tiles) ---------------------------------------
+void launch_exact_simt(const float* Y, const float* Yn, int64_t nq, const float* X,
+                       const float* Xn, int64_t n, int d, int dp, int kern, float h,
+                       double* acc, float* out, cudaStream_t s);
+void launch_assign_simt(const float* P, int64_t np, const float* C, int L, int d, int dp,
+                        int32_t* assign, float* best_d2, cudaStream_t s);
+void launch_dist_matrix(const float* Y, const float* Yn, int64_t nq, const float* C,
+                        const float* Cn, int L, int dp, float* D, cudaStream_t s);
+struct ScanPlan {
+  const int32_t* pair_q;      // query of each (query, probe) pair, bucketed by list
+  const int64_t* pair_dst;    // destination offset of the pair's segment in cand
+  const int64_t* bucket_off;  // [L + 1] pairs of list l: [bucket_off[l], bucket_off[l+1])
+  const int64_t* tile_off;    // [L + 1] query tiles of list l
+  int64_t max_tiles;          // grid bound
+};
+void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const float* XLn,
+                      const int64_t* list_off, int L, int dp, const ScanPlan& plan, float* cand,
+                      cudaStream_t s);
+
+// ---- select.cu -------------------------------------------------------------
+void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStream_t s);
+void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
+                          const float* C, int nprobe, int margin, int32_t* probes,
+                          cudaStream_t s);
+void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
+                       int64_t* q_count, int64_t* q_off, int64_t* seg_off, int64_t* list_cnt,
+                       int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
+                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
+                       cudaStream_t s);
+struct SelectArgs {
+  const float* cand;
+  const int64_t* q_off;
+  const int64_t* q_count;
+  const int64_t* seg_off;    // [nq x P]
+  const int32_t* probes;     // [nq x P]
+  int P;
+  const int64_t* list_off;
+  const float* XL;
+  const float* XLn;
+  const int32_t* perm;
+  const float* X;            // original order (Laplacian neighbour sums)
+  float xmax;                // max |x| over the dataset
+  const float* Y;
+  const float* Yn;
+  int64_t nq;
+  int d, dp;
+  int k, kprime;
+  int kern;
+  float h;
+  float err_scale;           // approx-distance error bound per unit of (|x| + |y|)^2
+  int32_t* nbr;              // [nq x k] original ids, -1 pad
+  float* nd2;                // [nq x k] precise squared distances (nullable)
+  float* s1;                 // [nq] sum of kernel values over the k' neighbours (nullable)
+  int32_t* kcount;           // [nq] k' (nullable)
+  uint32_t* err;
+};
+void launch_select_neighbors(const SelectArgs& a, cudaStream_t s);
+
+// ---- sample.cu --------------------------------------------------------------
+struct SampleArgs {
+  const float* X;            // original order
+  int64_t n;
+  int d, dp;
+  int kern;
+  float h;
+  const float* Y;
+  int64_t nq;
+  const int32_t* nbr;        // [nq x k] or null (k = 0)
+  int k;
+  int m;
+  uint64_t seed;
+  uint64_t qid_offset;
+  int mode;                  // 0 reject, 1 drop
+  const float* s1_in;        // precomputed neighbour sums (nullable)
+  const int32_t* kcount_in;  // matching k' (nullable)
+  float* out;                // [nq] estimates (nullable)
+  int32_t* samples;          // [nq x m] sample indices (nullable)
+  int rs;                    // 1: plain random sampling (ignore nbr)
+  // adjoint
+  const float* gout;         // [nq] (grad only)
+  float* dY;                 // [nq x d] (grad only)
+  float* dlogh;              // [nq] (grad only)
+  uint32_t* err;
+};
+void launch_estimate(const SampleArgs& a, cudaStream_t s);
+void launch_estimate_grad(const SampleArgs& a, cudaStream_t s);
+
+}  // namespace deann

@@ -1,0 +1,551 @@
+// The DEANN estimator's sampling half (Algorithm 1, lines 4-7) and random
+// sampling (Lemma RS), plus the adjoint of both.
+//
+// One CTA of 256 threads serves one query:
+//  1. the neighbour set X_1 (k ids, -1 padding, duplicates allowed) is sorted
+//     and deduplicated in shared memory: k' = |X_1|;
+//  2. s1 = sum_{X_1} K_h(x, y) (or taken from the selection kernel);
+//  3. the sample S: Philox draws t = 0, 1, 2, ... of the query's stream are
+//     mapped to indices in [0, n); draws that fall in X_1 are rejected (binary
+//     search in shared memory) and the first m accepted ones are kept, so S is
+//     uniform on X \ X_1 with repetition.  Draws are generated 256 at a time
+//     and ranked with warp ballots, which reproduces the sequential order
+//     exactly.  Past 64 m + 4096 draws the query is abandoned with an error
+//     flag (reachable only when k' is close to n);
+//  4. the sampled rows are gathered with coalesced 16-byte loads (G lanes per
+//     row, several rows in flight per group) and s2 = sum_S K_h(x, y);
+//  5. out = (s1 + ((n - k') / m) s2) / n.
+// "drop" mode (sample_mode 1) instead takes draws 0..m-1 from all of X and
+// gives the ones in X_1 weight zero: out = s1 / n + s2 / m.
+#include "common.cuh"
+
+namespace deann {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
+constexpr int kChunk = 1024;   // samples staged per gather round
+constexpr int kUnroll = 4;     // rows in flight per lane group
+
+struct EstSmem {
+  int nb[kMaxK];               // sorted distinct neighbour ids
+  int S[kChunk];
+  int warp_cnt[kNW];
+  float red[kNW];
+  int kk;
+  int cnt;
+  int64_t tnext;
+  int status;
+};
+
+__device__ __forceinline__ bool is_member(const int* nb, int kk, int64_t id) {
+  int lo = 0, hi = kk;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (nb[mid] < id) lo = mid + 1; else hi = mid;
+  }
+  return lo < kk && nb[lo] == id;
+}
+
+// Loads, sorts and deduplicates the neighbour row into sm.nb; sets sm.kk, or
+// sm.status = 1 when an id is >= n.
+__device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t n, EstSmem& sm,
+                                int* tmp /* >= next_pow2(k) ints */) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int P2 = 1;
+  while (P2 < k) P2 <<= 1;
+  if (tid == 0) sm.status = 0;
+  __syncthreads();
+  for (int i = tid; i < P2; i += kNT) {
+    int v = 0x7fffffff;
+    if (i < k) {
+      const int32_t id = row[i];
+      if (id >= 0) {
+        if ((int64_t)id >= n) sm.status = 1;
+        else v = id;
+      }
+    }
+    tmp[i] = v;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < P2 / 2; i += kNT) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const int a = tmp[lo], b = tmp[hi];
+        if ((a > b) == up) {
+          tmp[lo] = b;
+          tmp[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  // compact the distinct valid ids, keeping sorted order
+  int base = 0;
+  for (int b0 = 0; b0 < P2; b0 += kNT) {
+    const int i = b0 + tid;
+    const bool keep = i < P2 && tmp[i] != 0x7fffffff && (i == 0 || tmp[i] != tmp[i - 1]);
+    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) sm.warp_cnt[warp] = __popc(mk);
+    __syncthreads();
+    int off = base, tot = 0;
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) off += sm.warp_cnt[w];
+      tot += sm.warp_cnt[w];
+    }
+    if (keep) sm.nb[off + __popc(mk & ((1u << lane) - 1u))] = tmp[i];
+    base += tot;
+    __syncthreads();
+  }
+  if (tid == 0) sm.kk = base;
+  __syncthreads();
+}
+
+// Fills sm.S[0..sm.cnt) with the next accepted sample indices (at most
+// `room`), starting at draw t0; sets sm.tnext to the first unused draw.
+// mode 0 rejects members of X_1; mode 1 accepts every draw.  Returns false
+// when the draw cap is reached.
+__device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, int64_t cap,
+                           int room, int mode, const EstSmem& smc, EstSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int filled = 0;
+  int64_t t = t0;
+  bool ok = true;
+  while (filled < room) {
+    if (t >= cap) {
+      ok = false;
+      break;
+    }
+    const int64_t tt = t + tid;
+    bool acc = false;
+    int64_t id = 0;
+    if (tt < cap) {
+      id = draw_index(seed, qid, (uint32_t)tt, 0u, n);
+      acc = (mode == 1) || !is_member(smc.nb, smc.kk, id);
+    }
+    const unsigned ma = __ballot_sync(0xffffffffu, acc);
+    if (lane == 0) sm.warp_cnt[warp] = __popc(ma);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) off += sm.warp_cnt[w];
+      tot += sm.warp_cnt[w];
+    }
+    const int rank = off + __popc(ma & ((1u << lane) - 1u));
+    const int left = room - filled;
+    if (acc && rank < left) {
+      sm.S[filled + rank] = (int)id;
+      if (rank == left - 1) sm.tnext = tt + 1;
+    }
+    if (tot >= left) {
+      filled = room;
+    } else {
+      filled += tot;
+      t += kNT;
+      if (t > cap) t = cap;
+      if (tid == 0) sm.tnext = t;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) sm.cnt = filled;
+  __syncthreads();
+  return ok;
+}
+
+// Sum of kernel values over rows ids[0..cnt) of X, by groups of G lanes.
+// Returns this thread's partial (lane-in-group 0 holds the group sums).
+template <int G, bool L1>
+__device__ float gather_sum(const float* __restrict__ X, int dp, const float* __restrict__ ys,
+                            const int* ids, int cnt, int kern, float inv) {
+  const int tid = threadIdx.x;
+  const int lig = tid & (G - 1);
+  constexpr int kGpw = 32 / G;  // groups per warp
+  const int gw = (tid & 31) / G, warp = tid >> 5;
+  const int dp4 = dp >> 2;
+  const float4* y4 = reinterpret_cast<const float4*>(ys);
+  float part = 0.f;
+  // warp-uniform trip count: the group reductions below need all 32 lanes
+  for (int wb = warp * kGpw * kUnroll; wb < cnt; wb += kNW * kGpw * kUnroll) {
+    const int base = wb + gw * kUnroll;
+    const float4* rows[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int r = base + u;
+      rows[u] = r < cnt ? reinterpret_cast<const float4*>(X + (int64_t)ids[r] * dp) : nullptr;
+    }
+    float acc[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) acc[u] = 0.f;
+    for (int j4 = lig; j4 < dp4; j4 += G) {
+      const float4 yv = y4[j4];
+      float4 xv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        xv[u] = rows[u] ? __ldg(rows[u] + j4) : yv;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const float a = xv[u].x - yv.x, b = xv[u].y - yv.y, c = xv[u].z - yv.z,
+                    e = xv[u].w - yv.w;
+        if (L1) {
+          acc[u] += (fabsf(a) + fabsf(b)) + (fabsf(c) + fabsf(e));
+        } else {
+          acc[u] = fmaf(a, a, acc[u]);
+          acc[u] = fmaf(b, b, acc[u]);
+          acc[u] = fmaf(c, c, acc[u]);
+          acc[u] = fmaf(e, e, acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const float dist = group_sum<G>(acc[u]);
+      if (lig == 0 && base + u < cnt) part += kernel_from_dist(kern, dist, inv);
+    }
+  }
+  return part;
+}
+
+template <int G>
+__device__ float gather_sum_k(const float* X, int dp, const float* ys, const int* ids, int cnt,
+                              int kern, float inv) {
+  return kern == KDE_KERN_LAPLACIAN ? gather_sum<G, true>(X, dp, ys, ids, cnt, kern, inv)
+                                    : gather_sum<G, false>(X, dp, ys, ids, cnt, kern, inv);
+}
+
+__device__ float block_sum(float v, EstSmem& sm) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm.red[warp] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < kNW; ++w) t += sm.red[w];
+  __syncthreads();
+  return t;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kNT) k_estimate(SampleArgs a) {
+  __shared__ EstSmem sm;
+  __shared__ int tmp[kMaxK];
+  extern __shared__ float4 ys4[];
+  float* ys = reinterpret_cast<float*>(ys4);
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  const uint64_t qid = a.qid_offset + (uint64_t)q;
+  for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
+  const int k = a.rs ? 0 : a.k;
+  if (k > 0) {
+    load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
+  } else {
+    if (tid == 0) {
+      sm.kk = 0;
+      sm.status = 0;
+    }
+    __syncthreads();
+  }
+  if (sm.status) {
+    if (tid == 0) {
+      atomicOr(a.err, KDE_ERRBIT_BADNBR);
+      if (a.out) a.out[q] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  const int kk = sm.kk;
+  const float inv = kernel_inv(a.kern, a.h);
+  float s1 = 0.f;
+  if (a.s1_in != nullptr) {
+    s1 = a.s1_in[q];
+  } else if (kk > 0 && a.out) {
+    s1 = block_sum(gather_sum_k<G>(a.X, a.dp, ys, sm.nb, kk, a.kern, inv), sm);
+  }
+  const bool sampled = !((int64_t)kk == a.n || a.m == 0);
+  float s2 = 0.f;
+  bool ok = true;
+  if (sampled) {
+    const int64_t cap = a.mode == 1 ? (int64_t)a.m : 64 * (int64_t)a.m + 4096;
+    int64_t t0 = 0;
+    int got = 0;
+    float part = 0.f;
+    while (got < a.m) {
+      const int room = min(kChunk, a.m - got);
+      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm)) {
+        ok = false;
+        break;
+      }
+      const int cnt = sm.cnt;
+      t0 = sm.tnext;
+      if (a.samples)
+        for (int i = tid; i < cnt; i += kNT) a.samples[q * a.m + got + i] = sm.S[i];
+      if (a.out) {
+        if (a.mode == 1) {
+          // draws inside X_1 carry weight zero: compact them away first
+          __syncthreads();
+          if (tid == 0) {
+            int w = 0;
+            for (int i = 0; i < cnt; ++i)
+              if (!is_member(sm.nb, kk, sm.S[i])) sm.S[w++] = sm.S[i];
+            sm.cnt = w;
+          }
+          __syncthreads();
+        }
+        part += gather_sum_k<G>(a.X, a.dp, ys, sm.S, sm.cnt, a.kern, inv);
+      }
+      got += cnt;
+      __syncthreads();
+    }
+    if (a.out) s2 = block_sum(part, sm);
+  }
+  if (tid == 0) {
+    if (!ok) {
+      atomicOr(a.err, KDE_ERRBIT_DRAWCAP);
+      if (a.out) a.out[q] = __int_as_float(0x7fc00000);
+      if (a.samples)
+        for (int i = 0; i < a.m; ++i) a.samples[q * a.m + i] = -1;
+    } else if (a.out) {
+      const double n = (double)a.n;
+      double est;
+      if (!sampled) est = (double)s1 / n;
+      else if (a.mode == 1) est = (double)s1 / n + (double)s2 / (double)a.m;
+      else est = ((double)s1 + (n - (double)kk) / (double)a.m * (double)s2) / n;
+      a.out[q] = (float)est;
+    }
+    if (sampled == false && a.samples)
+      for (int i = 0; i < a.m; ++i) a.samples[q * a.m + i] = -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: d out / d y and d out / d log h with X_1 and S held fixed (the
+// pathwise derivative of the estimator; the paper defines none).  With
+// out = sum_i w_i K_h(x_i, y): dK/dy = K g, dK/dlog h = K s, where
+//   Gaussian:    g = (x - y) / h^2,        s = r^2 / h^2
+//   exponential: g = (x - y) / (h r),      s = r / h      (g = 0 at r = 0)
+//   Laplacian:   g = sign(x - y) / h,      s = |x - y|_1 / h
+// Rows are regathered from the saved ids and recomputed, never stored.
+// Each lane group keeps its own copy of the d-vector (NV float4s per lane);
+// the groups are combined through shared-memory atomics at the end.
+// ---------------------------------------------------------------------------
+template <int G, int NV>
+__device__ void grad_rows(const float* __restrict__ X, int dp, const float* __restrict__ ys,
+                          const int* ids, int cnt, int kern, float h, float w,
+                          float4 (&gacc)[NV], float& est, float& sl) {
+  const int tid = threadIdx.x;
+  const int lig = tid & (G - 1);
+  constexpr int kGpw = 32 / G;
+  const int gw = (tid & 31) / G, warp = tid >> 5;
+  const int dp4 = dp >> 2;
+  const float4* y4 = reinterpret_cast<const float4*>(ys);
+  const float inv = kernel_inv(kern, h);
+  // warp-uniform trip count (group reductions need all lanes)
+  for (int wb = warp * kGpw; wb < cnt; wb += kNW * kGpw) {
+    const int r = wb + gw;
+    const bool valid = r < cnt;
+    const float4* row =
+        valid ? reinterpret_cast<const float4*>(X + (int64_t)ids[r] * dp) : nullptr;
+    float4 diff[NV];
+    float dist = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int j4 = lig + v * G;
+      if (valid && j4 < dp4) {
+        const float4 xv = __ldg(row + j4), yv = y4[j4];
+        diff[v] = make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
+      } else {
+        diff[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (kern == KDE_KERN_LAPLACIAN) {
+        dist += (fabsf(diff[v].x) + fabsf(diff[v].y)) + (fabsf(diff[v].z) + fabsf(diff[v].w));
+      } else {
+        dist = fmaf(diff[v].x, diff[v].x, dist);
+        dist = fmaf(diff[v].y, diff[v].y, dist);
+        dist = fmaf(diff[v].z, diff[v].z, dist);
+        dist = fmaf(diff[v].w, diff[v].w, dist);
+      }
+    }
+    dist = group_sum<G>(dist);
+    const float K = kernel_from_dist(kern, dist, inv);
+    float gs, s;  // per-component factor and d/dlog h factor
+    if (kern == KDE_KERN_GAUSSIAN) {
+      gs = 1.f / (h * h);
+      s = dist / (h * h);
+    } else if (kern == KDE_KERN_EXPONENTIAL) {
+      const float r = sqrtf(fmaxf(dist, 0.f));
+      gs = r > 0.f ? 1.f / (h * r) : 0.f;
+      s = r / h;
+    } else {
+      gs = 1.f / h;
+      s = dist / h;
+    }
+    const float wk = valid ? w * K : 0.f;
+    if (lig == 0) {
+      est += wk;
+      sl += wk * s;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (kern == KDE_KERN_LAPLACIAN) {
+        gacc[v].x += wk * gs * (diff[v].x > 0.f ? 1.f : (diff[v].x < 0.f ? -1.f : 0.f));
+        gacc[v].y += wk * gs * (diff[v].y > 0.f ? 1.f : (diff[v].y < 0.f ? -1.f : 0.f));
+        gacc[v].z += wk * gs * (diff[v].z > 0.f ? 1.f : (diff[v].z < 0.f ? -1.f : 0.f));
+        gacc[v].w += wk * gs * (diff[v].w > 0.f ? 1.f : (diff[v].w < 0.f ? -1.f : 0.f));
+      } else {
+        gacc[v].x = fmaf(wk * gs, diff[v].x, gacc[v].x);
+        gacc[v].y = fmaf(wk * gs, diff[v].y, gacc[v].y);
+        gacc[v].z = fmaf(wk * gs, diff[v].z, gacc[v].z);
+        gacc[v].w = fmaf(wk * gs, diff[v].w, gacc[v].w);
+      }
+    }
+  }
+}
+
+template <int G, int NV>
+__global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
+  __shared__ EstSmem sm;
+  __shared__ int tmp[kMaxK];
+  extern __shared__ float4 dyn4[];
+  float* ys = reinterpret_cast<float*>(dyn4);
+  float* gsum = ys + a.dp;
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  const uint64_t qid = a.qid_offset + (uint64_t)q;
+  for (int j = tid; j < a.dp; j += kNT) {
+    ys[j] = a.Y[q * a.dp + j];
+    gsum[j] = 0.f;
+  }
+  const int k = a.rs ? 0 : a.k;
+  if (k > 0) {
+    load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
+  } else {
+    if (tid == 0) {
+      sm.kk = 0;
+      sm.status = 0;
+    }
+    __syncthreads();
+  }
+  if (sm.status) {
+    if (tid == 0) {
+      atomicOr(a.err, KDE_ERRBIT_BADNBR);
+      if (a.out) a.out[q] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  const int kk = sm.kk;
+  const double nd = (double)a.n;
+  const bool sampled = !((int64_t)kk == a.n || a.m == 0);
+  float4 gacc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) gacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float est = 0.f, sl = 0.f;
+  const float w1 = a.rs ? 0.f : (float)(1.0 / nd);
+  if (kk > 0) grad_rows<G, NV>(a.X, a.dp, ys, sm.nb, kk, a.kern, a.h, w1, gacc, est, sl);
+  bool ok = true;
+  if (sampled) {
+    const float w2 = a.mode == 1 || a.rs ? (float)(1.0 / (double)a.m)
+                                         : (float)((nd - (double)kk) / (nd * (double)a.m));
+    const int64_t cap = a.mode == 1 ? (int64_t)a.m : 64 * (int64_t)a.m + 4096;
+    int64_t t0 = 0;
+    int got = 0;
+    while (got < a.m) {
+      const int room = min(kChunk, a.m - got);
+      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm)) {
+        ok = false;
+        break;
+      }
+      const int cnt = sm.cnt;
+      t0 = sm.tnext;
+      if (a.mode == 1) {
+        __syncthreads();
+        if (tid == 0) {
+          int w = 0;
+          for (int i = 0; i < cnt; ++i)
+            if (!is_member(sm.nb, kk, sm.S[i])) sm.S[w++] = sm.S[i];
+          sm.cnt = w;
+        }
+        __syncthreads();
+      }
+      grad_rows<G, NV>(a.X, a.dp, ys, sm.S, sm.cnt, a.kern, a.h, w2, gacc, est, sl);
+      got += cnt;
+      __syncthreads();
+    }
+  }
+  // combine the groups' d-vectors
+  const int lig = tid & (G - 1);
+  const int dp4 = a.dp >> 2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int j4 = lig + v * G;
+    if (j4 < dp4) {
+      atomicAdd(gsum + 4 * j4 + 0, gacc[v].x);
+      atomicAdd(gsum + 4 * j4 + 1, gacc[v].y);
+      atomicAdd(gsum + 4 * j4 + 2, gacc[v].z);
+      atomicAdd(gsum + 4 * j4 + 3, gacc[v].w);
+    }
+  }
+  const float est_t = block_sum(est, sm);
+  const float sl_t = block_sum(sl, sm);
+  __syncthreads();
+  const float go = a.gout ? a.gout[q] : 1.f;
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(a.err, KDE_ERRBIT_DRAWCAP);
+      if (a.out) a.out[q] = __int_as_float(0x7fc00000);
+      if (a.dlogh) a.dlogh[q] = __int_as_float(0x7fc00000);
+    }
+    for (int j = tid; j < a.d; j += kNT) a.dY[q * a.d + j] = __int_as_float(0x7fc00000);
+    return;
+  }
+  for (int j = tid; j < a.d; j += kNT) a.dY[q * a.d + j] = go * gsum[j];
+  if (tid == 0) {
+    if (a.out) a.out[q] = est_t;
+    if (a.dlogh) a.dlogh[q] = go * sl_t;
+  }
+}
+
+int group_lanes(int dp) {
+  const int dp4 = dp / 4;
+  if (dp4 <= 4) return 4;
+  if (dp4 <= 8) return 8;
+  if (dp4 <= 16) return 16;
+  return 32;
+}
+
+}  // namespace
+
+void launch_estimate(const SampleArgs& a, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  const size_t dyn = sizeof(float) * a.dp;
+  const unsigned grid = (unsigned)a.nq;
+  switch (group_lanes(a.dp)) {
+    case 4: k_estimate<4><<<grid, kNT, dyn, s>>>(a); break;
+    case 8: k_estimate<8><<<grid, kNT, dyn, s>>>(a); break;
+    case 16: k_estimate<16><<<grid, kNT, dyn, s>>>(a); break;
+    default: k_estimate<32><<<grid, kNT, dyn, s>>>(a); break;
+  }
+}
+
+void launch_estimate_grad(const SampleArgs& a, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  const size_t dyn = sizeof(float) * 2 * a.dp;
+  const unsigned grid = (unsigned)a.nq;
+  const int G = group_lanes(a.dp);
+  const int dp4 = a.dp / 4;
+  if (G < 32) {
+    switch (G) {
+      case 4: k_estimate_grad<4, 1><<<grid, kNT, dyn, s>>>(a); break;
+      case 8: k_estimate_grad<8, 1><<<grid, kNT, dyn, s>>>(a); break;
+      default: k_estimate_grad<16, 1><<<grid, kNT, dyn, s>>>(a); break;
+    }
+    return;
+  }
+  const int nv = (dp4 + 31) / 32;
+  if (nv <= 1) k_estimate_grad<32, 1><<<grid, kNT, dyn, s>>>(a);
+  else if (nv <= 2) k_estimate_grad<32, 2><<<grid, kNT, dyn, s>>>(a);
+  else if (nv <= 4) k_estimate_grad<32, 4><<<grid, kNT, dyn, s>>>(a);
+  else k_estimate_grad<32, 8><<<grid, kNT, dyn, s>>>(a);
+}
+
+}  // namespace deann

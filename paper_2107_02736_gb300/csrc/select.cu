@@ -1,0 +1,410 @@
+// Candidate selection for the IVF search (paper Section 4: the inverted file
+// scans the lists of the n_q nearest centroids and returns the k nearest
+// points).
+//
+//  * query norms |y|^2;
+//  * probe selection: the nprobe nearest centroids of each query;
+//  * the (query, probe) work plan that groups pairs by list for the
+//    list-major scan;
+//  * neighbour selection: from the approximate distances written by the scan,
+//    a block-wide radix select keeps the k' = k + margin smallest, those are
+//    rescored in difference form with compensated FP32 arithmetic, sorted by
+//    (distance, id) and the first k are returned, together with the exact
+//    neighbour contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1, line 4).
+//
+// The margin is certified per query: every unselected candidate has an
+// approximate distance >= T (the k'-th smallest) and an error bound E, so if
+// T - E exceeds the k-th rescored distance plus its own bound, no unselected
+// candidate can belong to the top k.  Queries that fail the test are counted
+// in the device error word.
+#include "common.cuh"
+
+namespace deann {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
+
+__global__ void k_query_norms(const float* __restrict__ Y, int64_t nq, int dp,
+                              float* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  float s = 0.f;
+  for (int j = lane; j < dp; j += 32) {
+    const float v = Y[q * dp + j];
+    s = fmaf(v, v, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) out[q] = s;
+}
+
+struct SelectSmem {
+  int hist[256];
+  int warp_a[kNW];
+  int warp_b[kNW];
+  int digit, before;
+  int slot[kSelectCap];
+  unsigned long long key[kSelectCap];
+};
+
+// Selects the K smallest of vals[0..cnt) (1 <= K <= min(cnt, kSelectCap)):
+// sm.slot[0..K) receives their indices (those strictly below the K-th key in
+// index order, then the lowest-index ties).  Returns the K-th key.
+__device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, int K,
+                                 SelectSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t prefix = 0, pmask = 0;
+  int want = K;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int i = tid; i < 256; i += kNT) sm.hist[i] = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < cnt; i += kNT) {
+      const uint32_t key = dist_key(vals[i]);
+      if ((key & pmask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 255], 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int c[8], s = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        c[b] = sm.hist[lane * 8 + b];
+        s += c[b];
+      }
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int excl = incl - s;
+      if (excl < want && want <= incl) {
+        int run = excl;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          if (run < want && want <= run + c[b]) {
+            sm.digit = lane * 8 + b;
+            sm.before = run;
+          }
+          run += c[b];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (uint32_t)sm.digit << shift;
+    pmask |= 255u << shift;
+    want -= sm.before;
+    __syncthreads();
+  }
+  // collect: keys < thr in index order, then the first `want` keys == thr
+  const uint32_t thr = prefix;
+  const int n_lt = K - want;
+  int base_lt = 0, base_eq = 0;
+  for (int64_t b0 = 0; b0 < cnt; b0 += kNT) {
+    const int64_t i = b0 + tid;
+    uint32_t key = 0xffffffffu;
+    if (i < cnt) key = dist_key(vals[i]);
+    const bool lt = i < cnt && key < thr;
+    const bool eq = i < cnt && key == thr;
+    const unsigned mlt = __ballot_sync(0xffffffffu, lt);
+    const unsigned meq = __ballot_sync(0xffffffffu, eq);
+    if (lane == 0) {
+      sm.warp_a[warp] = __popc(mlt);
+      sm.warp_b[warp] = __popc(meq);
+    }
+    __syncthreads();
+    int off_lt = base_lt, off_eq = base_eq, tot_lt = 0, tot_eq = 0;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) {
+        off_lt += sm.warp_a[w];
+        off_eq += sm.warp_b[w];
+      }
+      tot_lt += sm.warp_a[w];
+      tot_eq += sm.warp_b[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (lt) {
+      const int r = off_lt + __popc(mlt & below);
+      if (r < n_lt) sm.slot[r] = (int)i;
+    }
+    if (eq) {
+      const int r = off_eq + __popc(meq & below);
+      if (r < want) sm.slot[n_lt + r] = (int)i;
+    }
+    base_lt += tot_lt;
+    base_eq += tot_eq;
+    __syncthreads();
+  }
+  return thr;
+}
+
+// Bitonic sort of sm.key[0..cnt) ascending (cnt padded to a power of two
+// with all-ones keys).
+__device__ void block_sort_keys(SelectSmem& sm, int cnt) {
+  int P2 = 1;
+  while (P2 < cnt) P2 <<= 1;
+  for (int i = cnt + threadIdx.x; i < P2; i += kNT) sm.key[i] = ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= P2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P2 / 2; i += kNT) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const unsigned long long a = sm.key[lo], b = sm.key[hi];
+        if ((a > b) == up) {
+          sm.key[lo] = b;
+          sm.key[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long pack_key(float d2, int id) {
+  return ((unsigned long long)dist_key(d2) << 32) | (unsigned)id;
+}
+
+// --------------------------------------------------------------------------
+// Probe selection: nprobe nearest centroids (ties to the lower id).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__ D, int64_t nq,
+                                                       int L, const float* __restrict__ Y, int d,
+                                                       int dp, const float* __restrict__ C,
+                                                       int nprobe, int kprime,
+                                                       int32_t* __restrict__ probes) {
+  __shared__ SelectSmem sm;
+  const int64_t q = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* vals = D + q * L;
+  const int K = min(kprime, L);
+  if (K < L) {
+    block_select(vals, L, K, sm);
+  } else {
+    for (int i = threadIdx.x; i < L; i += kNT) sm.slot[i] = i;
+    __syncthreads();
+  }
+  const float* y = Y + q * dp;
+  for (int j = warp; j < K; j += kNW) {
+    const int c = sm.slot[j];
+    const float d2 = precise_sq_dist<32>(C + (int64_t)c * dp, y, d, lane);
+    if (lane == 0) sm.key[j] = pack_key(d2, c);
+  }
+  __syncthreads();
+  block_sort_keys(sm, K);
+  for (int j = threadIdx.x; j < nprobe; j += kNT)
+    probes[q * nprobe + j] = j < K ? (int32_t)(sm.key[j] & 0xffffffffu) : -1;
+}
+
+// --------------------------------------------------------------------------
+// Work plan of the list-major scan.
+// --------------------------------------------------------------------------
+__global__ void k_plan_segments(const int32_t* __restrict__ probes, int64_t nq, int P,
+                                const int64_t* __restrict__ list_off,
+                                int64_t* __restrict__ q_count, int64_t* __restrict__ seg_off,
+                                int64_t* __restrict__ list_cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  int64_t run = 0;
+  for (int p = 0; p < P; ++p) {
+    const int l = probes[q * P + p];
+    seg_off[q * P + p] = run;
+    if (l >= 0) {
+      run += list_off[l + 1] - list_off[l];
+      atomicAdd(reinterpret_cast<unsigned long long*>(list_cnt + l), 1ull);
+    }
+  }
+  q_count[q] = run;
+}
+
+__global__ void k_plan_fill(const int32_t* __restrict__ probes, int64_t nq, int P,
+                            const int64_t* __restrict__ q_off,
+                            const int64_t* __restrict__ seg_off,
+                            const int64_t* __restrict__ bucket_off,
+                            int64_t* __restrict__ bucket_fill, int32_t* __restrict__ pair_q,
+                            int64_t* __restrict__ pair_dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * P) return;
+  const int64_t q = i / P;
+  const int l = probes[i];
+  if (l < 0) return;
+  const int64_t slot =
+      bucket_off[l] +
+      (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(bucket_fill + l), 1ull);
+  pair_q[slot] = (int32_t)q;
+  pair_dst[slot] = q_off[q] + seg_off[i];
+}
+
+__global__ void k_plan_tiles(const int64_t* __restrict__ list_cnt, int L, int qtile,
+                             int64_t* __restrict__ tile_cnt) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < L) tile_cnt[l] = (list_cnt[l] + qtile - 1) / qtile;
+}
+
+// Single-block exclusive scan; out has count + 1 entries (the last = total).
+__global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restrict__ in,
+                                                         int64_t count,
+                                                         int64_t* __restrict__ out) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (count + 1023) / 1024;
+  const int64_t b = tid * per, e = min(count, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int64_t t = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += t;
+    __syncthreads();
+  }
+  int64_t run = part[tid] - s;
+  for (int64_t i = b; i < e; ++i) {
+    const int64_t v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (tid == 1023) out[count] = part[1023];
+}
+
+// --------------------------------------------------------------------------
+// Neighbour selection from the scan's candidate buffer.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
+  __shared__ SelectSmem sm;
+  __shared__ int64_t s_seg[kMaxProbe + 1];
+  __shared__ int64_t s_lstart[kMaxProbe];
+  __shared__ float s_red[kNW];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cnt = a.q_count[q];
+  const float* vals = a.cand + a.q_off[q];
+  const float* y = a.Y + q * a.dp;
+  for (int p = tid; p < a.P; p += kNT) {
+    const int l = a.probes[q * a.P + p];
+    s_seg[p] = a.seg_off[q * a.P + p];
+    s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
+  }
+  if (tid == 0) s_seg[a.P] = cnt;
+  __syncthreads();
+  const int K = (int)(cnt < (int64_t)a.kprime ? cnt : (int64_t)a.kprime);
+  uint32_t thr = 0;
+  if (K > 0 && K < cnt) {
+    thr = block_select(vals, cnt, K, sm);
+  } else {
+    for (int i = tid; i < K; i += kNT) sm.slot[i] = i;
+    __syncthreads();
+  }
+  // rescore in difference form (compensated FP32), one warp per candidate
+  for (int j = warp; j < K; j += kNW) {
+    const int s = sm.slot[j];
+    int lo = 0, hi = a.P - 1;  // last segment with start <= s
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    const int64_t pos = s_lstart[lo] + (s - s_seg[lo]);
+    const float d2 = precise_sq_dist<32>(a.XL + pos * a.dp, y, a.d, lane);
+    if (lane == 0) sm.key[j] = pack_key(d2, a.perm[pos]);
+  }
+  __syncthreads();
+  block_sort_keys(sm, K);
+  const int kk = min(a.k, K);
+  for (int j = tid; j < a.k; j += kNT) {
+    if (j < kk) {
+      a.nbr[q * a.k + j] = (int32_t)(sm.key[j] & 0xffffffffu);
+      if (a.nd2) a.nd2[q * a.k + j] = __uint_as_float((uint32_t)(sm.key[j] >> 32));
+    } else {
+      a.nbr[q * a.k + j] = -1;
+      if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
+    }
+  }
+  // margin certificate: |approx - exact| <= err_scale (|x|max + |y|)^2 for
+  // every candidate, so unselected ones are >= T - E in exact distance
+  if (tid == 0 && K < cnt && kk > 0) {
+    const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
+    const float T = __uint_as_float(thr);
+    const float r = a.xmax + sqrtf(a.Yn[q]);
+    const float E = a.err_scale * r * r;
+    if (!(T - E > dk * (1.0f + 1e-6f))) {
+      atomicOr(a.err, KDE_ERRBIT_MARGIN);
+      atomicAdd(a.err + 1, 1u);
+    }
+  }
+  // exact neighbour contribution s1 and k'
+  if (a.s1 != nullptr || a.kcount != nullptr) {
+    const float inv = kernel_inv(a.kern, a.h);
+    float part = 0.f;
+    if (a.kern == KDE_KERN_LAPLACIAN) {
+      // the IVF ranks by Euclidean distance; the Laplacian kernel needs L1
+      for (int j = warp; j < kk; j += kNW) {
+        const int64_t id = (int64_t)(sm.key[j] & 0xffffffffu);
+        const float l1 = precise_l1_dist<32>(a.X + id * a.dp, y, a.d, lane);
+        if (lane == 0) part += kernel_from_dist(a.kern, l1, inv);
+      }
+    } else {
+      for (int j = tid; j < kk; j += kNT)
+        part += kernel_from_dist(a.kern, __uint_as_float((uint32_t)(sm.key[j] >> 32)), inv);
+    }
+    part = warp_sum(part);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < kNW; ++w) t += s_red[w];
+      if (a.s1) a.s1[q] = t;
+      if (a.kcount) a.kcount[q] = kk;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStream_t s) {
+  if (nq <= 0) return;
+  k_query_norms<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Y, nq, dp, out);
+}
+
+void launch_exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, cudaStream_t s) {
+  k_exclusive_scan<<<1, 1024, 0, s>>>(in, count, out);
+}
+
+void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
+                          const float* C, int nprobe, int margin, int32_t* probes,
+                          cudaStream_t s) {
+  if (nq <= 0) return;
+  int kprime = nprobe + margin;
+  if (kprime > kSelectCap) kprime = kSelectCap;
+  k_select_probes<<<(unsigned)nq, kNT, 0, s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes);
+}
+
+void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
+                       int64_t* q_count, int64_t* q_off, int64_t* seg_off, int64_t* list_cnt,
+                       int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
+                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
+                       cudaStream_t s) {
+  cudaMemsetAsync(list_cnt, 0, sizeof(int64_t) * L, s);
+  cudaMemsetAsync(bucket_fill, 0, sizeof(int64_t) * L, s);
+  k_plan_segments<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(probes, nq, P, list_off, q_count,
+                                                              seg_off, list_cnt);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(q_count, nq, q_off);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(list_cnt, L, bucket_off);
+  const int64_t np = nq * P;
+  k_plan_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(probes, nq, P, q_off, seg_off,
+                                                           bucket_off, bucket_fill, pair_q,
+                                                           pair_dst);
+  k_plan_tiles<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(list_cnt, L, qtile, tile_cnt);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(tile_cnt, L, tile_off);
+}
+
+void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  k_select_neighbors<<<(unsigned)a.nq, kNT, 0, s>>>(a);
+}
+
+}  // namespace deann
