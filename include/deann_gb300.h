@@ -192,6 +192,24 @@ kde_status kde_stats(kde_index* index, int64_t* margin_failures, const kde_opts*
 kde_status kde_reserve(kde_index* index, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
                        const kde_opts* opts);
 
+/* kde_exact_noalloc -- kde_exact for callers that may not allocate device
+ * memory while they call (the paper has no counterpart; it is a deployment
+ * aid).  A cudaMalloc inside a call is not an option while a CUDA graph is
+ * being captured, when an application has reserved all device memory for its
+ * own allocator, or in loops that cannot afford an allocation's implicit
+ * synchronisation.  This variant allocates nothing: its FP64 accumulators live
+ * in a fixed array of 65,536 doubles (512 KiB) inside the library, present on
+ * every GPU that loads it for the life of the process.
+ *   Y, out  DEVICE pointers of the index's GPU, which must be current; Y is
+ *           nq x d with d a multiple of 4 and 16-byte aligned; out is nq.
+ *   nq      0 <= nq <= 65536; larger batches are rejected with KDE_EINVAL.
+ * Same result as kde_exact.  The first call on a device looks up the array's
+ * address (make it before any stream capture).  Calls share the array and
+ * clear it at their start, so calls that overlap on the GPU race: order them
+ * on one stream.  Asynchronous like every device-pointer call. */
+kde_status kde_exact_noalloc(kde_index* index, const float* Y, int64_t nq, float* out,
+                             const kde_opts* opts);
+
 /* Per-stage device timing of an index's calls.  Stages: 0 query staging
  * (padding, norms), 1 coarse quantiser (probe selection), 2 scan work plan,
  * 3 IVF list scan, 4 candidate selection and rescoring, 5 estimator (sample

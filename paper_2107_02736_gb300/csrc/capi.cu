@@ -420,6 +420,8 @@ kde_status finish_call(kde_index* ix, bool host, cudaStream_t st) {
 
 }  // namespace
 
+void deann::set_last_error(const char* msg) { g_err = msg; }
+
 // ============================================================================
 extern "C" {
 

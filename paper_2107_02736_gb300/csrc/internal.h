@@ -93,6 +93,9 @@ struct kde_index {
 
 namespace deann {
 
+// Sets the calling thread's kde_last_error() message (capi.cu).
+void set_last_error(const char* msg);
+
 // ---- build.cu -------------------------------------------------------------
 void launch_row_norms(const float* X, int64_t n, int dp, float* out, cudaStream_t s);
 void launch_pad_rows(const float* src, int64_t n, int d, float* dst, int dp, cudaStream_t s);
