@@ -7,10 +7,10 @@ test queries (90 % mixture, 10 % uniform in the bounding box), Gaussian
 kernel with h bisected so that the mean exact KDE of 1,000 validation queries
 is 1e-3 (+-1 %), IVF with 1,024 lists.  A step is one kde_query call over the
 10,000 test queries with inputs resident in HBM (the dataset, 512 MB, is
-larger than L2).  The schedule (k, m, nprobe) is the cheapest one whose mean
-relative error on the validation queries is <= 1e-2, starting from the
-paper-style default k = 100, m = 1,000, nprobe = 16; the test-set error of
-every timed step is reported.
+larger than L2).  For each scan precision (FP32 SIMT, BF16 tcgen05) the
+schedule (k, m, nprobe) is the cheapest one whose mean relative error on the
+validation queries is <= 1e-2; the headline is the faster of the two, and the
+test-set error of every timed step is reported.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (a bounded query sample per step).
@@ -26,7 +26,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -38,6 +37,7 @@ import workloads  # noqa: E402
 
 TARGET_ERR = 1e-2
 WORKLOAD = "mixture_embed n=1M d=128 nq=10k gaussian mean-KDE=1e-3 IVF nlist=1024"
+PRECISIONS = {"fp32": 0, "bf16": 1}
 
 
 def parse():
@@ -54,7 +54,7 @@ def parse():
 
 
 # --------------------------------------------------------------- helpers ----
-def dist_init(args):
+def dist_init():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -119,8 +119,7 @@ class ClockSampler:
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-        return p, "measured"
+            return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
@@ -133,17 +132,16 @@ def src_digest(name):
 
 
 def ncu_traffic(stage):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu summary,
-    if its source is unchanged since the capture; else None."""
+    """DRAM bytes per launch of a stage's kernel at this workload, from the
+    committed ncu summary, if the kernel's source is unchanged since the
+    capture; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except OSError:
         return None
     e = t.get(stage)
-    if not e:
-        return None
-    if e.get("src_sha") != src_digest(e["source"]):
+    if not e or e.get("src_sha") != src_digest(e["source"]):
         return None
     return e.get("bytes_per_launch_full")
 
@@ -184,29 +182,28 @@ def time_calls(fn, reps, torch):
     return s.elapsed_time(e) / reps
 
 
-def tune(index, Yv_d, exact_v, torch, default):
-    """Cheapest (k, m, nprobe) with validation mean rel. err <= 1e-2."""
-    k0, m0, p0 = default
-    cands = []
-    for k in (k0 // 2, k0, 2 * k0):
-        for m in (m0 // 2, m0, 2 * m0, 4 * m0):
-            for P in (p0 // 2, p0, 2 * p0):
-                cands.append((k, m, P))
+def tune(index, Yv_d, exact_v, torch, precision):
+    """Cheapest (k, m, nprobe) whose validation mean rel. err is <= 1e-2.  For
+    every (k, nprobe), m doubles until the target is met (more samples only
+    cost more)."""
     results = []
-    for (k, m, P) in cands:
-        est = index.query(Yv_d, k, m, nprobe=P, seed=12345)
-        err = rel_err(est.cpu().numpy(), exact_v)
-        ms = time_calls(lambda: index.query(Yv_d, k, m, nprobe=P, seed=1), 2, torch)
-        results.append(dict(k=k, m=m, nprobe=P, val_err=err, val_ms=ms))
+    for P in (8, 16, 32):
+        for k in (100, 200, 400, 800, 1024):
+            for m in (1000, 2000, 4000, 8000, 16000, 32000, 64000):
+                est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=precision)
+                err = rel_err(est.cpu().numpy(), exact_v)
+                ms = time_calls(lambda: index.query(Yv_d, k, m, nprobe=P, seed=1,
+                                                    precision=precision), 2, torch)
+                results.append(dict(k=k, m=m, nprobe=P, val_err=err, val_ms=ms))
+                if err <= TARGET_ERR:
+                    break
     ok = [r for r in results if r["val_err"] <= TARGET_ERR]
-    if ok:
-        best = min(ok, key=lambda r: r["val_ms"])
-    else:
-        best = min(results, key=lambda r: r["val_err"])
+    best = min(ok, key=lambda r: r["val_ms"]) if ok else min(results, key=lambda r: r["val_err"])
     return best, results
 
 
 def tune_rs(index, Yv_d, exact_v, ms_list):
+    err = None
     for m in ms_list:
         est = index.query_rs(Yv_d, m, seed=777)
         err = rel_err(est.cpu().numpy(), exact_v)
@@ -218,12 +215,10 @@ def tune_rs(index, Yv_d, exact_v, ms_list):
 # ------------------------------------------------------------ cpu oracle ----
 def oracle_sample_rate(X, Y, C, assign, kernel, h, k, m, nprobe, budget):
     """Oracle DEANN (IVF search from the exported index + Algorithm 1) on a
-    bounded sample of the test queries; returns (queries/s, cores, sample)."""
+    bounded sample of the test queries; returns (queries/s, cores, n, secs)."""
     import oracle
     oracle.build()
-    q = 8
-    spent = 0.0
-    done = 0
+    q, spent, done = 4, 0.0, 0
     while True:
         Ys = Y[done:done + q]
         t0 = time.perf_counter()
@@ -246,30 +241,19 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     X, Y, Yval = make_workload(args)
-    # the oracle needs an IVF to search: a seeded k-means stand-in is not
-    # available on the CPU side, so it searches the same inverted file the GPU
-    # library would build; without a GPU it falls back to brute force.
     spec = workloads.CONFIGS[2]
     k, m, P = spec["k"], spec["m"], spec["nprobe"]
-    h = 13.0
-    try:
-        import torch
-        import paper_2107_02736_gb300 as pkg
-        if torch.cuda.is_available():
-            index = pkg.KDEIndex(torch.from_numpy(X).cuda(), args.kernel, 1.0, nlist=1024)
-            h, _ = fit_bandwidth(index, torch.from_numpy(Yval).cuda(), 1e-3)
-            C, assign = index.export_ivf()
-            C, assign = C.numpy(), assign.numpy()
-            index.close()
-        else:
-            raise RuntimeError
-    except Exception:
-        C = X[:1].copy()
-        assign = np.zeros(X.shape[0], np.int32)
-        P = 1
+    # The oracle searches an inverted file exported by the GPU library (its
+    # k-means is not part of the oracle); bandwidth as in the GPU arm.
+    import torch
+    import paper_2107_02736_gb300 as pkg
+    index = pkg.KDEIndex(torch.from_numpy(X).cuda(), args.kernel, 1.0, nlist=spec["nlist"], seed=1)
+    h, _ = fit_bandwidth(index, torch.from_numpy(Yval).cuda(), spec["target_mu"])
+    C, assign = index.export_ivf()
+    C, assign = C.numpy(), assign.numpy()
+    index.close()
     per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
-    rates = []
-    sample = 0
+    rates, sample = [], 0
     for step in range(args.warmup + args.steps):
         qps, cores, done, spent = oracle_sample_rate(X, Y, C, assign, args.kernel, h, k, m, P,
                                                      per_step)
@@ -278,22 +262,50 @@ def run_reference(args, rank, world):
             sample = done
     value = statistics.mean(rates)
     line = {
-        "impl": "reference", "metric": "kde_queries_per_s", "value": value, "unit": "queries/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "impl": "reference", "metric": "kde_queries_per_s_at_1e-2_mean_rel_err", "value": value,
+        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * Y.shape[0] / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "k": k, "m": m, "nprobe": P, "h": h},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} test queries per step (IVF search + DEANN, FP64)"},
+                         "sample": f"{sample} test queries per step (IVF search from the "
+                                   f"exported index + DEANN, FP64)"},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def roofline(stage, prof, calls, nq, n, d, nlist, k, m, P, peaks, peak_kind):
+    """Achieved vs peak for one stage of the query path, from its algorithmic
+    bytes or flops per call and its measured device time per call."""
+    ms = prof[stage]["ms"] / calls
+    cbar = P * n / nlist
+    if stage == "estimate":
+        # m sampled FP32 rows (plus the query, the neighbour ids and the output)
+        work = nq * (m * d * 4 + d * 4 + k * 4 + 4)
+        r = {"bound": "hbm", "achieved": work / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+             "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
+    elif stage == "scan":
+        work = 2.0 * nq * cbar * d
+        r = {"bound": "tensor", "achieved": work / (ms / 1e3) / 1e12,
+             "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+             "peak_source": f"{peak_kind} bf16_tflops (burst)"}
+    else:
+        # candidate values written by the scan, read by the selection
+        work = nq * cbar * 4
+        r = {"bound": "hbm", "achieved": work / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+             "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["traffic"] = ncu_traffic(stage)
+    r["stage"] = stage
+    r["ms_per_call"] = ms
+    return r
+
+
 def main():
     args = parse()
-    rank, world, local = dist_init(args)
+    rank, world, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -321,17 +333,33 @@ def main():
     exact_v = index.exact(Yv_d).cpu().numpy()
     exact_t = index.exact(Yd).cpu().numpy()
 
-    default = (spec["k"], spec["m"], spec["nprobe"])
-    if args.no_tune:
-        sched = dict(k=default[0], m=default[1], nprobe=default[2])
-        tuned = []
-    else:
-        sched, tuned = tune(index, Yv_d, exact_v, torch, default)
-    k, m, P = sched["k"], sched["m"], sched["nprobe"]
+    # ---- schedule per precision, on the validation queries ------------------
+    sched, tuned = {}, {}
+    for name, prec in PRECISIONS.items():
+        if args.no_tune:
+            sched[name] = dict(k=spec["k"], m=spec["m"], nprobe=spec["nprobe"], val_ms=0.0,
+                               val_err=None)
+            tuned[name] = []
+        else:
+            sched[name], tuned[name] = tune(index, Yv_d, exact_v, torch, prec)
+    variants = {}
+    for name, prec in PRECISIONS.items():
+        s = sched[name]
+        ms = time_calls(lambda: index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=5,
+                                            precision=prec), 3, torch)
+        err = rel_err(index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=6,
+                                  precision=prec).cpu().numpy(), exact_t)
+        variants[name] = dict(k=s["k"], m=s["m"], nprobe=s["nprobe"], qps=nq / (ms / 1e3),
+                              test_rel_err=err, val_rel_err=s["val_err"])
+    ok = [v for v in variants if variants[v]["val_rel_err"] is not None
+          and variants[v]["val_rel_err"] <= TARGET_ERR]
+    head = max(ok or variants, key=lambda v: variants[v]["qps"])
+    prec = PRECISIONS[head]
+    k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
 
     # ---- timed region: device-resident inputs -------------------------------
     for w in range(args.warmup):
-        index.query(Yd, k, m, nprobe=P, seed=1000 + w)
+        index.query(Yd, k, m, nprobe=P, seed=1000 + w, precision=prec)
     torch.cuda.synchronize()
     index.profile_read(reset=True)
     index.profile(True)
@@ -344,7 +372,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for s in range(args.steps):
-        outs.append(index.query(Yd, k, m, nprobe=P, seed=s))
+        outs.append(index.query(Yd, k, m, nprobe=P, seed=s, precision=prec))
     ev1.record()
     torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
@@ -363,11 +391,11 @@ def main():
     # ---- end to end through the host-pointer API ----------------------------
     Yh = torch.from_numpy(Y).pin_memory()
     for w in range(2):
-        index.query(Yh, k, m, nprobe=P, seed=2000 + w)
+        index.query(Yh, k, m, nprobe=P, seed=2000 + w, precision=prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        out_h = index.query(Yh, k, m, nprobe=P, seed=s)
+        out_h = index.query(Yh, k, m, nprobe=P, seed=s, precision=prec)
         _ = float(out_h[0])
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(nq * d * 4),
@@ -375,34 +403,18 @@ def main():
 
     # ---- baselines on the same GPU -----------------------------------------
     ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
-    rs_m, rs_val_err = tune_rs(index, Yv_d, exact_v, [m, 4 * m, 16 * m, 64 * m])
-    ms_rs = time_calls(lambda: index.query_rs(Yd, rs_m, seed=3), 3, torch)
+    rs_m, _ = tune_rs(index, Yv_d, exact_v, [4000, 16000, 64000, 256000, 1024000])
+    ms_rs = time_calls(lambda: index.query_rs(Yd, rs_m, seed=3), 2, torch)
     rs_err = rel_err(index.query_rs(Yd, rs_m, seed=4).cpu().numpy(), exact_t)
 
     # ---- roofline of the dominant stage ------------------------------------
     peaks, peak_kind = load_peaks()
-    stage_ms = {s: v["ms"] / max(1, v["timed"]) for s, v in prof.items() if v["timed"]}
-    dom = max(stage_ms, key=stage_ms.get)
+    stages = {s: v["ms"] / args.steps for s, v in prof.items() if v["timed"]}
+    dom = max(stages, key=stages.get)
+    roof = roofline(dom, prof, args.steps, nq, n, d, spec["nlist"], k, m, P, peaks, peak_kind)
+    others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, P, peaks,
+                          peak_kind) for s in ("scan", "estimate", "select") if s in stages}
     launches = sum(v["launches"] for v in prof.values())
-    dom_ms = stage_ms[dom]
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    if dom == "estimate":
-        algo = nq * (m * d * 4 + d * 4 + k * 4 + 8)
-        roof = {"bound": "hbm", "achieved": algo / (dom_ms / 1e3) / 1e9,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    else:
-        # SIMT FP32 distance tiles: 2 d flops per (query, candidate)
-        cbar = P * n / spec["nlist"]
-        algo = {"scan": 2.0 * nq * cbar * d, "select": 2.0 * nq * (k + k // 4 + 16) * d,
-                "coarse": 2.0 * nq * spec["nlist"] * d}.get(dom, 0.0)
-        roof = {"bound": "alu", "achieved": algo / (dom_ms / 1e3) / 1e12,
-                "peak": fp32_peak_tflops, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = ncu_traffic(dom)
-    roof["kernel_stage"] = dom
-    roof["peak_source"] = peak_kind if roof["bound"] == "hbm" else \
-        "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
 
     cpu = None
     if rank == 0 and world == 1:
@@ -420,12 +432,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "d": d, "nq": nq, "kernel": args.kernel,
                    "h": h, "val_mean_kde": mu_val, "nlist": spec["nlist"], "k": k, "m": m,
-                   "nprobe": P, "precision": "fp32", "parallelism": f"replicas x{world}",
+                   "nprobe": P, "scan_precision": head, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (X is 512 MB)"},
         "mean_rel_err": statistics.mean(errs), "max_step_rel_err": max(errs),
         "meets_target": max(errs) <= TARGET_ERR,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
-        "stages_ms": stage_ms, "cpu_baseline": cpu, "build_s": build_s,
+        "stage_ms_per_step": stages, "stage_rooflines": others, "cpu_baseline": cpu,
+        "build_s": build_s, "variants": variants,
         "baselines": {"exact_qps": nq / (ms_exact / 1e3), "rs_qps": nq / (ms_rs / 1e3),
                       "rs_m": rs_m, "rs_rel_err": rs_err},
         "margin_failures": index.margin_failures(),

@@ -237,6 +237,41 @@ __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int dp,
   }
 }
 
+// BF16 copy of the list-ordered rows centred on their list's centroid,
+// x~ = x - c_l, with FP32 squared norms |x~|^2 and the list radius
+// max |x~| (one block per list, one warp per row).
+__global__ void k_center_bf16(const float* __restrict__ XL, int dp,
+                              const int64_t* __restrict__ list_off, const float* __restrict__ C,
+                              __nv_bfloat16* __restrict__ dst, int dpb, float* __restrict__ xcn,
+                              float* __restrict__ rad) {
+  const int l = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t b = list_off[l], e = list_off[l + 1];
+  const float* c = C + (int64_t)l * dp;
+  float rmax = 0.f;
+  for (int64_t r = b + warp; r < e; r += nw) {
+    float s = 0.f;
+    for (int j = lane; j < dpb; j += 32) {
+      const float v = j < dp ? XL[r * dp + j] - c[j] : 0.f;
+      dst[r * dpb + j] = __float2bfloat16_rn(v);
+      s = fmaf(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      xcn[r] = s;
+      rmax = fmaxf(rmax, sqrtf(s));
+    }
+  }
+  __shared__ float red[32];
+  if (lane == 0) red[warp] = rmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, red[w]);
+    rad[l] = m;
+  }
+}
+
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -307,6 +342,12 @@ void launch_gather_f32(const float* v, const int32_t* ids, int64_t count, float*
 void launch_to_bf16(const float* X, int64_t n, int dp, void* dst, int dpb, cudaStream_t s) {
   k_to_bf16<<<grid_for(n * dpb, 256), 256, 0, s>>>(X, n, dp,
                                                    reinterpret_cast<__nv_bfloat16*>(dst), dpb);
+}
+
+void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L, const float* C,
+                        void* dst, int dpb, float* xcn, float* rad, cudaStream_t s) {
+  k_center_bf16<<<(unsigned)L, 256, 0, s>>>(XL, dp, list_off, C,
+                                            reinterpret_cast<__nv_bfloat16*>(dst), dpb, xcn, rad);
 }
 
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s) {

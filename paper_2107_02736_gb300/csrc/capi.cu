@@ -162,8 +162,10 @@ int select_margin(int k, int precision) { return precision == 0 ? k / 4 + 16 : k
 float scan_err_scale(int dp, int precision) {
   const float u = 1.0f / 16777216.0f;  // 2^-24
   if (precision == 0) return 2.0f * ((float)dp / 32.0f + 40.0f) * u;
-  // BF16 operands: each rounded to 8 significant bits
-  return 2.0f * (1.0f / 128.0f + ((float)dp / 32.0f + 40.0f) * u);
+  // BF16 operands, each rounded to nearest with 8 significant bits: the dot
+  // product is off by at most 2^-8 |x||y| <= 2^-10 (|x| + |y|)^2, twice that
+  // in D^2, plus the FP32 accumulation and norm terms
+  return 1.0f / 512.0f + 2.0f * ((float)dp / 32.0f + 40.0f) * u;
 }
 
 // ---- query scratch ---------------------------------------------------------
@@ -171,6 +173,7 @@ struct SearchBufs {
   int64_t qc = 0;  // queries per chunk
   float* D = nullptr;
   int32_t* probes = nullptr;
+  float* probe_d2 = nullptr;  // |y - c_probe|^2, rescored
   int64_t *q_count = nullptr, *q_off = nullptr, *seg_off = nullptr;
   int64_t *list_cnt = nullptr, *bucket_off = nullptr, *bucket_fill = nullptr;
   int64_t *tile_cnt = nullptr, *tile_off = nullptr;
@@ -187,8 +190,9 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
   qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
   s.qc = qc;
-  if (L > 1) s.D = b.take<float>((size_t)qc * L);
+  s.D = b.take<float>((size_t)qc * L);
   s.probes = b.take<int32_t>((size_t)qc * P);
+  s.probe_d2 = b.take<float>((size_t)qc * P);
   s.q_count = b.take<int64_t>(qc);
   s.q_off = b.take<int64_t>(qc + 1);
   s.seg_off = b.take<int64_t>((size_t)qc * P);
@@ -285,28 +289,36 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     const float* Yc = cb.Yp + q0 * ix->dp;
     const float* Ync = cb.Yn + q0;
     {
-      StageTimer t(ix, ST_COARSE, st, L > 1 ? 2 : 1);
-      if (L > 1) {
-        launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, st);
-        launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
-                             s.probes, st);
-      } else {
-        launch_fill_i32(s.probes, nc * P, 0, st);
-      }
+      // with one list the probe is list 0; the step still yields |y - c_0|^2
+      StageTimer t(ix, ST_COARSE, st, 2);
+      launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, st);
+      launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
+                           s.probes, s.probe_d2, st);
     }
+    // the BF16 tensor-core scan groups up to BN queries per list; the FP32
+    // SIMT scan groups 64
+    const bool tcore = precision == KDE_PREC_BF16;
+    if (tcore && !ix->tmap_ok)
+      return fail(KDE_ECUDA, "the BF16 tensor map could not be encoded on this driver");
+    const int qtile = tcore ? scan_tc_bn(ix->dpb) : kTile;
     {
       StageTimer t(ix, ST_PLAN, st, 6);
       launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
-                        s.tile_cnt, s.tile_off, kTile, st);
+                        s.tile_cnt, s.tile_off, qtile, st);
     }
     ScanPlan plan;
     plan.pair_q = s.pair_q;
     plan.pair_dst = s.pair_dst;
     plan.bucket_off = s.bucket_off;
     plan.tile_off = s.tile_off;
-    plan.max_tiles = (nc * P + kTile - 1) / kTile + L;
-    {
+    plan.max_tiles = (nc * P + qtile - 1) / qtile + L;
+    if (tcore) {
+      StageTimer t(ix, ST_SCAN, st, 1);
+      if (!launch_scan_tc(ix->tmap_xlb, Yc, ix->C, ix->dp, ix->XLcn, ix->list_off, L, ix->dpb,
+                          qtile, plan, s.cand, ix->err, st))
+        return fail(KDE_ECUDA, "could not configure the tensor-core scan kernel");
+    } else {
       StageTimer t(ix, ST_SCAN, st, 1);
       launch_scan_simt(Yc, Ync, ix->XL, ix->XLn, ix->list_off, L, ix->dp, plan, s.cand, st);
     }
@@ -338,6 +350,9 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.nd2 = nd2 ? nd2 + q0 * k : nullptr;
     a.s1 = s1 ? s1 + q0 : nullptr;
     a.kcount = nullptr;
+    a.probe_d2 = s.probe_d2;
+    a.rad = ix->rad;
+    a.centered = tcore ? 1 : 0;
     a.err = ix->err;
     launch_select_neighbors(a, st);
   }
@@ -498,6 +513,8 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   BTRY(dev_alloc(&ix->list_off, (size_t)L + 1));
   BTRY(dev_alloc(&ix->C, (size_t)L * ix->dp));
   BTRY(dev_alloc(&ix->Cn, (size_t)L));
+  BTRY(dev_alloc(&ix->XLcn, (size_t)n));
+  BTRY(dev_alloc(&ix->rad, (size_t)L));
   BTRY(dev_alloc(&ix->err, 4));
   BTRY(dev_alloc(&ix->xmax_d, 1));
   {
@@ -560,7 +577,9 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   launch_row_norms(ix->C, L, ix->dp, ix->Cn, st);
   launch_gather_rows(ix->X, ix->dp, ix->perm, n, ix->XL, st);
   launch_gather_f32(ix->Xn, ix->perm, n, ix->XLn, st);
-  launch_to_bf16(ix->XL, n, ix->dp, ix->XLb, ix->dpb, st);
+  launch_center_bf16(ix->XL, ix->dp, ix->list_off, (int)L, ix->C, ix->XLb, ix->dpb, ix->XLcn,
+                     ix->rad, st);
+  ix->tmap_ok = make_bf16_row_map(ix->tmap_xlb, ix->XLb, n, ix->dpb);
   BCK(cudaGetLastError());
 
   ix->h_list_off = new int64_t[L + 1];
@@ -597,6 +616,8 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->list_off);
   cudaFree(ix->C);
   cudaFree(ix->Cn);
+  cudaFree(ix->XLcn);
+  cudaFree(ix->rad);
   cudaFree(ix->err);
   cudaFree(ix->xmax_d);
   if (ix->scratch.base) cudaFree(ix->scratch.base);

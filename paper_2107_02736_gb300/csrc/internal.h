@@ -65,7 +65,9 @@ struct kde_index {
   // dataset, IVF list order (list-contiguous): FP32, BF16 and norms
   float* XL = nullptr;
   float* XLn = nullptr;
-  void* XLb = nullptr;        // __nv_bfloat16 [n x dpb]
+  void* XLb = nullptr;        // __nv_bfloat16 [n x dpb], rows centred on their centroid
+  float* XLcn = nullptr;      // |x - c_list|^2 of each list-ordered row (FP32)
+  float* rad = nullptr;       // [nlist] max |x - c_list| over the list
   int32_t* perm = nullptr;    // list position -> original id
   int32_t* assign = nullptr;  // original id -> list id
   int64_t* list_off = nullptr;  // [nlist + 1] device
@@ -73,6 +75,10 @@ struct kde_index {
   int64_t max_list = 0;
   float* C = nullptr;         // centroids [nlist x dp]
   float* Cn = nullptr;
+  // TMA descriptor (CUtensorMap, 128 bytes) of XLb: 64 x 128 BF16 boxes,
+  // 128-byte swizzle
+  alignas(64) unsigned char tmap_xlb[128] = {0};
+  bool tmap_ok = false;
   uint32_t* err = nullptr;    // device error words [4]
   float* xmax_d = nullptr;    // device max |x|^2
   float xmax = 0.f;           // max |x| over the dataset
@@ -115,6 +121,8 @@ void launch_gather_rows(const float* X, int dp, const int32_t* ids, int64_t coun
 void launch_gather_f32(const float* v, const int32_t* ids, int64_t count, float* dst,
                        cudaStream_t s);
 void launch_to_bf16(const float* X, int64_t n, int dp, void* dst, int dpb, cudaStream_t s);
+void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L, const float* C,
+                        void* dst, int dpb, float* xcn, float* rad, cudaStream_t s);
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s);
 
 // ---- tiles.cu (SIMT distance tiles) ---------------------------------------
@@ -136,11 +144,18 @@ void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const fl
                       const int64_t* list_off, int L, int dp, const ScanPlan& plan, float* cand,
                       cudaStream_t s);
 
+// ---- tc_scan.cu (tcgen05 BF16 scan) ----------------------------------------
+int scan_tc_bn(int dpb);                    // queries per CTA for a given row width
+bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb);
+bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, const float* XLcn,
+                    const int64_t* list_off, int L, int dpb, int BN, const ScanPlan& plan,
+                    float* cand, uint32_t* err, cudaStream_t s);
+
 // ---- select.cu -------------------------------------------------------------
 void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStream_t s);
 void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
                           const float* C, int nprobe, int margin, int32_t* probes,
-                          cudaStream_t s);
+                          float* probe_d2, cudaStream_t s);
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
                        int64_t* q_count, int64_t* q_off, int64_t* seg_off, int64_t* list_cnt,
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
@@ -171,6 +186,10 @@ struct SelectArgs {
   float* nd2;                // [nq x k] precise squared distances (nullable)
   float* s1;                 // [nq] sum of kernel values over the k' neighbours (nullable)
   int32_t* kcount;           // [nq] k' (nullable)
+  // centred scan (BF16): the error bound uses |y - c_probe| and list radii
+  const float* probe_d2;     // [nq x P]
+  const float* rad;          // [nlist]
+  int centered;
   uint32_t* err;
 };
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s);

@@ -53,7 +53,7 @@ struct SelectSmem {
 // sm.slot[0..K) receives their indices (those strictly below the K-th key in
 // index order, then the lowest-index ties).  Returns the K-th key.
 __device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, int K,
-                                 SelectSmem& sm) {
+                                 SelectSmem& sm, bool collect = true) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t prefix = 0, pmask = 0;
   int want = K;
@@ -98,6 +98,7 @@ __device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, in
     want -= sm.before;
     __syncthreads();
   }
+  if (!collect) return prefix;
   // collect: keys < thr in index order, then the first `want` keys == thr
   const uint32_t thr = prefix;
   const int n_lt = K - want;
@@ -141,6 +142,35 @@ __device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, in
   return thr;
 }
 
+// Collects, in index order, the indices of all keys <= thr into
+// sm.slot[0..cap).  Returns the total count, which may exceed cap (then the
+// slots hold only the first cap).
+__device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uint32_t thr, int cap,
+                                SelectSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int base = 0;
+  for (int64_t b0 = 0; b0 < cnt; b0 += kNT) {
+    const int64_t i = b0 + tid;
+    const bool take = i < cnt && dist_key(vals[i]) <= thr;
+    const unsigned mt = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) sm.warp_a[warp] = __popc(mt);
+    __syncthreads();
+    int off = base, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) off += sm.warp_a[w];
+      tot += sm.warp_a[w];
+    }
+    if (take) {
+      const int r = off + __popc(mt & ((1u << lane) - 1u));
+      if (r < cap) sm.slot[r] = (int)i;
+    }
+    base += tot;
+    __syncthreads();
+  }
+  return base;
+}
+
 // Bitonic sort of sm.key[0..cnt) ascending (cnt padded to a power of two
 // with all-ones keys).
 __device__ void block_sort_keys(SelectSmem& sm, int cnt) {
@@ -176,7 +206,8 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
                                                        int L, const float* __restrict__ Y, int d,
                                                        int dp, const float* __restrict__ C,
                                                        int nprobe, int kprime,
-                                                       int32_t* __restrict__ probes) {
+                                                       int32_t* __restrict__ probes,
+                                                       float* __restrict__ probe_d2) {
   __shared__ SelectSmem sm;
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -196,8 +227,11 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
   }
   __syncthreads();
   block_sort_keys(sm, K);
-  for (int j = threadIdx.x; j < nprobe; j += kNT)
+  for (int j = threadIdx.x; j < nprobe; j += kNT) {
     probes[q * nprobe + j] = j < K ? (int32_t)(sm.key[j] & 0xffffffffu) : -1;
+    probe_d2[q * nprobe + j] =
+        j < K ? __uint_as_float((uint32_t)(sm.key[j] >> 32)) : __int_as_float(0x7f800000);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -290,15 +324,46 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     s_seg[p] = a.seg_off[q * a.P + p];
     s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
   }
-  if (tid == 0) s_seg[a.P] = cnt;
+  // Error bound E of the scan's distances for this query: |approx - exact|
+  // <= err_scale r^2 with r = |x| + |y| (|x| <= the dataset's largest norm),
+  // or, for the centred scan, r = |x~| + |y~| <= list radius + |y - c_probe|.
+  __shared__ float s_E;
+  if (tid == 0) {
+    s_seg[a.P] = cnt;
+    float r = a.xmax + sqrtf(a.Yn[q]);
+    if (a.centered) {
+      r = 0.f;
+      for (int p = 0; p < a.P; ++p) {
+        const int l = a.probes[q * a.P + p];
+        if (l >= 0) r = fmaxf(r, sqrtf(a.probe_d2[q * a.P + p]) + a.rad[l]);
+      }
+    }
+    s_E = a.err_scale * r * r;
+  }
   __syncthreads();
-  const int K = (int)(cnt < (int64_t)a.kprime ? cnt : (int64_t)a.kprime);
-  uint32_t thr = 0;
-  if (K > 0 && K < cnt) {
-    thr = block_select(vals, cnt, K, sm);
-  } else {
+  // Candidates to rescore: every one whose approximate distance is within 2E
+  // of the k-th smallest approximate distance t_k.  The true k-th distance is
+  // at most t_k + E, and a point of the true top k has an approximate
+  // distance at most (t_k + E) + E, so this set always contains the exact
+  // top k.  Beyond kSelectCap candidates the kSelectCap smallest are kept and
+  // the query is counted as uncertified.
+  int K;
+  if (cnt <= (int64_t)a.k) {
+    K = (int)cnt;
     for (int i = tid; i < K; i += kNT) sm.slot[i] = i;
     __syncthreads();
+  } else {
+    const uint32_t tk = block_select(vals, cnt, a.k, sm, false);
+    const uint32_t thr = dist_key(__uint_as_float(tk) + 2.f * s_E);
+    K = block_collect_le(vals, cnt, thr, kSelectCap, sm);
+    if (K > kSelectCap) {
+      block_select(vals, cnt, kSelectCap, sm);
+      K = kSelectCap;
+      if (tid == 0) {
+        atomicOr(a.err, KDE_ERRBIT_MARGIN);
+        atomicAdd(a.err + 1, 1u);
+      }
+    }
   }
   // rescore in difference form (compensated FP32), one warp per candidate
   for (int j = warp; j < K; j += kNW) {
@@ -322,18 +387,6 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     } else {
       a.nbr[q * a.k + j] = -1;
       if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
-    }
-  }
-  // margin certificate: |approx - exact| <= err_scale (|x|max + |y|)^2 for
-  // every candidate, so unselected ones are >= T - E in exact distance
-  if (tid == 0 && K < cnt && kk > 0) {
-    const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
-    const float T = __uint_as_float(thr);
-    const float r = a.xmax + sqrtf(a.Yn[q]);
-    const float E = a.err_scale * r * r;
-    if (!(T - E > dk * (1.0f + 1e-6f))) {
-      atomicOr(a.err, KDE_ERRBIT_MARGIN);
-      atomicAdd(a.err + 1, 1u);
     }
   }
   // exact neighbour contribution s1 and k'
@@ -376,11 +429,12 @@ void launch_exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, c
 
 void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
                           const float* C, int nprobe, int margin, int32_t* probes,
-                          cudaStream_t s) {
+                          float* probe_d2, cudaStream_t s) {
   if (nq <= 0) return;
   int kprime = nprobe + margin;
   if (kprime > kSelectCap) kprime = kSelectCap;
-  k_select_probes<<<(unsigned)nq, kNT, 0, s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes);
+  k_select_probes<<<(unsigned)nq, kNT, 0, s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
+                                               probe_d2);
 }
 
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,

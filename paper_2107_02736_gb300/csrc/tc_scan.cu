@@ -1,0 +1,314 @@
+// IVF list scan on the 5th-generation tensor cores (tcgen05), BF16 operands,
+// FP32 accumulation in TMEM.
+//
+// Squared distances by the identity |x - y|^2 = |x|^2 + |y|^2 - 2 <x, y>
+// (paper Appendix D, Eq. "d2"): the inner products of one IVF list's points
+// with the queries that probe that list form one GEMM, D = X_list Y^T.
+//
+// One CTA = one (list, group of up to BN probing queries).  Roles:
+//   warp 0 (one lane): TMA producer, streams 128-point x 64-dim BF16 tiles of
+//                      the list (128-byte swizzle) through a 4-stage ring;
+//   warp 1 (one lane): MMA issuer, tcgen05.mma M=128 (points) x N=BN
+//                      (queries) x K=16 into a double-buffered TMEM
+//                      accumulator; warp 1 also owns the TMEM allocation;
+//   warps 2-5        : epilogue, one TMEM lane (= one list point) per thread:
+//                      D^2 = |x|^2 + |y|^2 - 2 acc, clamped at 0, written to
+//                      each query's candidate segment (coalesced along points).
+// Both operands are centred on the list's centroid c_l (x~ = x - c_l, stored
+// that way at build time; y~ = y - c_l, formed here), which leaves the
+// distances unchanged but shrinks the magnitudes that the BF16 rounding error
+// scales with from |x||y| to |x~||y~|.  The centred queries (B operand) are
+// staged once per CTA by all threads into the swizzled layout and stay
+// resident for the whole list.
+// The approximate distances only rank candidates: the selection kernel
+// rescores the best k + margin in FP32 difference form.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace deann {
+
+namespace {
+
+constexpr int kBM = 128;          // points per tile (MMA M)
+constexpr int kBK = 64;           // BF16 elements per 128-byte row chunk
+constexpr int kStages = 4;
+constexpr int kStageBytes = kBM * 128;
+constexpr int kThreads = 192;
+
+struct ScanShared {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+  int list;
+  int64_t dst[256];
+  float yn[256];
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_scan_tc(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ Yp,
+              const float* __restrict__ C, int dp, const float* __restrict__ XLcn,
+              const int64_t* __restrict__ list_off, int L, int dpb, int BN,
+              const int32_t* __restrict__ pair_q, const int64_t* __restrict__ pair_dst,
+              const int64_t* __restrict__ bucket_off, const int64_t* __restrict__ tile_off,
+              float* __restrict__ cand, uint32_t* __restrict__ err) {
+  __shared__ ScanShared sh;
+  extern __shared__ uint8_t dyn_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t t = blockIdx.x;
+  if (t >= tile_off[L]) return;
+
+  // 1024-byte aligned operand area: A ring, then the resident B block
+  const uint32_t raw = tc::smem_u32(dyn_raw);
+  uint8_t* base = dyn_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t* A = base;
+  uint8_t* B = base + kStages * kStageBytes;
+  const int KB = dpb / kBK;
+
+  if (tid == 0) {
+    int lo = 0, hi = L - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    sh.list = lo;
+    sh.abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&sh.full[s], 1);
+      tc::mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&sh.tfull[b], 1);
+      tc::mbar_init(&sh.tempty[b], 4);
+    }
+    tc::mbar_init(&sh.drain, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const int l = sh.list;
+  const int64_t pb = bucket_off[l] + (t - tile_off[l]) * BN;
+  const int64_t left_pairs = bucket_off[l + 1] - pb;
+  const int npairs = left_pairs < (int64_t)BN ? (int)left_pairs : BN;
+  const int64_t xb = list_off[l];
+  const int64_t len = list_off[l + 1] - xb;
+  const int ntiles = (int)((len + kBM - 1) / kBM);
+
+  // stage the queries centred on this list's centroid, y~ = y - c_l, in BF16:
+  // row r of block kb at B + kb*BN*128 + r*128, 16-byte chunk c stored at
+  // chunk position c ^ (r & 7) (the 128-byte swizzle)
+  const float* cl = C + (int64_t)l * dp;
+  const int chunks = BN * KB * 8;
+  for (int i = tid; i < chunks; i += kThreads) {
+    const int r = i / (KB * 8);
+    const int rem = i - r * (KB * 8);
+    const int kb = rem >> 3, c = rem & 7;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (r < npairs) {
+      const float* yq = Yp + (int64_t)pair_q[pb + r] * dp;
+      const int j0 = kb * kBK + c * 8;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + 2 * u;
+        const float f0 = j < dp ? yq[j] - cl[j] : 0.f;
+        const float f1 = j + 1 < dp ? yq[j + 1] - cl[j + 1] : 0.f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f0, f1);
+        w[u] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+    }
+    *reinterpret_cast<uint4*>(B + (size_t)kb * BN * 128 + r * 128 + ((c ^ (r & 7)) << 4)) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  // |y~|^2 in FP32 and the candidate destinations, one warp per query row
+  for (int r = warp; r < BN; r += kThreads / 32) {
+    float s = 0.f;
+    if (r < npairs) {
+      const float* yq = Yp + (int64_t)pair_q[pb + r] * dp;
+      for (int j = lane; j < dp; j += 32) {
+        const float v = yq[j] - cl[j];
+        s = fmaf(v, v, s);
+      }
+      s = warp_sum(s);
+    }
+    if (lane == 0) {
+      sh.dst[r] = r < npairs ? pair_dst[pb + r] : -1;
+      sh.yn[r] = s;
+    }
+  }
+  tc::fence_proxy_async_smem();
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(2 * BN)) ncols <<= 1;
+  if (warp == 1) tc::tmem_alloc(&sh.tmem_base, ncols);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort = &sh.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int it = 0;  // loads issued so far
+      for (int tt = 0; tt < ntiles && !*abort; ++tt) {
+        for (int kb = 0; kb < KB; ++kb) {
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!tc::mbar_wait(&sh.empty[s], ph ^ 1u, abort)) break;
+          tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
+          tc::tma_load_2d(A + s * kStageBytes, &tmap, kb * kBK, (int)(xb + (int64_t)tt * kBM),
+                          &sh.full[s]);
+          ++it;
+        }
+      }
+      if (*abort) {
+        // let the last (at most kStages) loads land before the CTA's shared
+        // memory goes away; every earlier load was consumed by the MMA warp
+        volatile int no_abort = 0;
+        for (int j = it > kStages ? it - kStages : 0; j < it; ++j)
+          tc::mbar_wait(&sh.full[j % kStages], (uint32_t)(j / kStages) & 1u, &no_abort);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = tc::make_idesc(kBM, BN, 1u);
+      int it = 0;
+      bool ok = true;
+      for (int tt = 0; tt < ntiles && ok; ++tt) {
+        const int b = tt & 1;
+        const uint32_t tph = (uint32_t)(tt >> 1) & 1u;
+        if (!tc::mbar_wait(&sh.tempty[b], tph ^ 1u, abort)) break;
+        tc::tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!tc::mbar_wait(&sh.full[s], ph, abort)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::smem_u32(A + s * kStageBytes);
+          const uint32_t b0 = tc::smem_u32(B + (size_t)kb * BN * 128);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            tc::mma_f16(d_tmem, tc::desc_sw128(a0 + kk * 32), tc::desc_sw128(b0 + kk * 32),
+                        idesc, (kb | kk) != 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&sh.empty[s]);
+        }
+        if (ok) tc::mma_commit(&sh.tfull[b]);
+      }
+      // all issued MMAs complete before TMEM is released
+      tc::mma_commit(&sh.drain);
+      volatile int no_abort = 0;
+      tc::mbar_wait(&sh.drain, 0u, &no_abort);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 ----------------
+    const int lg = (warp & 3) * 32;
+    const int row = lg + lane;
+    for (int tt = 0; tt < ntiles; ++tt) {
+      const int b = tt & 1;
+      const uint32_t tph = (uint32_t)(tt >> 1) & 1u;
+      int ok = 1;
+      if (lane == 0) ok = tc::mbar_wait(&sh.tfull[b], tph, abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const int64_t pt = (int64_t)tt * kBM + row;
+      const bool valid = pt < len;
+      const float xn = valid ? XLcn[xb + pt] : 0.f;
+      const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * BN);
+      for (int c0 = 0; c0 < npairs; c0 += 16) {
+        uint32_t v[16];
+        tc::tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = c0 + j;
+          if (valid && col < npairs) {
+            const float d2 = fmaxf(xn + sh.yn[col] - 2.f * __uint_as_float(v[j]), 0.f);
+            cand[sh.dst[col] + pt] = d2;
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&sh.tempty[b]);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && sh.abort) atomicOr(err, KDE_ERRBIT_TMA);
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, ncols);
+  }
+}
+
+// the driver's tensor-map encoder, resolved at run time (no libcuda link)
+using EncodeTiledFn = decltype(&cuTensorMapEncodeTiled);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int scan_tc_bn(int dpb) {
+  const int KB = dpb / kBK;
+  int bn = 128;
+  while (bn > 16 && (size_t)KB * bn * 128 > 100 * 1024) bn -= 16;
+  return bn;
+}
+
+size_t scan_tc_smem(int dpb, int BN) {
+  return 1024 + (size_t)kStages * kStageBytes + (size_t)(dpb / kBK) * BN * 128;
+}
+
+bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return false;
+  CUtensorMap* map = reinterpret_cast<CUtensorMap*>(map_out);
+  cuuint64_t dims[2] = {(cuuint64_t)dpb, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dpb * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, const float* XLcn,
+                    const int64_t* list_off, int L, int dpb, int BN, const ScanPlan& plan,
+                    float* cand, uint32_t* err, cudaStream_t s) {
+  if (plan.max_tiles <= 0) return true;
+  const size_t smem = scan_tc_smem(dpb, BN);
+  static size_t configured = 0;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return false;
+    configured = smem;
+  }
+  k_scan_tc<<<(unsigned)plan.max_tiles, kThreads, smem, s>>>(
+      *reinterpret_cast<const CUtensorMap*>(tmap),
+      Yp, C, dp, XLcn, list_off, L, dpb, BN, plan.pair_q,
+      plan.pair_dst, plan.bucket_off, plan.tile_off, cand, err);
+  return true;
+}
+
+}  // namespace deann

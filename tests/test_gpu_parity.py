@@ -222,6 +222,44 @@ def test_query_end_to_end(pkg):
     assert index.margin_failures() == 0
 
 
+@pytest.mark.parametrize("which", ["iso16", "embed128", "unit300", "sparse784"])
+def test_bf16_tensor_core_scan(pkg, which):
+    """precision=BF16: the tcgen05 scan ranks candidates in BF16; after FP32
+    rescoring the neighbours match the oracle's IVF search as tightly as the
+    FP32 path does."""
+    if which == "iso16":
+        X, Y, _ = workloads.mixture_iso(n=7000, d=16, nq=300)
+    elif which == "embed128":
+        X, Y, _ = workloads.mixture_embed(n=9000, nq=300, n_centres=30)
+    elif which == "unit300":
+        X, Y, _ = workloads.unit_powerlaw(n=6000, nq=200, n_centres=40)
+    else:
+        X, Y, _ = workloads.sparse_image(n=5000, nq=120)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=12, seed=2)
+    C, assign = index.export_ivf()
+    for P, k in ((1, 25), (3, 60), (12, 100)):
+        nbr, d2 = index.search(_dev(Y), k, nprobe=P, precision=1)
+        _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, P, k)
+        assert_neighbours_match(X, Y, nbr.cpu().numpy(), want, want_d2)
+        f32, _ = index.search(_dev(Y), k, nprobe=P, precision=0)
+        assert np.array_equal(np.sort(f32.cpu().numpy(), 1), np.sort(nbr.cpu().numpy(), 1))
+    assert index.margin_failures() == 0
+    out, nb = index.query(_dev(Y), 30, 300, nprobe=3, seed=9, precision=1, return_neighbors=True)
+    assert_kde_close(out.cpu().numpy(),
+                     oracle.deann(X, Y, "gaussian", 2.0, nb.cpu().numpy(), 300, 9))
+
+
+def test_bf16_scan_many_queries_per_list(pkg):
+    """Hundreds of queries probing the same lists: several CTAs per list, ragged
+    last query group and ragged last 128-point tile."""
+    X, Y, _ = workloads.mixture_iso(n=3000, d=32, nq=900, n_centres=3)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=5, seed=4)
+    C, assign = index.export_ivf()
+    nbr, _ = index.search(_dev(Y), 64, nprobe=2, precision=1)
+    _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, 2, 64)
+    assert_neighbours_match(X, Y, nbr.cpu().numpy(), want, want_d2)
+
+
 def test_query_k_equals_n_is_exact(pkg):
     X, Y = _data(700, 4, 15, seed=8)
     index = pkg.KDEIndex(_dev(X), "gaussian", 1.2)
