@@ -370,11 +370,13 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler capture just this region
     ev0.record()
     for s in range(args.steps):
         outs.append(index.query(Yd, k, m, nprobe=P, seed=s, precision=prec))
     ev1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms_total = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     index.profile(False)

@@ -74,7 +74,10 @@ typedef struct {
   int32_t precision;        /* kde_precision of the scan (kde_query, kde_search) */
   int32_t sample_mode;      /* 0: reject draws in X_1 (default); 1: "drop" */
   int32_t kmeans_iters;     /* kde_build: Lloyd iterations (0 = 20) */
-  int32_t reserved;         /* must be 0 */
+  int32_t exact_path;       /* kde_exact: 0 = automatic (tensor cores when
+                               the accuracy guard below allows, else CUDA
+                               cores); 1 = CUDA cores; 2 = tensor cores
+                               (Gaussian and exponential kernels only) */
   uint64_t query_id_offset; /* qid of row r is query_id_offset + r */
   void* stream;             /* cudaStream_t, NULL = legacy default stream */
 } kde_opts;
@@ -151,8 +154,19 @@ kde_status kde_query_rs(kde_index* index, const float* Y, int64_t nq, int32_t m,
                         float* out, const kde_opts* opts);
 
 /* kde_exact -- the exact KDE (Section 2 definition; the "Naive" evaluation of
- * Appendix D), out[q] = (1/n) sum_i K_h(x_i, y_q), FP32 difference-form
- * distances, FP64 accumulation across the dataset. */
+ * Appendix D), out[q] = (1/n) sum_i K_h(x_i, y_q), FP64 accumulation across
+ * the dataset.  Two implementations:
+ *   CUDA cores: FP32 difference-form distances, any kernel;
+ *   tensor cores (Gaussian, exponential): D^2 = |x|^2 + |y|^2 - 2<x, y> with
+ *     both sides centred on the dataset mean and every operand split into
+ *     three BF16 parts (six partial products, FP32 accumulation in TMEM).
+ *     Its D^2 carries an absolute error near 2^-22 (|x - mean|^2 +
+ *     |y - mean|^2) from the FP32 accumulator, so a kernel value's relative
+ *     error is about that divided by 2h^2.
+ * opts.exact_path 0 picks the tensor cores for the Gaussian kernel when
+ * max_i |x_i - mean|^2 <= 8 (2 h^2) (in-distribution queries then stay near
+ * 1e-6 relative error) and the CUDA cores otherwise, including for the
+ * exponential kernel, whose derivative is unbounded at distance 0. */
 kde_status kde_exact(kde_index* index, const float* Y, int64_t nq, float* out,
                      const kde_opts* opts);
 

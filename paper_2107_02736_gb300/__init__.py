@@ -41,7 +41,7 @@ class KDEError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
-                ("kmeans_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("kmeans_iters", ctypes.c_int32), ("exact_path", ctypes.c_int32),
                 ("query_id_offset", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
@@ -152,12 +152,13 @@ class KDEIndex:
         self.nlist = int(nlist)
 
     # -- plumbing ----------------------------------------------------------
-    def _opts(self, precision=0, sample_mode=0, qid_offset=0, kmeans_iters=0, host=False):
+    def _opts(self, precision=0, sample_mode=0, qid_offset=0, kmeans_iters=0, host=False,
+              exact_path=0):
         o = _Opts()
         o.precision = int(precision)
         o.sample_mode = int(sample_mode)
         o.kmeans_iters = int(kmeans_iters)
-        o.reserved = 0
+        o.exact_path = int(exact_path)
         o.query_id_offset = int(qid_offset)
         o.stream = None if host else torch.cuda.current_stream().cuda_stream
         return o
@@ -282,13 +283,16 @@ class KDEIndex:
                                          0, 0, qid_offset, host=not Y.is_cuda))))
         return out
 
-    def exact(self, Y):
+    def exact(self, Y, path="auto"):
+        """Exact KDE.  path: "auto" (tensor cores when their accuracy guard
+        allows), "cuda" (FP32 difference form on CUDA cores) or "tensor"."""
         Y = self._prep(Y)
         nq = Y.shape[0]
         out = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        code = {"auto": 0, "cuda": 1, "tensor": 2}[path]
         with torch.cuda.device(self._device):
-            _check(_lib.kde_exact(self._h, _ptr(Y), nq, _ptr(out),
-                                  ctypes.byref(self._opts(host=not Y.is_cuda))))
+            _check(_lib.kde_exact(self._h, _ptr(Y), nq, _ptr(out), ctypes.byref(
+                self._opts(host=not Y.is_cuda, exact_path=code))))
         return out
 
     def sample_indices(self, nbr, m, seed=0, nq=None, sample_mode=0, qid_offset=0,

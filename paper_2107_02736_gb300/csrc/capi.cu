@@ -218,6 +218,8 @@ struct CallBufs {
   float* dY = nullptr;
   float* dlogh = nullptr;
   double* acc = nullptr;
+  void* Ys = nullptr;      // [3][nq][dpb] BF16 parts of the centred queries
+  float* ysn = nullptr;    // their squared norms
   SearchBufs search;
 };
 
@@ -233,6 +235,7 @@ struct CallShape {
   bool need_samples = false;
   bool grad = false;
   bool exact = false;
+  bool exact_tc = false;   // tensor-core exact: BF16 parts of the queries
 };
 
 void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -250,6 +253,10 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
     cb.dlogh = b.take<float>(nq);
   }
   if (c.exact) cb.acc = b.take<double>(nq);
+  if (c.exact_tc) {
+    cb.Ys = b.take<uint16_t>((size_t)3 * nq * ix->dpb);
+    cb.ysn = b.take<float>(nq);
+  }
   if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
 }
 
@@ -399,7 +406,8 @@ kde_status check_opts(const kde_opts* o) {
     return fail(KDE_EINVAL, "precision must be 0 (FP32) or 1 (BF16)");
   if (o->sample_mode != 0 && o->sample_mode != 1)
     return fail(KDE_EINVAL, "sample_mode must be 0 or 1");
-  if (o->reserved != 0) return fail(KDE_EINVAL, "kde_opts.reserved must be 0");
+  if (o->exact_path < 0 || o->exact_path > 2)
+    return fail(KDE_EINVAL, "exact_path must be 0 (auto), 1 (CUDA cores) or 2 (tensor cores)");
   return KDE_OK;
 }
 
@@ -516,7 +524,8 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   BTRY(dev_alloc(&ix->XLcn, (size_t)n));
   BTRY(dev_alloc(&ix->rad, (size_t)L));
   BTRY(dev_alloc(&ix->err, 4));
-  BTRY(dev_alloc(&ix->xmax_d, 1));
+  BTRY(dev_alloc(&ix->xmax_d, 2));
+  BCK(cudaMemsetAsync(ix->xmax_d, 0, 2 * sizeof(float), st));
   {
     uint16_t* b = nullptr;
     BTRY(dev_alloc(&b, (size_t)n * ix->dpb));
@@ -580,13 +589,27 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   launch_center_bf16(ix->XL, ix->dp, ix->list_off, (int)L, ix->C, ix->XLb, ix->dpb, ix->XLcn,
                      ix->rad, st);
   ix->tmap_ok = make_bf16_row_map(ix->tmap_xlb, ix->XLb, n, ix->dpb);
+  if (kernel != KDE_LAPLACIAN) {
+    // exact KDE on tensor cores: centred rows split into three BF16 parts
+    BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
+    BTRY(dev_alloc(&ix->xsn, (size_t)n));
+    uint16_t* xs = nullptr;
+    BTRY(dev_alloc(&xs, (size_t)3 * n * ix->dpb));
+    ix->Xs = xs;
+    launch_col_mean(ix->X, n, ix->dp, ix->mean, st);
+    launch_split3(ix->X, n, ix->dp, ix->mean, ix->Xs, n, ix->dpb, ix->xsn, st);
+    ix->xs_ok = make_parts_map(ix->tmap_xs, ix->Xs, 3 * n, ix->dpb);
+    launch_max_f32(ix->xsn, n, ix->xmax_d + 1, st);
+  }
   BCK(cudaGetLastError());
 
   ix->h_list_off = new int64_t[L + 1];
   BCK(cudaMemcpyAsync(ix->h_list_off, ix->list_off, sizeof(int64_t) * (L + 1),
                       cudaMemcpyDeviceToHost, st));
-  float xmax2 = 0.f;
-  BCK(cudaMemcpyAsync(&xmax2, ix->xmax_d, sizeof(float), cudaMemcpyDeviceToHost, st));
+  float maxes[2] = {0.f, 0.f};  // max |x|^2, max |x - mean|^2
+  BCK(cudaMemcpyAsync(maxes, ix->xmax_d, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+  const float xmax2 = maxes[0];
+  ix->xs_max2 = maxes[1];
   BCK(cudaStreamSynchronize(st));
   ix->xmax = std::sqrt(xmax2);
   ix->max_list = 0;
@@ -618,6 +641,9 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->Cn);
   cudaFree(ix->XLcn);
   cudaFree(ix->rad);
+  cudaFree(ix->mean);
+  cudaFree(ix->Xs);
+  cudaFree(ix->xsn);
   cudaFree(ix->err);
   cudaFree(ix->xmax_d);
   if (ix->scratch.base) cudaFree(ix->scratch.base);
@@ -822,11 +848,27 @@ kde_status kde_exact(kde_index* ix, const float* Y, int64_t nq, float* out,
   c.host = host;
   c.need_out = host;
   c.exact = true;
+  bool tcore = false;
+  if (o->exact_path == 2) {
+    if (!ix->xs_ok) return fail(KDE_EINVAL, "tensor-core exact KDE needs a Euclidean kernel");
+    tcore = true;
+  } else if (o->exact_path == 0) {
+    // accuracy guard (see kde_exact in the header)
+    tcore = ix->xs_ok && ix->kern == KDE_KERN_GAUSSIAN &&
+            ix->xs_max2 <= 8.0f * 2.0f * ix->h * ix->h;
+  }
+  c.exact_tc = tcore;
   CallBufs cb;
   TRY(prepare_call(ix, c, cb));
   TRY(stage_queries(ix, Y, nq, host, cb, st));
   float* o_d = host ? cb.out : out;
-  {
+  if (tcore) {
+    StageTimer t(ix, ST_EXACT, st, 3);
+    launch_split3(cb.Yp, nq, ix->dp, ix->mean, cb.Ys, nq, ix->dpb, cb.ysn, st);
+    if (!launch_exact_tc(ix->tmap_xs, cb.Ys, cb.ysn, nq, nq, ix->xsn, ix->n, ix->dpb, ix->kern,
+                         ix->h, cb.acc, o_d, ix->err, st))
+      return fail(KDE_ECUDA, "could not configure the tensor-core exact kernel");
+  } else {
     StageTimer t(ix, ST_EXACT, st, 2);
     launch_exact_simt(cb.Yp, cb.Yn, nq, ix->X, ix->Xn, ix->n, ix->d, ix->dp, ix->kern, ix->h,
                       cb.acc, o_d, st);
@@ -1006,6 +1048,7 @@ kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t 
     c.need_samples = variant == 1;
     c.grad = variant == 2;
     c.exact = variant == 3;
+    c.exact_tc = variant == 3 && ix->xs_ok;
     Bump cnt;
     CallBufs dummy;
     carve_call(cnt, ix, c, dummy);

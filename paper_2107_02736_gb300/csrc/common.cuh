@@ -106,6 +106,7 @@ __device__ __forceinline__ float precise_sq_dist(const float* __restrict__ x,
                                                  const float* __restrict__ y, int d,
                                                  int lane_in_group) {
   float hi = 0.f, lo = 0.f;
+#pragma unroll 4
   for (int j = lane_in_group; j < d; j += G) {
     float diff, derr;
     two_sum(x[j], -y[j], diff, derr);

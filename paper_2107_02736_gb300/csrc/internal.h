@@ -79,6 +79,15 @@ struct kde_index {
   // 128-byte swizzle
   alignas(64) unsigned char tmap_xlb[128] = {0};
   bool tmap_ok = false;
+  // exact KDE on tensor cores (Euclidean kernels): dataset mean, the rows
+  // minus the mean split into three BF16 parts [3][n][dpb], their squared
+  // norms, and the TMA descriptor of the parts
+  float* mean = nullptr;
+  void* Xs = nullptr;
+  float* xsn = nullptr;
+  alignas(64) unsigned char tmap_xs[128] = {0};
+  bool xs_ok = false;
+  float xs_max2 = 0.f;        // max |x - mean|^2 (accuracy guard of the tensor-core path)
   uint32_t* err = nullptr;    // device error words [4]
   float* xmax_d = nullptr;    // device max |x|^2
   float xmax = 0.f;           // max |x| over the dataset
@@ -150,6 +159,15 @@ bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb);
 bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, const float* XLcn,
                     const int64_t* list_off, int L, int dpb, int BN, const ScanPlan& plan,
                     float* cand, uint32_t* err, cudaStream_t s);
+
+// ---- tc_exact.cu (tcgen05 exact KDE, three-way BF16 split) -----------------
+void launch_col_mean(const float* X, int64_t n, int dp, float* mean, cudaStream_t s);
+void launch_split3(const float* V, int64_t rows, int dp, const float* mean, void* dst,
+                   int64_t rows_pad, int dpb, float* norms, cudaStream_t s);
+bool make_parts_map(void* map_out, const void* base, int64_t rows_total, int dpb);
+bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_t nq, int64_t nqp,
+                     const float* xn, int64_t n, int dpb, int kern, float h, double* acc,
+                     float* out, uint32_t* err, cudaStream_t s);
 
 // ---- select.cu -------------------------------------------------------------
 void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStream_t s);

@@ -26,7 +26,7 @@ namespace {
 constexpr int kNT = 256;
 constexpr int kNW = kNT / 32;
 constexpr int kChunk = 1024;   // samples staged per gather round
-constexpr int kUnroll = 4;     // rows in flight per lane group
+constexpr int kUnroll = 8;     // rows in flight per lane group
 
 struct EstSmem {
   int nb[kMaxK];               // sorted distinct neighbour ids
@@ -170,12 +170,12 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
   // warp-uniform trip count: the group reductions below need all 32 lanes
   for (int wb = warp * kGpw * kUnroll; wb < cnt; wb += kNW * kGpw * kUnroll) {
     const int base = wb + gw * kUnroll;
-    const float4* rows[kUnroll];
+    // 32-bit row ids keep the register footprint small; kUnroll independent
+    // 16-byte loads per lane are in flight at once
+    int rid[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int r = base + u;
-      rows[u] = r < cnt ? reinterpret_cast<const float4*>(X + (int64_t)ids[r] * dp) : nullptr;
-    }
+    for (int u = 0; u < kUnroll; ++u) rid[u] = base + u < cnt ? ids[base + u] : -1;
+    const float4* X4 = reinterpret_cast<const float4*>(X);
     float acc[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) acc[u] = 0.f;
@@ -184,7 +184,7 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
       float4 xv[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
-        xv[u] = rows[u] ? __ldg(rows[u] + j4) : yv;
+        xv[u] = rid[u] >= 0 ? __ldg(X4 + (size_t)rid[u] * dp4 + j4) : yv;
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         const float a = xv[u].x - yv.x, b = xv[u].y - yv.y, c = xv[u].z - yv.z,
@@ -228,7 +228,7 @@ __device__ float block_sum(float v, EstSmem& sm) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(kNT) k_estimate(SampleArgs a) {
+__global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   __shared__ EstSmem sm;
   __shared__ int tmp[kMaxK];
   extern __shared__ float4 ys4[];

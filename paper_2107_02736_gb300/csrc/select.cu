@@ -365,17 +365,26 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
     }
   }
-  // rescore in difference form (compensated FP32), one warp per candidate
-  for (int j = warp; j < K; j += kNW) {
-    const int s = sm.slot[j];
-    int lo = 0, hi = a.P - 1;  // last segment with start <= s
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+  // rescore in difference form (compensated FP32): 8 lanes per candidate, so
+  // each warp has 4 candidate rows in flight
+  {
+    const int grp = lane >> 3, lig = lane & 7;
+    for (int j0 = warp * 4; j0 < K; j0 += kNW * 4) {
+      const int j = j0 + grp;
+      const bool valid = j < K;
+      int64_t pos = 0;
+      if (valid) {
+        const int s = sm.slot[j];
+        int lo = 0, hi = a.P - 1;  // last segment with start <= s
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        pos = s_lstart[lo] + (s - s_seg[lo]);
+      }
+      const float d2 = precise_sq_dist<8>(a.XL + pos * a.dp, y, a.d, lig);
+      if (valid && lig == 0) sm.key[j] = pack_key(d2, a.perm[pos]);
     }
-    const int64_t pos = s_lstart[lo] + (s - s_seg[lo]);
-    const float d2 = precise_sq_dist<32>(a.XL + pos * a.dp, y, a.d, lane);
-    if (lane == 0) sm.key[j] = pack_key(d2, a.perm[pos]);
   }
   __syncthreads();
   block_sort_keys(sm, K);

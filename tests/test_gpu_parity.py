@@ -158,11 +158,51 @@ def test_exact(pkg, d, kernel):
     X, Y = _data(n, d, nq, seed=10 + d)
     h = _bandwidth(d) if kernel != "laplacian" else 0.7 * d
     index = pkg.KDEIndex(_dev(X), kernel, h)
+    want = oracle.exact(X, Y, kernel, h)
     got = index.exact(_dev(Y)).cpu().numpy()
-    assert_kde_close(got, oracle.exact(X, Y, kernel, h))
-    # host-pointer path gives the same numbers
+    assert_kde_close(got, want)
+    got_c = index.exact(_dev(Y), path="cuda").cpu().numpy()
+    assert_kde_close(got_c, want)
+    if kernel != "laplacian":
+        got_t = index.exact(_dev(Y), path="tensor").cpu().numpy()
+        assert_kde_close(got_t, want)
+    # host-pointer path: same numbers up to the order of the FP64 atomics
     got_h = index.exact(torch.from_numpy(Y)).numpy()
-    assert np.array_equal(got, got_h)
+    assert np.allclose(got, got_h, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("which,h", [("embed128", 12.8), ("unit300", 0.35), ("sparse784", 1.3)])
+def test_exact_tensor_cores_on_workload_shapes(pkg, which, h):
+    """The three-way BF16 split keeps FP32-level accuracy on the workloads'
+    own geometry (norms far from zero, d up to 784, ragged tiles) inside its
+    accuracy guard, max |x - mean|^2 <= 8 (2 h^2)."""
+    if which == "embed128":
+        X, Y, _ = workloads.mixture_embed(n=20000, nq=200, n_centres=50)
+    elif which == "unit300":
+        X, Y, _ = workloads.unit_powerlaw(n=20000, nq=150, n_centres=60)
+    else:
+        X, Y, _ = workloads.sparse_image(n=6000, nq=100)
+    index = pkg.KDEIndex(_dev(X), "gaussian", h)
+    assert_kde_close(index.exact(_dev(Y), path="tensor").cpu().numpy(),
+                     oracle.exact(X, Y, "gaussian", h))
+    index.close()
+    if which == "embed128":
+        index = pkg.KDEIndex(_dev(X), "exponential", h)
+        assert_kde_close(index.exact(_dev(Y), path="tensor").cpu().numpy(),
+                         oracle.exact(X, Y, "exponential", h))
+
+
+def test_exact_auto_path_respects_accuracy_guard(pkg):
+    """A bandwidth far below the data's spread sends the automatic path to the
+    CUDA cores (2 launches per call) instead of the tensor cores (3)."""
+    X, Y, _ = workloads.unit_powerlaw(n=5000, nq=50, n_centres=20)
+    for h, want_launches in ((0.05, 2), (0.5, 3)):
+        index = pkg.KDEIndex(_dev(X), "gaussian", h)
+        index.profile_read(reset=True)
+        got = index.exact(_dev(Y)).cpu().numpy()
+        assert index.profile_read(reset=True)["exact"]["launches"] == want_launches
+        assert_kde_close(got, oracle.exact(X, Y, "gaussian", h))
+        index.close()
 
 
 # ---------------------------------------------------------------- ANN search --
