@@ -189,6 +189,19 @@ kde_status kde_grad_with_neighbors(kde_index* index, const float* Y, int64_t nq,
                                    const float* gout, float* out, float* dY, float* dlogh,
                                    const kde_opts* opts);
 
+/* kde_mean_shift -- density-gradient flow with the DEANN estimate (Gaussian
+ * kernel only; the paper names gradient lines of densities as a use of KDE,
+ * Section 1): `steps` updates y <- y + h^2 grad(KDE~)(y) / KDE~(y), which for
+ * the Gaussian kernel move y to the estimate-weighted mean of its neighbour
+ * and sample points.  Step s draws X_1 and S afresh with seed + s; the
+ * gradient is the adjoint of kde_grad_with_neighbors.
+ *   Y    nq x d, updated in place (host or device).
+ *   est  NULL or nq: the estimate at the start of the last step.
+ * Same argument limits as kde_query; d <= 1024. */
+kde_status kde_mean_shift(kde_index* index, float* Y, int64_t nq, int32_t steps, int32_t k,
+                          int32_t m, int32_t nprobe, uint64_t seed, float* est,
+                          const kde_opts* opts);
+
 /* kde_sync -- wait for the index's work on opts->stream and report (then
  * clear) errors raised by kernels of earlier device-pointer calls:
  * KDE_ELIMIT (draw cap), KDE_EINVAL (neighbour id >= n). */

@@ -83,6 +83,7 @@ def load_library():
         "kde_exact": [P, P, i64, P, O],
         "kde_sample_indices": [P, i64, P, i32, i32, u64, P, O],
         "kde_grad_with_neighbors": [P, P, i64, P, i32, i32, u64, P, P, P, P, O],
+        "kde_mean_shift": [P, P, i64, i32, i32, i32, i32, u64, P, O],
         "kde_sync": [P, O],
         "kde_stats": [P, P, O],
         "kde_reserve": [P, i64, i32, i32, i32, O],
@@ -317,6 +318,19 @@ class KDEIndex:
                 ctypes.byref(self._opts(0, sample_mode, qid_offset,
                                         host=S.device.type == "cpu"))))
         return S
+
+    def mean_shift(self, Y, steps, k, m, nprobe=1, seed=0, precision=0, qid_offset=0):
+        """Runs `steps` Gaussian mean-shift updates on a copy of Y; returns
+        (moved queries, estimate at the start of the last step)."""
+        Y = self._prep(Y).clone()
+        nq = Y.shape[0]
+        est = torch.empty(nq, dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_mean_shift(self._h, _ptr(Y), nq, int(steps), int(k), int(m),
+                                       int(nprobe), int(seed) & (2**64 - 1), _ptr(est),
+                                       ctypes.byref(self._opts(precision, 0, qid_offset,
+                                                               host=not Y.is_cuda))))
+        return Y, est
 
     def grad_with_neighbors(self, Y, nbr, m, seed=0, gout=None, sample_mode=0, qid_offset=0):
         """(out, dY, dlogh_per_query) of the estimate with X_1 and S fixed."""

@@ -182,7 +182,7 @@ struct SearchBufs {
   float* cand = nullptr;
 };
 
-constexpr size_t kCandCap = size_t(2) << 30;
+constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of queries
 
 void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
   const int L = ix->nlist;
@@ -970,6 +970,66 @@ kde_status kde_grad_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
     if (out) TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
     if (dlogh) TRY(copy_out(dlogh, cb.dlogh, sizeof(float) * nq, true, st));
   }
+  return finish_call(ix, host, st);
+}
+
+kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, int32_t k,
+                          int32_t m, int32_t nprobe, uint64_t seed, float* est,
+                          const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m));
+  if (ix->kern != KDE_KERN_GAUSSIAN)
+    return fail(KDE_EINVAL, "mean shift is defined here for the Gaussian kernel");
+  if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
+  if (steps < 0) return fail(KDE_EINVAL, "steps must be >= 0");
+  if (k > 0) {
+    TRY(check_search_args(ix, nq, k, nprobe));
+  } else if (m < 1) {
+    return fail(KDE_EINVAL, "k = 0 needs m >= 1");
+  }
+  if (nq == 0) return KDE_OK;
+  if (Y == nullptr) return fail(KDE_EINVAL, "Y must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {est}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.P = nprobe;
+  c.search = k > 0;
+  c.host = host;
+  c.need_out = true;
+  c.need_nbr = k > 0;
+  c.grad = true;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  if (steps == 0) CK(cudaMemsetAsync(cb.out, 0, sizeof(float) * nq, st));
+  for (int s = 0; s < steps; ++s) {
+    if (s > 0) {
+      StageTimer t(ix, ST_STAGE, st, 1);
+      launch_query_norms(cb.Yp, nq, ix->dp, cb.Yn, st);
+    }
+    // X_1 and S are redrawn at every step: the step's seed is seed + step
+    if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, cb.nbr, nullptr, nullptr, st));
+    SampleArgs a = sample_args(ix, cb, nq, k > 0 ? cb.nbr : nullptr, k, m, seed + (uint64_t)s, o);
+    a.rs = k == 0 ? 1 : 0;
+    a.out = cb.out;
+    a.dY = cb.dY;
+    {
+      StageTimer t(ix, ST_GRAD, st, 2);
+      launch_estimate_grad(a, st);
+      launch_mean_shift_update(cb.Yp, ix->dp, ix->d, cb.dY, cb.out, nq, ix->h, st);
+    }
+  }
+  CK(cudaMemcpy2DAsync(Y, sizeof(float) * ix->d, cb.Yp, sizeof(float) * ix->dp,
+                       sizeof(float) * ix->d, (size_t)nq,
+                       host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (est) TRY(copy_out(est, cb.out, sizeof(float) * nq, host, st));
   return finish_call(ix, host, st);
 }
 

@@ -240,5 +240,7 @@ struct SampleArgs {
 };
 void launch_estimate(const SampleArgs& a, cudaStream_t s);
 void launch_estimate_grad(const SampleArgs& a, cudaStream_t s);
+void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,
+                              int64_t nq, float h, cudaStream_t s);
 
 }  // namespace deann

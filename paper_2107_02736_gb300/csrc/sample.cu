@@ -505,6 +505,20 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
   }
 }
 
+// One Gaussian mean-shift step with the estimated density: the fixed point
+// of y = sum_i w_i K_i x_i / sum_i w_i K_i is reached by
+// y <- y + h^2 grad(est)(y) / est(y) (grad = sum_i w_i K_i (x_i - y) / h^2).
+__global__ void k_mean_shift_update(float* __restrict__ Yp, int dp, int d,
+                                    const float* __restrict__ dY, const float* __restrict__ est,
+                                    int64_t nq, float h2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * d) return;
+  const int64_t q = i / d;
+  const int j = (int)(i - q * d);
+  const float e = est[q];
+  if (e > 0.f) Yp[q * dp + j] += h2 * dY[i] / e;
+}
+
 int group_lanes(int dp) {
   const int dp4 = dp / 4;
   if (dp4 <= 4) return 4;
@@ -525,6 +539,14 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s) {
     case 16: k_estimate<16><<<grid, kNT, dyn, s>>>(a); break;
     default: k_estimate<32><<<grid, kNT, dyn, s>>>(a); break;
   }
+}
+
+void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,
+                              int64_t nq, float h, cudaStream_t s) {
+  const int64_t total = nq * d;
+  if (total <= 0) return;
+  k_mean_shift_update<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Yp, dp, d, dY, est, nq,
+                                                                      h * h);
 }
 
 void launch_estimate_grad(const SampleArgs& a, cudaStream_t s) {

@@ -61,9 +61,20 @@ __device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, in
     const int shift = 24 - 8 * pass;
     for (int i = tid; i < 256; i += kNT) sm.hist[i] = 0;
     __syncthreads();
-    for (int64_t i = tid; i < cnt; i += kNT) {
-      const uint32_t key = dist_key(vals[i]);
-      if ((key & pmask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 255], 1);
+    // four independent loads per thread per iteration keep more reads in flight
+    for (int64_t i0 = tid; i0 < cnt; i0 += 4 * kNT) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * kNT;
+        v[u] = i < cnt ? vals[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (i0 + u * kNT >= cnt) continue;
+        const uint32_t key = dist_key(v[u]);
+        if ((key & pmask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 255], 1);
+      }
     }
     __syncthreads();
     if (warp == 0) {

@@ -1,0 +1,173 @@
+"""The five synthetic workloads through the C-ABI, checked against the oracle.
+
+The low-dimensional workload runs at full size on every query.  The
+1M-point d=128 workload runs at full size in the launch configuration the
+benchmark times (BF16 tcgen05 scan, k = 1024, m = 8000, nprobe = 8, 10k
+queries) and sampled queries are checked one by one.  The others run at
+reduced n with their own dimension, kernel and parameters.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from test_gpu_parity import assert_kde_close, assert_neighbours_match
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2107_02736_gb300 as p
+    p.load_library()
+    return p
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_low_dim_brute_force_full(pkg):
+    """n = 10,000, d = 16, 1,000 queries, Gaussian h = 2, brute-force kNN,
+    k = 50, m = 500, seed 0; exact KDE for every query."""
+    w = workloads.make(1)
+    assert w.X.shape == (10_000, 16) and w.Y.shape == (1_000, 16)
+    index = pkg.KDEIndex(_dev(w.X), "gaussian", 2.0, nlist=1)
+    out, nbr = index.query(_dev(w.Y), 50, 500, nprobe=1, seed=0, return_neighbors=True)
+    nbr = nbr.cpu().numpy()
+    want_nbr, want_d2 = oracle.knn(w.X, w.Y, 50)
+    assert_neighbours_match(w.X, w.Y, nbr, want_nbr, want_d2)
+    assert_kde_close(out.cpu().numpy(), oracle.deann(w.X, w.Y, "gaussian", 2.0, nbr, 500, 0))
+    ex = oracle.exact(w.X, w.Y, "gaussian", 2.0)
+    assert_kde_close(index.exact(_dev(w.Y)).cpu().numpy(), ex)
+    assert_kde_close(index.query_rs(_dev(w.Y), 500, seed=0).cpu().numpy(),
+                     oracle.rs(w.X, w.Y, "gaussian", 2.0, 500, 0))
+
+
+@pytest.fixture(scope="module")
+def embed(pkg):
+    X, Y, _ = workloads.mixture_embed()
+    index = pkg.KDEIndex(_dev(X), "gaussian", 12.85, nlist=1024, seed=1)
+    C, assign = index.export_ivf()
+    return X, Y, index, C.numpy(), assign.numpy()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_embed_full_size_sampled(embed, precision):
+    X, Y, index, C, assign = embed
+    k, m, P, h = 1024, 8000, 8, 12.85
+    out, nbr = index.query(_dev(Y), k, m, nprobe=P, seed=3, precision=precision,
+                           return_neighbors=True)
+    out, nbr = out.cpu().numpy(), nbr.cpu().numpy()
+    rng = np.random.default_rng(precision)
+    qs = np.sort(rng.choice(Y.shape[0], 24, replace=False))
+    _, want, want_d2 = oracle.ivf_search(X, C, assign, Y[qs], P, k)
+    assert_neighbours_match(X, Y[qs], nbr[qs], want, want_d2)
+    # the estimator's stream of query row q is qid = q
+    for q in qs:
+        v = oracle.deann(X, Y[q:q + 1], "gaussian", h, nbr[q:q + 1], m, 3, qid_offset=int(q))
+        assert_kde_close(out[q:q + 1], v)
+    assert index.margin_failures() == 0
+
+
+def test_embed_full_size_exact_sampled(embed):
+    X, Y, index, _, _ = embed
+    ex = index.exact(_dev(Y)).cpu().numpy()
+    qs = np.arange(0, Y.shape[0], 625)  # 16 queries
+    assert_kde_close(ex[qs], oracle.exact(X, Y[qs], "gaussian", 12.85))
+
+
+def test_sparse_image_reduced(pkg):
+    """d = 784 sparse [0, 1] data: BF16 and FP32 scans give the same
+    neighbours; estimates match the oracle."""
+    X, Y, _ = workloads.sparse_image(n=30_000, nq=200)
+    h = 1.3
+    index = pkg.KDEIndex(_dev(X), "gaussian", h, nlist=64, seed=2)
+    C, assign = index.export_ivf()
+    o16, n16 = index.query(_dev(Y), 200, 2000, nprobe=8, seed=1, precision=1,
+                           return_neighbors=True)
+    o32, n32 = index.query(_dev(Y), 200, 2000, nprobe=8, seed=1, precision=0,
+                           return_neighbors=True)
+    n16, n32 = n16.cpu().numpy(), n32.cpu().numpy()
+    assert np.array_equal(np.sort(n16, 1), np.sort(n32, 1))
+    _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, 8, 200)
+    assert_neighbours_match(X, Y, n16, want, want_d2)
+    assert_kde_close(o16.cpu().numpy(), oracle.deann(X, Y, "gaussian", h, n16, 2000, 1))
+    assert index.margin_failures() == 0
+
+
+def test_aniso_gradient_and_mean_shift(pkg):
+    """d = 64 anisotropic mixture, Gaussian h = 1: forward and adjoint against
+    the oracle's analytic gradient and FP64 central differences (step 1e-3 h),
+    and mean-shift steps against the oracle's."""
+    X, Y, _ = workloads.mixture_aniso(n=20_000, nq=64)
+    h, k, m, P = 1.0, 100, 1000, 8
+    index = pkg.KDEIndex(_dev(X), "gaussian", h, nlist=64, seed=3)
+    C, assign = index.export_ivf()
+    C, assign = C.numpy(), assign.numpy()
+    out, nbr = index.query(_dev(Y), k, m, nprobe=P, seed=5, return_neighbors=True)
+    nbr = nbr.cpu().numpy()
+    est, dY, dl = index.grad_with_neighbors(_dev(Y), _dev(nbr), m, seed=5)
+    w_out, w_dY, w_dl = oracle.deann_grad(X, Y, "gaussian", h, nbr, m, 5)
+    assert_kde_close(est.cpu().numpy(), w_out)
+    assert_kde_close(out.cpu().numpy(), w_out)
+    dY = dY.cpu().numpy().astype(np.float64)
+    for q in range(Y.shape[0]):
+        assert np.linalg.norm(dY[q] - w_dY[q]) <= 1e-4 * np.linalg.norm(w_dY[q]) + 1e-12
+    assert np.allclose(dl.cpu().numpy(), w_dl, rtol=1e-4, atol=1e-12)
+    # central differences of the oracle estimator with the same sets, 8 queries
+    _, S = oracle.deann(X, Y, "gaussian", h, nbr, m, 5, return_samples=True)
+    step = 1e-3 * h
+    for q in range(8):
+        ids = np.unique(nbr[q][nbr[q] >= 0])
+        def f(y):
+            k1 = np.exp(-((X[ids].astype(np.float64) - y) ** 2).sum(1) / (2 * h * h)).sum()
+            k2 = np.exp(-((X[S[q]].astype(np.float64) - y) ** 2).sum(1) / (2 * h * h)).sum()
+            n = X.shape[0]
+            return (k1 + (n - ids.size) / m * k2) / n
+        y0 = Y[q].astype(np.float64)
+        fd = np.array([(f(y0 + step * e) - f(y0 - step * e)) / (2 * step)
+                       for e in np.eye(X.shape[1])])
+        assert np.linalg.norm(dY[q] - fd) <= 1e-3 * np.linalg.norm(fd)
+    # two mean-shift steps: the oracle repeats search + adjoint with seed + step
+    Yg, _ = index.mean_shift(_dev(Y[:16]), 2, k, m, nprobe=P, seed=7)
+    Yo = Y[:16].astype(np.float64)
+    for s in range(2):
+        Y32 = Yo.astype(np.float32)
+        _, nb, _ = oracle.ivf_search(X, C, assign, Y32, P, k)
+        e, g, _ = oracle.deann_grad(X, Y32, "gaussian", h, nb, m, 7 + s)
+        Yo = Y32.astype(np.float64) + h * h * g / e[:, None]
+    moved = np.linalg.norm(Yo - Y[:16], axis=1)
+    err = np.linalg.norm(Yg.cpu().numpy() - Yo, axis=1)
+    assert np.all(err <= 1e-4 * np.maximum(moved, 1e-3)), (err, moved)
+
+
+def test_unit_powerlaw_uneven_batches(pkg):
+    """d = 300 unit vectors, exponential kernel, BF16 scan: uneven batches
+    served one call each (query-id offsets) or all in one call give identical
+    results, and spot checks match the oracle."""
+    X, Y, _ = workloads.unit_powerlaw(n=40_000, nq=2_000, n_centres=200)
+    h = 0.2
+    sizes = workloads.uneven_batches(total=2_000, nbatch=8, lo=16, hi=800, seed=1)
+    index = pkg.KDEIndex(_dev(X), "exponential", h, nlist=128, seed=4)
+    Yd = _dev(Y)
+    whole, nbr = index.query(Yd, 200, 2000, nprobe=8, seed=9, precision=1,
+                             return_neighbors=True)
+    whole, nbr = whole.cpu().numpy(), nbr.cpu().numpy()
+    start, parts = 0, []
+    for b in sizes:
+        parts.append(index.query(Yd[start:start + b], 200, 2000, nprobe=8, seed=9, precision=1,
+                                 qid_offset=start).cpu().numpy())
+        start += int(b)
+    assert np.array_equal(np.concatenate(parts), whole)
+    C, assign = index.export_ivf()
+    qs = np.array([0, 17, 555, 1999])
+    _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y[qs], 8, 200)
+    assert_neighbours_match(X, Y[qs], nbr[qs], want, want_d2)
+    for q in qs:
+        v = oracle.deann(X, Y[q:q + 1], "exponential", h, nbr[q:q + 1], 2000, 9,
+                         qid_offset=int(q))
+        assert_kde_close(whole[q:q + 1], v)
