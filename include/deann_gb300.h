@@ -80,6 +80,11 @@ typedef struct {
                                (Gaussian and exponential kernels only) */
   uint64_t query_id_offset; /* qid of row r is query_id_offset + r */
   void* stream;             /* cudaStream_t, NULL = legacy default stream */
+  const void* dev_query_id_offset; /* NULL, or a DEVICE pointer to a uint64
+                               added to query_id_offset when the estimator
+                               runs: a call captured in a CUDA graph then
+                               serves a new batch (new sample streams) per
+                               replay by rewriting this value */
 } kde_opts;
 
 /* kde_build -- build an index over X (Section 4: FAISS-style inverted file).

@@ -22,8 +22,8 @@ import torch
 
 from . import build as _build_mod
 
-__all__ = ["KDEIndex", "DeannKDE", "KDEError", "library_path", "load_library",
-           "GAUSSIAN", "EXPONENTIAL", "LAPLACIAN"]
+__all__ = ["KDEIndex", "DeannKDE", "GraphedQuery", "BatchServer", "KDEError", "library_path",
+           "load_library", "GAUSSIAN", "EXPONENTIAL", "LAPLACIAN"]
 
 GAUSSIAN, EXPONENTIAL, LAPLACIAN = 0, 1, 2
 _KERNELS = {"gaussian": GAUSSIAN, "exponential": EXPONENTIAL, "laplacian": LAPLACIAN}
@@ -42,7 +42,8 @@ class KDEError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
                 ("kmeans_iters", ctypes.c_int32), ("exact_path", ctypes.c_int32),
-                ("query_id_offset", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("query_id_offset", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("dev_query_id_offset", ctypes.c_void_p)]
 
 
 STAGES = ["stage", "coarse", "plan", "scan", "select", "estimate", "exact", "grad"]
@@ -248,18 +249,31 @@ class KDEIndex:
         return nbr, d2
 
     def query(self, Y, k, m, nprobe=1, seed=0, precision=0, sample_mode=0, qid_offset=0,
-              return_neighbors=False):
+              return_neighbors=False, dev_qid=None):
+        """DEANN estimates (Algorithm 1).  dev_qid: optional int64 CUDA tensor
+        of one element added to qid_offset on the device (graph replays)."""
         Y = self._prep(Y)
         nq = Y.shape[0]
         out = torch.empty(nq, dtype=torch.float32, device=Y.device)
         nbr = (torch.empty((nq, k), dtype=torch.int32, device=Y.device)
                if return_neighbors and k > 0 else None)
+        o = self._opts(precision, sample_mode, qid_offset, host=not Y.is_cuda)
+        if dev_qid is not None:
+            o.dev_query_id_offset = dev_qid.data_ptr()
         with torch.cuda.device(self._device):
             _check(_lib.kde_query(self._h, _ptr(Y), nq, int(k), int(m), int(nprobe),
                                   int(seed) & (2**64 - 1), _ptr(out), _ptr(nbr),
-                                  ctypes.byref(self._opts(precision, sample_mode, qid_offset,
-                                                          host=not Y.is_cuda))))
+                                  ctypes.byref(o)))
         return (out, nbr) if return_neighbors else out
+
+    def query_batches(self, Ys, k, m, nprobe=1, seed=0, precision=0):
+        """Uneven batches served by one call over their concatenation (one
+        launch per stage for all of them); batch b keeps the sample streams it
+        would get alone with qid_offset = its start row.  Returns a list."""
+        sizes = [int(y.shape[0]) for y in Ys]
+        out = self.query(torch.cat([self._prep(y) for y in Ys]), k, m, nprobe=nprobe,
+                         seed=seed, precision=precision)
+        return list(torch.split(out, sizes))
 
     def query_with_neighbors(self, Y, nbr, m, seed=0, sample_mode=0, qid_offset=0):
         Y = self._prep(Y)
@@ -351,6 +365,73 @@ class KDEIndex:
                 int(seed) & (2**64 - 1), _ptr(g), _ptr(out), _ptr(dY), _ptr(dl),
                 ctypes.byref(self._opts(0, sample_mode, qid_offset, host=not Y.is_cuda))))
         return out, dY, dl
+
+
+class GraphedQuery:
+    """kde_query of a fixed capacity captured once in a CUDA graph.
+
+    The index's scratch is reserved before the capture, so the captured call
+    allocates nothing.  Each replay serves one batch of at most `capacity`
+    queries: the batch is copied into the static input (rows past the batch
+    keep stale values; their outputs are discarded) and the batch's first
+    query id is written to a device scalar that the estimator reads, so every
+    replay draws the sample streams the direct call with that qid_offset
+    would draw.
+    """
+
+    def __init__(self, index: KDEIndex, capacity, k, m, nprobe=1, seed=0, precision=0):
+        self.index, self.capacity = index, int(capacity)
+        dev = index.device
+        self.Y = torch.zeros((self.capacity, index.d), dtype=torch.float32, device=dev)
+        self.qid = torch.zeros(1, dtype=torch.int64, device=dev)
+        index.reserve(self.capacity, k, m, nprobe)
+        args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision, dev_qid=self.qid)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):  # first launches (module loading) outside the capture
+            index.query(self.Y, **args)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self.out = index.query(self.Y, **args)
+
+    def __call__(self, Yb, qid_offset=0):
+        nb = int(Yb.shape[0])
+        if nb > self.capacity:
+            raise ValueError(f"batch of {nb} exceeds the captured capacity {self.capacity}")
+        self.Y[:nb].copy_(Yb, non_blocking=True)
+        self.qid.fill_(int(qid_offset))
+        self.graph.replay()
+        return self.out[:nb]
+
+
+class BatchServer:
+    """Serves uneven batches with CUDA graphs captured per power-of-two
+    capacity class (16 ... max_batch); the query ids run on across batches."""
+
+    def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192):
+        self.index, self.args = index, dict(k=k, m=m, nprobe=nprobe, seed=seed,
+                                            precision=precision)
+        self.max_batch = int(max_batch)
+        self.graphs = {}
+        self.next_qid = 0
+
+    def _graph(self, nb):
+        cap = 16
+        while cap < nb:
+            cap *= 2
+        if cap not in self.graphs:
+            self.graphs[cap] = GraphedQuery(self.index, cap, **self.args)
+        return self.graphs[cap]
+
+    def __call__(self, Yb):
+        nb = int(Yb.shape[0])
+        if nb > self.max_batch:
+            raise ValueError(f"batch of {nb} exceeds max_batch {self.max_batch}")
+        out = self._graph(nb)(Yb, self.next_qid)
+        self.next_qid += nb
+        return out
 
 
 class DeannKDE(torch.autograd.Function):

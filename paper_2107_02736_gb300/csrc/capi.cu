@@ -72,7 +72,7 @@ cudaStream_t stream_of(const kde_opts* o) {
                                                 : cudaStream_t(0);
 }
 
-const kde_opts kDefaultOpts = {0, 0, 0, 0, 0, nullptr};
+const kde_opts kDefaultOpts = {0, 0, 0, 0, 0, nullptr, nullptr};
 
 // Bump layout over the index's scratch buffer; with base == nullptr it only
 // counts bytes, so the same carve code sizes and places the buffers.
@@ -383,6 +383,7 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.m = m;
   a.seed = seed;
   a.qid_offset = o->query_id_offset;
+  a.dev_qid = reinterpret_cast<const uint64_t*>(o->dev_query_id_offset);
   a.mode = o->sample_mode;
   a.s1_in = nullptr;
   a.kcount_in = nullptr;

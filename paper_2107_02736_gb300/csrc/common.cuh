@@ -129,6 +129,22 @@ __device__ __forceinline__ float precise_sq_dist(const float* __restrict__ x,
   return hi + lo;
 }
 
+// Plain FP32 difference-form squared distance by G lanes: each lane sums
+// ceil(d/G) squares with FMA, then a log2(G)-level tree.  Relative error at
+// most (ceil(d/G) + log2(G) + 2) units of 2^-24.
+template <int G>
+__device__ __forceinline__ float plain_sq_dist(const float* __restrict__ x,
+                                               const float* __restrict__ y, int d,
+                                               int lane_in_group) {
+  float s = 0.f;
+#pragma unroll 4
+  for (int j = lane_in_group; j < d; j += G) {
+    const float t = x[j] - y[j];
+    s = fmaf(t, t, s);
+  }
+  return group_sum<G>(s);
+}
+
 // Same for the L1 distance (Laplacian kernel).
 template <int G>
 __device__ __forceinline__ float precise_l1_dist(const float* __restrict__ x,

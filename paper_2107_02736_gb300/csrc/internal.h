@@ -226,6 +226,7 @@ struct SampleArgs {
   int m;
   uint64_t seed;
   uint64_t qid_offset;
+  const uint64_t* dev_qid;   // optional device-side addition to qid_offset
   int mode;                  // 0 reject, 1 drop
   const float* s1_in;        // precomputed neighbour sums (nullable)
   const int32_t* kcount_in;  // matching k' (nullable)

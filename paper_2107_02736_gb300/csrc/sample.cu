@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   float* ys = reinterpret_cast<float*>(ys4);
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x;
-  const uint64_t qid = a.qid_offset + (uint64_t)q;
+  const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;
   if (k > 0) {
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
   float* gsum = ys + a.dp;
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x;
-  const uint64_t qid = a.qid_offset + (uint64_t)q;
+  const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) {
     ys[j] = a.Y[q * a.dp + j];
     gsum[j] = 0.f;

@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
     }
   }
-  // rescore in difference form (compensated FP32): 8 lanes per candidate, so
-  // each warp has 4 candidate rows in flight
+  // rescore in plain FP32 difference form: 8 lanes per candidate, so each
+  // warp has 4 candidate rows in flight
   {
     const int grp = lane >> 3, lig = lane & 7;
     for (int j0 = warp * 4; j0 < K; j0 += kNW * 4) {
@@ -393,13 +393,59 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
         }
         pos = s_lstart[lo] + (s - s_seg[lo]);
       }
-      const float d2 = precise_sq_dist<8>(a.XL + pos * a.dp, y, a.d, lig);
+      const float d2 = plain_sq_dist<8>(a.XL + pos * a.dp, y, a.d, lig);
       if (valid && lig == 0) sm.key[j] = pack_key(d2, a.perm[pos]);
     }
   }
   __syncthreads();
   block_sort_keys(sm, K);
   const int kk = min(a.k, K);
+  // Only candidates whose plain distance lies within the FP32 error band of
+  // the k-th can be misordered across the k-th place: recompute those with the
+  // compensated distance (relative error a few 2^-24) and re-sort that range.
+  if (kk > 0 && kk < K) {
+    __shared__ int s_lo, s_hi;
+    // four times the plain distance's error bound (ceil(d/8) + 3 + 2 units)
+    const float band_rel = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
+    if (tid == 0) {
+      const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
+      const float band = band_rel * dk;
+      int lo = kk - 1, hi = kk;
+      while (lo > 0 && __uint_as_float((uint32_t)(sm.key[lo - 1] >> 32)) >= dk - band) --lo;
+      while (hi < K && __uint_as_float((uint32_t)(sm.key[hi] >> 32)) <= dk + band) ++hi;
+      s_lo = lo;
+      s_hi = hi;
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    if (hi - lo > 1) {
+      const int grp = lane >> 3, lig = lane & 7;
+      for (int j0 = lo + warp * 4; j0 < hi; j0 += kNW * 4) {
+        const int j = j0 + grp;
+        const bool valid = j < hi;
+        const int64_t id = valid ? (int64_t)(sm.key[j] & 0xffffffffu) : 0;
+        const float d2 = precise_sq_dist<8>(a.X + id * a.dp, y, a.d, lig);
+        if (valid && lig == 0) sm.key[j] = pack_key(d2, (int)id);
+      }
+      __syncthreads();
+      if (hi - lo <= 64) {
+        if (tid == 0) {  // a short band (the usual case): insertion sort
+          for (int i = lo + 1; i < hi; ++i) {
+            const unsigned long long v = sm.key[i];
+            int j = i - 1;
+            while (j >= lo && sm.key[j] > v) {
+              sm.key[j + 1] = sm.key[j];
+              --j;
+            }
+            sm.key[j + 1] = v;
+          }
+        }
+        __syncthreads();
+      } else {
+        block_sort_keys(sm, K);  // many near-equal distances: sort everything again
+      }
+    }
+  }
   for (int j = tid; j < a.k; j += kNT) {
     if (j < kk) {
       a.nbr[q * a.k + j] = (int32_t)(sm.key[j] & 0xffffffffu);

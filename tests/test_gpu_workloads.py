@@ -171,3 +171,22 @@ def test_unit_powerlaw_uneven_batches(pkg):
         v = oracle.deann(X, Y[q:q + 1], "exponential", h, nbr[q:q + 1], 2000, 9,
                          qid_offset=int(q))
         assert_kde_close(whole[q:q + 1], v)
+
+
+def test_graph_replays_serve_uneven_batches(pkg):
+    """Batches of uneven size served by CUDA-graph replays (one graph per
+    power-of-two capacity) give exactly the direct calls' results, each batch
+    on its own sample streams (query ids continue across batches)."""
+    X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=1_500, n_centres=100)
+    index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=64, seed=5)
+    sizes = workloads.uneven_batches(total=1_500, nbatch=9, lo=16, hi=600, seed=3)
+    server = pkg.BatchServer(index, 100, 1000, nprobe=4, seed=11, precision=1, max_batch=1024)
+    Yd = _dev(Y)
+    start = 0
+    for b in sizes:
+        got = server(Yd[start:start + b]).clone()
+        want = index.query(Yd[start:start + b], 100, 1000, nprobe=4, seed=11, precision=1,
+                           qid_offset=start)
+        assert torch.equal(got, want), b
+        start += int(b)
+    assert len(server.graphs) >= 3
