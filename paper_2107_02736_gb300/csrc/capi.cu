@@ -285,8 +285,11 @@ kde_status stage_queries(kde_index* ix, const float* Y, int64_t nq, bool host, C
 }
 
 // IVF search on staged queries: neighbours, optional squared distances and s1.
+// ids_only: the caller needs the neighbour set in any order (and s1), not
+// the sorted list with distances; the selection then skips the full sort.
 kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int P, int precision,
-                      int32_t* nbr, float* nd2, float* s1, cudaStream_t st) {
+                      int32_t* nbr, float* nd2, float* s1, cudaStream_t st,
+                      bool ids_only = false) {
   const SearchBufs& s = cb.search;
   const int L = ix->nlist;
   const int margin = select_margin(k, precision);
@@ -360,6 +363,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.probe_d2 = s.probe_d2;
     a.rad = ix->rad;
     a.centered = tcore ? 1 : 0;
+    a.ids_only = ids_only && nd2 == nullptr ? 1 : 0;
     a.err = ix->err;
     launch_select_neighbors(a, st);
   }
@@ -768,7 +772,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   TRY(prepare_call(ix, c, cb));
   TRY(stage_queries(ix, Y, nq, host, cb, st));
   int32_t* nb = (k > 0) ? ((host || nbr == nullptr) ? cb.nbr : nbr) : nullptr;
-  if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st));
+  if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st, true));
   SampleArgs a = sample_args(ix, cb, nq, nb, k, m, seed, o);
   a.s1_in = k > 0 ? cb.s1 : nullptr;
   a.out = host ? cb.out : out;
@@ -1016,7 +1020,8 @@ kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, in
       launch_query_norms(cb.Yp, nq, ix->dp, cb.Yn, st);
     }
     // X_1 and S are redrawn at every step: the step's seed is seed + step
-    if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, cb.nbr, nullptr, nullptr, st));
+    if (k > 0)
+      TRY(run_search(ix, cb, nq, k, nprobe, o->precision, cb.nbr, nullptr, nullptr, st, true));
     SampleArgs a = sample_args(ix, cb, nq, k > 0 ? cb.nbr : nullptr, k, m, seed + (uint64_t)s, o);
     a.rs = k == 0 ? 1 : 0;
     a.out = cb.out;

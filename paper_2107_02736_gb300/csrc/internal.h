@@ -208,6 +208,7 @@ struct SelectArgs {
   const float* probe_d2;     // [nq x P]
   const float* rad;          // [nlist]
   int centered;
+  int ids_only;              // 1: the neighbour set in any order (+ s1); no nd2
   uint32_t* err;
 };
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s);

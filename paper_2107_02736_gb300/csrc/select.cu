@@ -182,6 +182,150 @@ __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uin
   return base;
 }
 
+// Brackets the k-th smallest of the nonnegative vals[0..cnt) (1 <= k <= cnt)
+// with two passes: the minimum and maximum, then a 4096-bin histogram on the
+// linear scale between them.  Returns lo <= (k-th smallest) <= hi, the bounds
+// of the bin that holds it, widened by a few units of rounding.
+__device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, int k,
+                                  SelectSmem& sm, float& lo_out, float& hi_out) {
+  constexpr int kBins = 4096;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float s_mn[kNW], s_mx[kNW];
+  __shared__ int s_scan[kNW];
+  __shared__ float s_lo, s_hi;
+  int* hist = reinterpret_cast<int*>(sm.key);  // 16 KiB, free until rescoring
+  float mn = __int_as_float(0x7f800000), mx = 0.f;
+  for (int64_t i0 = tid; i0 < cnt; i0 += 4 * kNT) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * kNT;
+      if (i < cnt) {
+        const float v = vals[i];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    s_mn[warp] = mn;
+    s_mx[warp] = mx;
+  }
+  for (int b = tid; b < kBins; b += kNT) hist[b] = 0;
+  __syncthreads();
+  mn = s_mn[0];
+  mx = s_mx[0];
+  for (int w = 1; w < kNW; ++w) {
+    mn = fminf(mn, s_mn[w]);
+    mx = fmaxf(mx, s_mx[w]);
+  }
+  const float scale = mx > mn ? (float)kBins / (mx - mn) : 0.f;
+  for (int64_t i0 = tid; i0 < cnt; i0 += 4 * kNT) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * kNT;
+      if (i < cnt) {
+        const int bin = min(kBins - 1, max(0, (int)((vals[i] - mn) * scale)));
+        atomicAdd(&hist[bin], 1);
+      }
+    }
+  }
+  __syncthreads();
+  // thread t owns bins [16 t, 16 t + 16)
+  constexpr int kPer = kBins / kNT;
+  int c[kPer], s = 0;
+#pragma unroll
+  for (int b = 0; b < kPer; ++b) {
+    c[b] = hist[tid * kPer + b];
+    s += c[b];
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_scan[warp] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += s_scan[w];
+  incl += before;
+  const int excl = incl - s;
+  if (excl < k && k <= incl) {
+    int run = excl, bin = tid * kPer;
+#pragma unroll
+    for (int b = 0; b < kPer; ++b) {
+      if (run < k && k <= run + c[b]) bin = tid * kPer + b;
+      run += c[b];
+    }
+    if (scale > 0.f) {
+      const float lo = mn + (float)bin / scale, hi = mn + (float)(bin + 1) / scale;
+      s_lo = fmaxf(0.f, lo - fabsf(lo) * 1e-6f - 1e-30f);
+      s_hi = hi + fabsf(hi) * 1e-6f + 1e-30f;
+    } else {
+      s_lo = mn;
+      s_hi = mx;
+    }
+  }
+  __syncthreads();
+  lo_out = s_lo;
+  hi_out = s_hi;
+}
+
+// k-th smallest distance key (upper 32 bits) among sm.key[0..K), 1 <= k <= K,
+// by four 8-bit radix passes over shared memory.
+__device__ uint32_t smem_kth_dist(SelectSmem& sm, int K, int k) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t prefix = 0, pmask = 0;
+  int want = k;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int i = tid; i < 256; i += kNT) sm.hist[i] = 0;
+    __syncthreads();
+    for (int j = tid; j < K; j += kNT) {
+      const uint32_t key = (uint32_t)(sm.key[j] >> 32);
+      if ((key & pmask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 255], 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int c[8], s = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        c[b] = sm.hist[lane * 8 + b];
+        s += c[b];
+      }
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int excl = incl - s;
+      if (excl < want && want <= incl) {
+        int run = excl;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          if (run < want && want <= run + c[b]) {
+            sm.digit = lane * 8 + b;
+            sm.before = run;
+          }
+          run += c[b];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (uint32_t)sm.digit << shift;
+    pmask |= 255u << shift;
+    want -= sm.before;
+    __syncthreads();
+  }
+  return prefix;
+}
+
 // Bitonic sort of sm.key[0..cnt) ascending (cnt padded to a power of two
 // with all-ones keys).
 __device__ void block_sort_keys(SelectSmem& sm, int cnt) {
@@ -364,8 +508,9 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     for (int i = tid; i < K; i += kNT) sm.slot[i] = i;
     __syncthreads();
   } else {
-    const uint32_t tk = block_select(vals, cnt, a.k, sm, false);
-    const uint32_t thr = dist_key(__uint_as_float(tk) + 2.f * s_E);
+    float tk_lo, tk_hi;  // t_k lies in [tk_lo, tk_hi]
+    block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi);
+    const uint32_t thr = dist_key(tk_hi + 2.f * s_E);
     K = block_collect_le(vals, cnt, thr, kSelectCap, sm);
     if (K > kSelectCap) {
       block_select(vals, cnt, kSelectCap, sm);
@@ -398,6 +543,95 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     }
   }
   __syncthreads();
+  if (a.ids_only && K > a.k && a.kern != KDE_KERN_LAPLACIAN) {
+    // The query path needs the set and s1, not the order: find the k-th
+    // smallest rescored distance T, take every candidate clearly below it,
+    // and rank only those within the FP32 error band of T by compensated
+    // distance.
+    const int k = a.k;
+    const float T = __uint_as_float(smem_kth_dist(sm, K, k));
+    const float bw = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T;
+    const uint32_t lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
+    const uint32_t hi_key = dist_key(T + bw);
+    unsigned long long* amb = reinterpret_cast<unsigned long long*>(sm.slot);  // 1024 keys
+    const float inv = kernel_inv(a.kern, a.h);
+    int c_in = 0, n_amb = 0;
+    float part = 0.f;
+    const unsigned below = (1u << lane) - 1u;
+    for (int j0 = 0; j0 < K; j0 += kNT) {
+      const int j = j0 + tid;
+      const unsigned long long key = j < K ? sm.key[j] : ~0ull;
+      const uint32_t dk = (uint32_t)(key >> 32);
+      const bool cert = j < K && dk < lo_key;
+      const bool ambi = j < K && dk >= lo_key && dk <= hi_key;
+      const unsigned mc = __ballot_sync(0xffffffffu, cert), ma = __ballot_sync(0xffffffffu, ambi);
+      if (lane == 0) {
+        sm.warp_a[warp] = __popc(mc);
+        sm.warp_b[warp] = __popc(ma);
+      }
+      __syncthreads();
+      int oc = c_in, oa = n_amb, tc = 0, ta = 0;
+      for (int w = 0; w < kNW; ++w) {
+        if (w < warp) {
+          oc += sm.warp_a[w];
+          oa += sm.warp_b[w];
+        }
+        tc += sm.warp_a[w];
+        ta += sm.warp_b[w];
+      }
+      if (cert) {
+        a.nbr[q * k + oc + __popc(mc & below)] = (int32_t)(key & 0xffffffffu);
+        part += kernel_from_dist(a.kern, __uint_as_float(dk), inv);
+      }
+      if (ambi) {
+        const int r = oa + __popc(ma & below);
+        if (r < 1024) amb[r] = key;
+      }
+      c_in += tc;
+      n_amb += ta;
+      __syncthreads();
+    }
+    const int need = k - c_in;  // 1 <= need <= n_amb
+    if (n_amb <= 1024) {
+      // compensated distances for the ambiguous candidates, then their order
+      const int grp = lane >> 3, lig = lane & 7;
+      for (int j0 = warp * 4; j0 < n_amb; j0 += kNW * 4) {
+        const int j = j0 + grp;
+        const bool valid = j < n_amb;
+        const int64_t id = valid ? (int64_t)(amb[j] & 0xffffffffu) : 0;
+        const float d2 = precise_sq_dist<8>(a.X + id * a.dp, y, a.d, lig);
+        if (valid && lig == 0) amb[j] = pack_key(d2, (int)id);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int i = 1; i < n_amb; ++i) {  // short in practice: insertion sort
+          const unsigned long long v = amb[i];
+          int j = i - 1;
+          while (j >= 0 && amb[j] > v) {
+            amb[j + 1] = amb[j];
+            --j;
+          }
+          amb[j + 1] = v;
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < need; j += kNT) {
+        a.nbr[q * k + c_in + j] = (int32_t)(amb[j] & 0xffffffffu);
+        part += kernel_from_dist(a.kern, __uint_as_float((uint32_t)(amb[j] >> 32)), inv);
+      }
+      part = warp_sum(part);
+      if (lane == 0) s_red[warp] = part;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kNW; ++w) t += s_red[w];
+        if (a.s1) a.s1[q] = t;
+      }
+      return;
+    }
+    // a very wide ambiguous band (many equal distances): fall through to the
+    // full sort below, which rewrites the whole output
+  }
   block_sort_keys(sm, K);
   const int kk = min(a.k, K);
   // Only candidates whose plain distance lies within the FP32 error band of
