@@ -84,6 +84,8 @@ def _load():
         lib.or_deann_grad.restype = i32
         lib.or_deannp.argtypes = [P, i64, i32, P, i64, i32, f64, P, P, i32, i32, i64, P, P]
         lib.or_deannp.restype = i32
+        lib.or_feistel_perm.argtypes = [u64, i64, i64]
+        lib.or_feistel_perm.restype = i64
         _lib = lib
         return lib
 
@@ -237,8 +239,18 @@ def deann_grad(X, Y, kernel, h, nbr, m, seed, qid_offset=0, gout=None):
     return out, dY, dl
 
 
+def feistel_perm(seed: int, n: int, idx=None):
+    """The keyed permutation of [0, n) used as Algorithm 2's random
+    permutation (Feistel network with cycle walking); returns pi(idx) for the
+    given indices (all of [0, n) by default) as int32."""
+    lib = _load()
+    idx = range(n) if idx is None else idx
+    return np.array([lib.or_feistel_perm(seed, n, int(i)) for i in idx], dtype=np.int32)
+
+
 def deannp(X, Y, kernel, h, perm, nbr, m, ell0=0):
-    """DEANNP: DEANN with permuted random sampling (Algorithm 2)."""
+    """DEANNP: DEANN with permuted random sampling (Algorithm 2): query q uses
+    the window perm[(ell0 + q m + t) mod n], t < m, minus the members of X_1."""
     X, Y, perm = _f32(X), _f32(Y), _i32(perm)
     nq = Y.shape[0]
     if nbr is None:

@@ -513,47 +513,79 @@ int or_deann_grad(const float* X, int64_t n, int d, const float* Y, int64_t nq,
  * Sampling"): given the permutation pi and the running index ell, the sample
  * of a query is the window x'_{ell}, ..., x'_{ell+m-1} (indices mod n) of the
  * permuted dataset x'_i = x_{pi(i)}; ell then advances by m mod n.  Queries are
- * served in order, so query q starts at (ell0 + q m) mod n.  DEANNP combines
- * it with the neighbour set: window entries that fall in X_1 are skipped and
- * the window extends past them until m points of X \ X_1 are taken (at most
- * n - k' distinct ones, so m <= n - k' is required); ell advances by the
- * window length.  Both variants return (1/n)[s1 + ((n-k')/m) s2].
+ * served in order, so query q's window starts at (ell0 + q m) mod n.
+ * DEANNP combines it with the neighbour set: window entries that fall in X_1
+ * are dropped and the window's sum is normalised by the m' entries of
+ * X \ X_1 it holds, out = (1/n)[s1 + ((n - k')/m') s2] (s1/n when m' = 0).
+ * Given m', the kept entries are a uniform m'-subset of X \ X_1 for a random
+ * permutation, so the estimate is unbiased.  Requires m <= n.
  * ell_out (nullable) receives the running index after the last query.
  * ---------------------------------------------------------------------- */
 int or_deannp(const float* X, int64_t n, int d, const float* Y, int64_t nq,
               int kern, double h, const int32_t* perm, const int32_t* nbr,
               int k, int m, int64_t ell0, double* out, int64_t* ell_out) {
-  int64_t ell = ell0 % n;
+  if (n <= 0) return OR_EINVAL;
+  int64_t ell = ((ell0 % n) + n) % n;
   int64_t* set = (int64_t*)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
   int status = OR_OK;
-  for (int64_t q = 0; q < nq; ++q) {
+  if (m < 0 || (int64_t)m > n) status = OR_EINVAL;
+  for (int64_t q = 0; q < nq && status == OR_OK; ++q) {
     const float* y = Y + q * (int64_t)d;
     int kk = distinct_neighbours(nbr ? nbr + q * (int64_t)k : NULL, nbr ? k : 0,
                                  n, set);
-    if (kk < 0 || (m > 0 && (int64_t)m > n - kk)) {
+    if (kk < 0) {
       status = OR_EINVAL;
       out[q] = NAN;
-      continue;
+      break;
     }
     double s1 = 0.0;
     for (int t = 0; t < kk; ++t)
       s1 += or_kernel_value(kern, X + set[t] * (int64_t)d, y, d, h);
-    if ((int64_t)kk == n || m == 0) {
-      out[q] = s1 / (double)n;
-      continue;
-    }
     double s2 = 0.0;
-    int taken = 0;
-    while (taken < m) {
-      int64_t id = perm[ell];
-      ell = (ell + 1) % n;
-      if (in_set(set, kk, id)) continue;
-      s2 += or_kernel_value(kern, X + id * (int64_t)d, y, d, h);
-      ++taken;
+    int64_t kept = 0;
+    if ((int64_t)kk < n) {
+      for (int t = 0; t < m; ++t) {
+        int64_t id = perm[(ell + t) % n];
+        if (in_set(set, kk, id)) continue;
+        s2 += or_kernel_value(kern, X + id * (int64_t)d, y, d, h);
+        ++kept;
+      }
     }
-    out[q] = (s1 + ((double)(n - kk) / (double)m) * s2) / (double)n;
+    out[q] = kept > 0 ? (s1 + ((double)(n - kk) / (double)kept) * s2) / (double)n
+                      : s1 / (double)n;
+    ell = (ell + m) % n;
   }
   free(set);
   if (ell_out) *ell_out = ell;
   return status;
+}
+
+/* Keyed pseudo-random permutation of [0, n) drawn for Algorithm 2's
+ * preprocessing: a 4-round balanced Feistel network on 2h bits (h = half the
+ * bit length of n - 1, rounded up) whose round function is Philox4x32-10
+ * (counter (R, round, 0, 3), key (lo32(seed), hi32(seed)), output word r0),
+ * made into a permutation of [0, n) by cycle walking (Black, Rogaway,
+ * "Ciphers with Arbitrary Finite Domains", CT-RSA 2002): re-apply the network
+ * until the value falls below n. */
+int64_t or_feistel_perm(uint64_t seed, int64_t n, int64_t i) {
+  int bits = 1;
+  while (bits < 62 && ((int64_t)1 << bits) < n) ++bits;
+  const int hb = (bits + 1) / 2;
+  const uint64_t mask = ((uint64_t)1 << hb) - 1;
+  uint64_t x = (uint64_t)i;
+  do {
+    uint64_t L = x >> hb, R = x & mask;
+    for (uint32_t r = 0; r < 4; ++r) {
+      uint32_t ctr[4] = {(uint32_t)R, r, 0u, 3u};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      uint32_t o[4];
+      or_philox4x32_10(ctr, key, o);
+      uint64_t F = (uint64_t)o[0] & mask;
+      uint64_t nL = R, nR = L ^ F;
+      L = nL;
+      R = nR;
+    }
+    x = (L << hb) | R;
+  } while ((int64_t)x >= n);
+  return (int64_t)x;
 }

@@ -423,13 +423,65 @@ def test_exact_gradient_symmetry_and_fd():
 
 # ----------------------------------------------------------- DEANNP / RSP ---
 def test_deannp_full_window_is_exact():
-    """m = n - k': the window covers X \\ X_1 exactly once, so DEANNP returns
-    the exact KDE for any permutation and starting index."""
+    """m = n: the window covers every point once; the members of X_1 are
+    dropped, so m' = n - k' and DEANNP returns the exact KDE for any
+    permutation and starting index."""
     X, Y = _small_problem(n=90)
     nbr, _ = oracle.knn(X, Y, 12)
     perm = np.random.default_rng(1).permutation(90).astype(np.int32)
-    out, _ = oracle.deannp(X, Y, "gaussian", 0.8, perm, nbr, m=90 - 12, ell0=37)
+    out, ell = oracle.deannp(X, Y, "gaussian", 0.8, perm, nbr, m=90, ell0=37)
+    assert ell == 37
     assert np.allclose(out, oracle.exact(X, Y, "gaussian", 0.8), rtol=1e-13)
+
+
+def test_deannp_unbiased_over_all_permutations():
+    """Brute force over every permutation of a 6-point dataset: with m > k'
+    the window always keeps a point, and the mean of the DEANNP estimate over
+    the uniform permutation is the exact KDE (each kept window is a uniform
+    sample without replacement from X minus X_1)."""
+    import itertools
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((6, 2)).astype(np.float32)
+    Y = rng.standard_normal((1, 2)).astype(np.float32)
+    nbr = np.array([[4, 1]], np.int32)
+    vals = []
+    for p in itertools.permutations(range(6)):
+        out, _ = oracle.deannp(X, Y, "gaussian", 0.9, np.array(p, np.int32), nbr,
+                               m=3, ell0=2)
+        vals.append(out[0])
+    assert math.isclose(np.mean(vals), oracle.exact(X, Y, "gaussian", 0.9)[0],
+                        rel_tol=1e-12)
+    # and the estimator is not trivially exact on each permutation
+    assert np.std(vals) > 1e-3 * np.mean(vals)
+
+
+def test_deannp_rejects_window_longer_than_n():
+    X, Y = _small_problem(n=30, nq=2)
+    perm = np.arange(30, dtype=np.int32)
+    with pytest.raises(Exception):
+        oracle.deannp(X, Y, "gaussian", 0.8, perm, None, m=31)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 100, 1000, 4097, 65536])
+def test_feistel_perm_is_a_bijection(n):
+    """The keyed Feistel permutation with cycle walking maps [0, n) onto
+    itself one-to-one for any n, and different keys give different orders."""
+    a = oracle.feistel_perm(11, n)
+    assert a.min() >= 0 and a.max() < n
+    assert np.array_equal(np.sort(a), np.arange(n))
+    if n >= 100:
+        b = oracle.feistel_perm(12, n)
+        assert not np.array_equal(a, b)
+        assert not np.array_equal(a, np.arange(n))
+
+
+def test_feistel_perm_is_roughly_uniform():
+    """Position of element 0 across keys is spread over [0, n) (a chi-square
+    test on 8 bins over 4000 keys, n = 64)."""
+    pos = np.array([np.where(oracle.feistel_perm(s, 64) == 0)[0][0] for s in range(4000)])
+    counts = np.bincount(pos // 8, minlength=8)
+    chi2 = ((counts - 500.0) ** 2 / 500.0).sum()
+    assert chi2 < 30.0  # 7 dof: p ~ 1e-4
 
 
 def test_rsp_consecutive_windows_cover_dataset():
