@@ -72,7 +72,10 @@ typedef enum {
 
 typedef struct {
   int32_t precision;        /* kde_precision of the scan (kde_query, kde_search) */
-  int32_t sample_mode;      /* 0: reject draws in X_1 (default); 1: "drop" */
+  int32_t sample_mode;      /* 0: reject draws in X_1 (default); 1: "drop";
+                               2: permuted window (Algorithm 2, DEANNP /
+                               RSP): needs kde_prepare_permuted and m <= n;
+                               not for the adjoint or mean shift */
   int32_t kmeans_iters;     /* kde_build: Lloyd iterations (0 = 20) */
   int32_t exact_path;       /* kde_exact: 0 = automatic (tensor cores when
                                the accuracy guard below allows, else CUDA
@@ -106,6 +109,23 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
 /* kde_free -- release the index and all device memory it owns (NULL is a
  * no-op).  Synchronises the device first. */
 void kde_free(kde_index* index);
+
+/* kde_prepare_permuted -- Algorithm 2's preprocessing: a random permutation
+ * pi of [0, n) and the permuted copy XP[i] = X[pi(i)] (n x d FP32 more device
+ * memory), which opts.sample_mode = 2 reads.  pi is a 4-round Feistel network
+ * on 2 hb bits (hb = ceil(b / 2), b the bit length of n - 1, at least 1),
+ * round r (0..3) mapping (L, R) to (R, L xor F_r(R)) with F_r(R) the low hb bits
+ * of word r0 of Philox4x32-10 at counter (R, r, 0, 3) and key (lo32(seed),
+ * hi32(seed)) of the build seed, x = (L << hb) | R; values >= n are enciphered
+ * again until they fall below n (cycle walking).
+ * Permuted mode: the query with global id qid (see kde_opts) reads the m
+ * consecutive rows of XP from ell = (qid m) mod n, wrapping at n (the running
+ * index of Algorithm 2, advanced by m per query); entries in X_1 are dropped
+ * and the m' kept ones give out = (1/n) [ sum_{X_1} K + ((n - k')/m') sum K ]
+ * (sum_{X_1} K / n when m' = 0); with k = 0 (kde_query_rs) it is RSP.
+ *   perm_out  NULL, or n int32 (host or device) receiving pi(0..n-1).
+ * Idempotent (the permutation is built once).  Errors: ENOMEM, ECUDA. */
+kde_status kde_prepare_permuted(kde_index* index, int32_t* perm_out, const kde_opts* opts);
 
 /* kde_set_bandwidth -- replace h (> 0, finite).  The IVF does not depend on h. */
 kde_status kde_set_bandwidth(kde_index* index, float h);
@@ -154,7 +174,8 @@ kde_status kde_query_with_neighbors(kde_index* index, const float* Y, int64_t nq
 
 /* kde_query_rs -- random sampling (Lemma RS): m >= 1 draws uniform on X with
  * repetition (the first m draws of each query's stream), out = mean kernel
- * value. */
+ * value; with opts.sample_mode = 2, RSP (Algorithm 2): the mean over the
+ * query's permuted window. */
 kde_status kde_query_rs(kde_index* index, const float* Y, int64_t nq, int32_t m, uint64_t seed,
                         float* out, const kde_opts* opts);
 
@@ -177,8 +198,9 @@ kde_status kde_exact(kde_index* index, const float* Y, int64_t nq, float* out,
 
 /* kde_sample_indices -- the sample S that kde_query_with_neighbors uses for
  * each query (nq x m original ids): the accepted draws in draw order
- * (sample_mode 0) or the raw draws (sample_mode 1).  Rows with no sampling
- * (k' = n or m = 0) are filled with -1. */
+ * (sample_mode 0), the raw draws (sample_mode 1), or the window's ids in
+ * window order with -1 for the dropped members of X_1 (sample_mode 2).  Rows
+ * with no sampling (k' = n or m = 0) are filled with -1. */
 kde_status kde_sample_indices(kde_index* index, int64_t nq, const int32_t* nbr, int32_t k,
                               int32_t m, uint64_t seed, int32_t* samples, const kde_opts* opts);
 

@@ -88,6 +88,7 @@ def load_library():
         "kde_sync": [P, O],
         "kde_stats": [P, P, O],
         "kde_reserve": [P, i64, i32, i32, i32, O],
+        "kde_prepare_permuted": [P, P, O],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +210,16 @@ class KDEIndex:
             _check(_lib.kde_export_ivf(self._h, _ptr(C), _ptr(a)))
         return C, a
 
+    def prepare_permuted(self, return_perm=False):
+        """Algorithm 2's preprocessing (random permutation pi and the
+        permuted dataset copy) for sample_mode=2; returns pi as an int32 CUDA
+        tensor when asked."""
+        perm = (torch.empty(self.n, dtype=torch.int32, device=self._device)
+                if return_perm else None)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_prepare_permuted(self._h, _ptr(perm), ctypes.byref(self._opts())))
+        return perm
+
     def sync(self):
         with torch.cuda.device(self._device):
             _check(_lib.kde_sync(self._h, ctypes.byref(self._opts())))
@@ -288,14 +299,15 @@ class KDEIndex:
                 ctypes.byref(self._opts(0, sample_mode, qid_offset, host=not Y.is_cuda))))
         return out
 
-    def query_rs(self, Y, m, seed=0, qid_offset=0):
+    def query_rs(self, Y, m, seed=0, qid_offset=0, sample_mode=0):
+        """Random sampling; sample_mode=2 gives RSP (Algorithm 2)."""
         Y = self._prep(Y)
         nq = Y.shape[0]
         out = torch.empty(nq, dtype=torch.float32, device=Y.device)
         with torch.cuda.device(self._device):
             _check(_lib.kde_query_rs(self._h, _ptr(Y), nq, int(m), int(seed) & (2**64 - 1),
                                      _ptr(out), ctypes.byref(self._opts(
-                                         0, 0, qid_offset, host=not Y.is_cuda))))
+                                         0, sample_mode, qid_offset, host=not Y.is_cuda))))
         return out
 
     def exact(self, Y, path="auto"):
@@ -376,16 +388,19 @@ class GraphedQuery:
     keep stale values; their outputs are discarded) and the batch's first
     query id is written to a device scalar that the estimator reads, so every
     replay draws the sample streams the direct call with that qid_offset
-    would draw.
+    would draw (with sample_mode=2, the permuted windows of Algorithm 2 that
+    follow on from the previous batch's).
     """
 
-    def __init__(self, index: KDEIndex, capacity, k, m, nprobe=1, seed=0, precision=0):
+    def __init__(self, index: KDEIndex, capacity, k, m, nprobe=1, seed=0, precision=0,
+                 sample_mode=0):
         self.index, self.capacity = index, int(capacity)
         dev = index.device
         self.Y = torch.zeros((self.capacity, index.d), dtype=torch.float32, device=dev)
         self.qid = torch.zeros(1, dtype=torch.int64, device=dev)
         index.reserve(self.capacity, k, m, nprobe)
-        args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision, dev_qid=self.qid)
+        args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision,
+                    sample_mode=sample_mode, dev_qid=self.qid)
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):  # first launches (module loading) outside the capture
@@ -410,9 +425,10 @@ class BatchServer:
     """Serves uneven batches with CUDA graphs captured per power-of-two
     capacity class (16 ... max_batch); the query ids run on across batches."""
 
-    def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192):
+    def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192,
+                 sample_mode=0):
         self.index, self.args = index, dict(k=k, m=m, nprobe=nprobe, seed=seed,
-                                            precision=precision)
+                                            precision=precision, sample_mode=sample_mode)
         self.max_batch = int(max_batch)
         self.graphs = {}
         self.next_qid = 0

@@ -368,6 +368,48 @@ __global__ void k_max_f32(const float* __restrict__ v, int64_t n, unsigned* __re
 }
 }  // namespace
 
+namespace {
+// Algorithm 2's preprocessing permutation pi of [0, n): a 4-round balanced
+// Feistel network on 2 hb bits (2^(2 hb) >= n) keyed by the index seed, its
+// round function the word r0 of Philox4x32-10 at counter (R, round, 0, 3);
+// values >= n are re-enciphered until they fall in [0, n) (cycle walking,
+// Black and Rogaway, CT-RSA 2002).  The walk stays on the cycle of i under a
+// bijection of [0, 2^(2 hb)), which contains i < n, so it ends after fewer
+// than 2^(2 hb) - n + 2 passes (expected at most 4).
+__device__ __forceinline__ uint32_t feistel_once(uint32_t x, int hb, uint32_t mask,
+                                                 uint64_t seed) {
+  uint32_t L = x >> hb, R = x & mask;
+#pragma unroll
+  for (uint32_t r = 0; r < 4; ++r) {
+    const uint4 o = Philox::block(make_uint4(R, r, 0u, 3u), (uint32_t)seed,
+                                  (uint32_t)(seed >> 32));
+    const uint32_t nR = L ^ (o.x & mask);
+    L = R;
+    R = nR;
+  }
+  return (L << hb) | R;
+}
+
+__global__ void k_feistel_perm(uint64_t seed, int64_t n, int hb, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t mask = (1u << hb) - 1u;
+  uint32_t x = (uint32_t)i;
+  do {
+    x = feistel_once(x, hb, mask, seed);
+  } while ((int64_t)x >= n);
+  out[i] = (int32_t)x;
+}
+}  // namespace
+
+void launch_feistel_perm(uint64_t seed, int64_t n, int32_t* out, cudaStream_t s) {
+  if (n <= 0) return;
+  int bits = 1;
+  while (((int64_t)1 << bits) < n) ++bits;  // n < 2^31, so bits <= 31 and 2 hb <= 32
+  const int hb = (bits + 1) / 2;
+  k_feistel_perm<<<grid_for(n, 256), 256, 0, s>>>(seed, n, hb, out);
+}
+
 void launch_max_f32(const float* v, int64_t n, float* out, cudaStream_t s) {
   cudaMemsetAsync(out, 0, sizeof(float), s);
   k_max_f32<<<grid_for(n, 256), 256, 0, s>>>(v, n, reinterpret_cast<unsigned*>(out));

@@ -389,6 +389,8 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.qid_offset = o->query_id_offset;
   a.dev_qid = reinterpret_cast<const uint64_t*>(o->dev_query_id_offset);
   a.mode = o->sample_mode;
+  a.XP = ix->XP;
+  a.wperm = ix->wperm;
   a.s1_in = nullptr;
   a.kcount_in = nullptr;
   a.out = nullptr;
@@ -409,8 +411,8 @@ kde_status check_index(const kde_index* ix) {
 kde_status check_opts(const kde_opts* o) {
   if (o->precision != KDE_PREC_FP32 && o->precision != KDE_PREC_BF16)
     return fail(KDE_EINVAL, "precision must be 0 (FP32) or 1 (BF16)");
-  if (o->sample_mode != 0 && o->sample_mode != 1)
-    return fail(KDE_EINVAL, "sample_mode must be 0 or 1");
+  if (o->sample_mode < 0 || o->sample_mode > 2)
+    return fail(KDE_EINVAL, "sample_mode must be 0 (reject), 1 (drop) or 2 (permuted window)");
   if (o->exact_path < 0 || o->exact_path > 2)
     return fail(KDE_EINVAL, "exact_path must be 0 (auto), 1 (CUDA cores) or 2 (tensor cores)");
   return KDE_OK;
@@ -651,6 +653,8 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->xsn);
   cudaFree(ix->err);
   cudaFree(ix->xmax_d);
+  cudaFree(ix->wperm);
+  cudaFree(ix->XP);
   if (ix->scratch.base) cudaFree(ix->scratch.base);
   for (const auto& e : ix->events) {
     cudaEventDestroy(e.a);
@@ -658,6 +662,35 @@ void kde_free(kde_index* ix) {
   }
   delete[] ix->h_list_off;
   delete ix;
+}
+
+kde_status kde_prepare_permuted(kde_index* ix, int32_t* perm_out, const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  DeviceGuard g(ix->device);
+  cudaStream_t st = stream_of(o);
+  if (ix->wperm == nullptr) {
+    int32_t* wp = nullptr;
+    float* xp = nullptr;
+    TRY(dev_alloc(&wp, (size_t)ix->n));
+    if (dev_alloc(&xp, (size_t)ix->n * ix->dp) != KDE_OK) {
+      cudaFree(wp);
+      return fail(KDE_ENOMEM, "no room for the permuted dataset copy (%lld x %d floats)",
+                  (long long)ix->n, ix->dp);
+    }
+    launch_feistel_perm(ix->seed, ix->n, wp, st);
+    launch_gather_rows(ix->X, ix->dp, wp, ix->n, xp, st);
+    CK(cudaGetLastError());
+    ix->wperm = wp;
+    ix->XP = xp;
+  }
+  if (perm_out == nullptr) return KDE_OK;
+  const Space sp = space_of(perm_out, ix->device);
+  if (sp == SPACE_FOREIGN) return fail(KDE_ESTATE, "perm_out lives on another device");
+  const bool host = sp == SPACE_HOST;
+  TRY(copy_out(perm_out, ix->wperm, sizeof(int32_t) * ix->n, host, st));
+  return finish_call(ix, host, st);
 }
 
 kde_status kde_set_bandwidth(kde_index* ix, float h) {
@@ -732,11 +765,17 @@ kde_status kde_search(kde_index* ix, const float* Y, int64_t nq, int32_t k, int3
   return finish_call(ix, host, st);
 }
 
-static kde_status check_est_args(const kde_index* ix, int64_t nq, int32_t k, int32_t m) {
+static kde_status check_est_args(const kde_index* ix, int64_t nq, int32_t k, int32_t m,
+                                 const kde_opts* o) {
   if (nq < 0 || nq > INT32_MAX) return fail(KDE_EINVAL, "nq must be in [0, 2^31 - 1]");
   if (k < 0 || k > kMaxK) return fail(KDE_EINVAL, "k must be in [0, %d]", kMaxK);
   if (m < 0) return fail(KDE_EINVAL, "m must be >= 0");
   if ((int64_t)m * 64 + 4096 > INT32_MAX) return fail(KDE_EINVAL, "m too large");
+  if (o->sample_mode == 2) {
+    if (ix->wperm == nullptr || ix->XP == nullptr)
+      return fail(KDE_ESTATE, "sample_mode 2 needs kde_prepare_permuted on the index first");
+    if ((int64_t)m > ix->n) return fail(KDE_EINVAL, "sample_mode 2 needs m <= n");
+  }
   return KDE_OK;
 }
 
@@ -746,7 +785,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));
-  TRY(check_est_args(ix, nq, k, m));
+  TRY(check_est_args(ix, nq, k, m, o));
   if (k > 0) {
     TRY(check_search_args(ix, nq, k, nprobe));
   } else if (m < 1) {
@@ -794,7 +833,7 @@ kde_status kde_query_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));
-  TRY(check_est_args(ix, nq, k, m));
+  TRY(check_est_args(ix, nq, k, m, o));
   if (nq == 0) return KDE_OK;
   if (Y == nullptr || out == nullptr || (k > 0 && nbr == nullptr))
     return fail(KDE_EINVAL, "Y, out (and nbr when k > 0) must not be NULL");
@@ -831,8 +870,9 @@ kde_status kde_query_rs(kde_index* ix, const float* Y, int64_t nq, int32_t m, ui
                         float* out, const kde_opts* opts) {
   TRY(check_index(ix));
   if (m < 1) return fail(KDE_EINVAL, "m must be >= 1");
+  TRY(check_opts(opts ? opts : &kDefaultOpts));
   kde_opts o2 = opts ? *opts : kDefaultOpts;
-  o2.sample_mode = 0;
+  if (o2.sample_mode != 2) o2.sample_mode = 0;  // with no X_1, reject = drop = plain RS
   return kde_query_with_neighbors(ix, Y, nq, nullptr, 0, m, seed, out, &o2);
 }
 
@@ -887,7 +927,7 @@ kde_status kde_sample_indices(kde_index* ix, int64_t nq, const int32_t* nbr, int
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));
-  TRY(check_est_args(ix, nq, k, m));
+  TRY(check_est_args(ix, nq, k, m, o));
   if (nq == 0 || m == 0) return KDE_OK;
   if (samples == nullptr || (k > 0 && nbr == nullptr))
     return fail(KDE_EINVAL, "samples (and nbr when k > 0) must not be NULL");
@@ -928,8 +968,9 @@ kde_status kde_grad_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));
-  TRY(check_est_args(ix, nq, k, m));
+  TRY(check_est_args(ix, nq, k, m, o));
   if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
+  if (o->sample_mode == 2) return fail(KDE_EINVAL, "the adjoint supports sample_mode 0 and 1");
   if (nq == 0) return KDE_OK;
   if (Y == nullptr || dY == nullptr || (k > 0 && nbr == nullptr))
     return fail(KDE_EINVAL, "Y, dY (and nbr when k > 0) must not be NULL");
@@ -984,11 +1025,12 @@ kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, in
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));
-  TRY(check_est_args(ix, nq, k, m));
+  TRY(check_est_args(ix, nq, k, m, o));
   if (ix->kern != KDE_KERN_GAUSSIAN)
     return fail(KDE_EINVAL, "mean shift is defined here for the Gaussian kernel");
   if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
   if (steps < 0) return fail(KDE_EINVAL, "steps must be >= 0");
+  if (o->sample_mode == 2) return fail(KDE_EINVAL, "mean shift supports sample_mode 0 and 1");
   if (k > 0) {
     TRY(check_search_args(ix, nq, k, nprobe));
   } else if (m < 1) {

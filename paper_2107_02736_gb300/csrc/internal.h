@@ -88,6 +88,10 @@ struct kde_index {
   alignas(64) unsigned char tmap_xs[128] = {0};
   bool xs_ok = false;
   float xs_max2 = 0.f;        // max |x - mean|^2 (accuracy guard of the tensor-core path)
+  // permuted sampling (Algorithm 2): pi and the dataset in pi order,
+  // XP[i] = X[pi(i)]; built by kde_prepare_permuted
+  int32_t* wperm = nullptr;   // [n] window position -> original id
+  float* XP = nullptr;        // [n x dp]
   uint32_t* err = nullptr;    // device error words [4]
   float* xmax_d = nullptr;    // device max |x|^2
   float xmax = 0.f;           // max |x| over the dataset
@@ -133,6 +137,7 @@ void launch_to_bf16(const float* X, int64_t n, int dp, void* dst, int dpb, cudaS
 void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L, const float* C,
                         void* dst, int dpb, float* xcn, float* rad, cudaStream_t s);
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s);
+void launch_feistel_perm(uint64_t seed, int64_t n, int32_t* out, cudaStream_t s);
 
 // ---- tiles.cu (SIMT distance tiles) ---------------------------------------
 void launch_exact_simt(const float* Y, const float* Yn, int64_t nq, const float* X,
@@ -228,7 +233,9 @@ struct SampleArgs {
   uint64_t seed;
   uint64_t qid_offset;
   const uint64_t* dev_qid;   // optional device-side addition to qid_offset
-  int mode;                  // 0 reject, 1 drop
+  int mode;                  // 0 reject, 1 drop, 2 permuted window (Algorithm 2)
+  const float* XP;           // mode 2: the dataset in pi order
+  const int32_t* wperm;      // mode 2: pi
   const float* s1_in;        // precomputed neighbour sums (nullable)
   const int32_t* kcount_in;  // matching k' (nullable)
   float* out;                // [nq] estimates (nullable)

@@ -17,6 +17,11 @@
 //  5. out = (s1 + ((n - k') / m) s2) / n.
 // "drop" mode (sample_mode 1) instead takes draws 0..m-1 from all of X and
 // gives the ones in X_1 weight zero: out = s1 / n + s2 / m.
+// Permuted mode (sample_mode 2, Algorithm 2) reads the window of m
+// consecutive rows of the permuted dataset XP (XP[i] = X[pi(i)]) starting at
+// ell = (qid m) mod n, wrapping at n; window entries whose id pi(j) is in X_1
+// are dropped and the m' kept ones are normalised by m':
+// out = (s1 + ((n - k') / m') s2) / n (s1 / n when m' = 0).
 #include "common.cuh"
 
 namespace deann {
@@ -155,6 +160,42 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
   return ok;
 }
 
+// Algorithm 2 window, positions t in [t0, t0 + room): row j = (w0 + t) mod n
+// of XP holds original id pi(j) = wperm[j].  Rows whose id is not in X_1 go to
+// sm.S in window order and sm.cnt counts them; srow (nullable) receives
+// pi(j), or -1 for a dropped entry, at its window position t.
+__device__ void window_chunk(const int32_t* __restrict__ wperm, int64_t n, int64_t w0, int t0,
+                             int room, EstSmem& sm, int32_t* srow) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int filled = 0;
+  for (int b0 = 0; b0 < room; b0 += kNT) {
+    const int t = t0 + b0 + tid;
+    bool keep = false;
+    int j = 0;
+    if (b0 + tid < room) {
+      int64_t jj = w0 + t;  // w0 < n and t < m <= n
+      if (jj >= n) jj -= n;
+      j = (int)jj;
+      const int32_t id = wperm[j];
+      keep = !is_member(sm.nb, sm.kk, id);
+      if (srow) srow[t] = keep ? id : -1;
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) sm.warp_cnt[warp] = __popc(mk);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) off += sm.warp_cnt[w];
+      tot += sm.warp_cnt[w];
+    }
+    if (keep) sm.S[filled + off + __popc(mk & ((1u << lane) - 1u))] = j;
+    filled += tot;
+    __syncthreads();
+  }
+  if (tid == 0) sm.cnt = filled;
+  __syncthreads();
+}
+
 // Sum of kernel values over rows ids[0..cnt) of X, by groups of G lanes.
 // Returns this thread's partial (lane-in-group 0 holds the group sums).
 template <int G, bool L1>
@@ -265,7 +306,20 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   const bool sampled = !((int64_t)kk == a.n || a.m == 0);
   float s2 = 0.f;
   bool ok = true;
-  if (sampled) {
+  int kept = a.m;  // m' of the permuted mode
+  if (sampled && a.mode == 2) {
+    const int64_t w0 = (int64_t)(((qid % (uint64_t)a.n) * (uint64_t)a.m) % (uint64_t)a.n);
+    float part = 0.f;
+    kept = 0;
+    for (int t0 = 0; t0 < a.m; t0 += kChunk) {
+      const int room = min(kChunk, a.m - t0);
+      window_chunk(a.wperm, a.n, w0, t0, room, sm, a.samples ? a.samples + q * a.m : nullptr);
+      if (a.out) part += gather_sum_k<G>(a.XP, a.dp, ys, sm.S, sm.cnt, a.kern, inv);
+      kept += sm.cnt;
+      __syncthreads();
+    }
+    if (a.out) s2 = block_sum(part, sm);
+  } else if (sampled) {
     const int64_t cap = a.mode == 1 ? (int64_t)a.m : 64 * (int64_t)a.m + 4096;
     int64_t t0 = 0;
     int got = 0;
@@ -308,8 +362,9 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
     } else if (a.out) {
       const double n = (double)a.n;
       double est;
-      if (!sampled) est = (double)s1 / n;
+      if (!sampled || kept == 0) est = (double)s1 / n;
       else if (a.mode == 1) est = (double)s1 / n + (double)s2 / (double)a.m;
+      else if (a.mode == 2) est = ((double)s1 + (n - (double)kk) / (double)kept * (double)s2) / n;
       else est = ((double)s1 + (n - (double)kk) / (double)a.m * (double)s2) / n;
       a.out[q] = (float)est;
     }

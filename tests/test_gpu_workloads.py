@@ -73,6 +73,24 @@ def test_embed_full_size_sampled(embed, precision):
     assert index.margin_failures() == 0
 
 
+def test_embed_full_size_deannp_sampled(embed):
+    """DEANNP (Algorithm 2) at full size: the 1M-entry permutation is
+    bit-exact and sampled estimates match the oracle's windows."""
+    X, Y, index, _, _ = embed
+    k, m, P, h = 1024, 8000, 8, 12.85
+    perm = index.prepare_permuted(return_perm=True).cpu().numpy()
+    want_perm = oracle.feistel_perm(1, X.shape[0])
+    assert np.array_equal(perm, want_perm)
+    out, nbr = index.query(_dev(Y), k, m, nprobe=P, precision=1, sample_mode=2,
+                           return_neighbors=True)
+    out, nbr = out.cpu().numpy(), nbr.cpu().numpy()
+    n = X.shape[0]
+    for q in np.arange(0, Y.shape[0], 417)[:24]:
+        v, _ = oracle.deannp(X, Y[q:q + 1], "gaussian", h, want_perm, nbr[q:q + 1], m,
+                             ell0=(int(q) * m) % n)
+        assert_kde_close(out[q:q + 1], v)
+
+
 def test_embed_full_size_exact_sampled(embed):
     X, Y, index, _, _ = embed
     ex = index.exact(_dev(Y)).cpu().numpy()
