@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdeann_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["build.cu", "tiles.cu", "select.cu", "sample.cu", "capi.cu", "noalloc.cu",
-           "tc_scan.cu", "tc_exact.cu"]
+           "tc_scan.cu", "tc_exact.cu", "window.cu"]
 HEADERS = ["common.cuh", "internal.h", "tc.cuh"]
 
 

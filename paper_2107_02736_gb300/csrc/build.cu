@@ -410,6 +410,19 @@ void launch_feistel_perm(uint64_t seed, int64_t n, int32_t* out, cudaStream_t s)
   k_feistel_perm<<<grid_for(n, 256), 256, 0, s>>>(seed, n, hb, out);
 }
 
+namespace {
+__global__ void k_invert_perm(const int32_t* __restrict__ perm, int64_t n,
+                              int32_t* __restrict__ inv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) inv[perm[i]] = (int32_t)i;
+}
+}  // namespace
+
+void launch_invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s) {
+  if (n <= 0) return;
+  k_invert_perm<<<grid_for(n, 256), 256, 0, s>>>(perm, n, inv);
+}
+
 void launch_max_f32(const float* v, int64_t n, float* out, cudaStream_t s) {
   cudaMemsetAsync(out, 0, sizeof(float), s);
   k_max_f32<<<grid_for(n, 256), 256, 0, s>>>(v, n, reinterpret_cast<unsigned*>(out));

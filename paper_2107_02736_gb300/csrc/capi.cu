@@ -220,6 +220,13 @@ struct CallBufs {
   double* acc = nullptr;
   void* Ys = nullptr;      // [3][nq][dpb] BF16 parts of the centred queries
   float* ysn = nullptr;    // their squared norms
+  // tiled permuted windows
+  WindowPlan win;
+  int32_t* win_drops = nullptr;  // nq x max(k, 1)
+  int32_t* win_dcnt = nullptr;
+  int32_t* win_kk = nullptr;
+  float* win_s1 = nullptr;
+  double* win_part = nullptr;    // nq x nslices
   SearchBufs search;
 };
 
@@ -236,6 +243,7 @@ struct CallShape {
   bool grad = false;
   bool exact = false;
   bool exact_tc = false;   // tensor-core exact: BF16 parts of the queries
+  bool window = false;     // permuted-window estimator (sample_mode 2)
 };
 
 void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -256,6 +264,16 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
   if (c.exact_tc) {
     cb.Ys = b.take<uint16_t>((size_t)3 * nq * ix->dpb);
     cb.ysn = b.take<float>(nq);
+  }
+  if (c.window && c.m > 0) {
+    cb.win = window_plan(c.nq, ix->n, c.m);
+    if (window_tiled(cb.win)) {
+      cb.win_drops = b.take<int32_t>((size_t)nq * std::max(c.k, 1));
+      cb.win_dcnt = b.take<int32_t>(nq);
+      cb.win_kk = b.take<int32_t>(nq);
+      cb.win_s1 = b.take<float>(nq);
+      cb.win_part = b.take<double>((size_t)nq * cb.win.nslices);
+    }
   }
   if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
 }
@@ -391,6 +409,8 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.mode = o->sample_mode;
   a.XP = ix->XP;
   a.wperm = ix->wperm;
+  a.wpinv = ix->wpinv;
+  a.win_period = window_period(ix->n, m);
   a.s1_in = nullptr;
   a.kcount_in = nullptr;
   a.out = nullptr;
@@ -446,6 +466,39 @@ kde_status finish_call(kde_index* ix, bool host, cudaStream_t st) {
   kde_status s = collect_errors(ix, st, &margin);
   ix_margin_accumulate(ix, margin);
   return s;
+}
+
+// The estimator of a query call: per-query gathers (k_estimate), or, for
+// permuted windows that many queries of the batch share, the tiled window
+// path (prep, tiles, finish).
+void run_estimate(kde_index* ix, const CallBufs& cb, const SampleArgs& a, cudaStream_t st) {
+  if (a.mode == 2 && a.m > 0 && a.out != nullptr && a.samples == nullptr &&
+      cb.win_part != nullptr) {
+    StageTimer t(ix, ST_ESTIMATE, st, 3);
+    const int dstride = std::max(a.k, 1);
+    launch_window_prep(a, cb.win_drops, dstride, cb.win_dcnt, cb.win_kk, cb.win_s1, st);
+    WindowTileArgs w;
+    w.Y = a.Y;
+    w.dp = a.dp;
+    w.nq = a.nq;
+    w.XP = a.XP;
+    w.n = a.n;
+    w.m = a.m;
+    w.p = cb.win;
+    w.qid_offset = a.qid_offset;
+    w.dev_qid = a.dev_qid;
+    w.drops = cb.win_drops;
+    w.dstride = dstride;
+    w.dcnt = cb.win_dcnt;
+    w.kern = a.kern;
+    w.h = a.h;
+    w.part = cb.win_part;
+    launch_window_tile(w, st);
+    launch_window_finish(a, cb.win, cb.win_dcnt, cb.win_kk, cb.win_s1, cb.win_part, st);
+    return;
+  }
+  StageTimer t(ix, ST_ESTIMATE, st, 1);
+  launch_estimate(a, st);
 }
 
 }  // namespace
@@ -654,6 +707,7 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->err);
   cudaFree(ix->xmax_d);
   cudaFree(ix->wperm);
+  cudaFree(ix->wpinv);
   cudaFree(ix->XP);
   if (ix->scratch.base) cudaFree(ix->scratch.base);
   for (const auto& e : ix->events) {
@@ -672,17 +726,21 @@ kde_status kde_prepare_permuted(kde_index* ix, int32_t* perm_out, const kde_opts
   cudaStream_t st = stream_of(o);
   if (ix->wperm == nullptr) {
     int32_t* wp = nullptr;
+    int32_t* wi = nullptr;
     float* xp = nullptr;
     TRY(dev_alloc(&wp, (size_t)ix->n));
-    if (dev_alloc(&xp, (size_t)ix->n * ix->dp) != KDE_OK) {
+    if (dev_alloc(&wi, (size_t)ix->n) != KDE_OK || dev_alloc(&xp, (size_t)ix->n * ix->dp) != KDE_OK) {
       cudaFree(wp);
+      cudaFree(wi);
       return fail(KDE_ENOMEM, "no room for the permuted dataset copy (%lld x %d floats)",
                   (long long)ix->n, ix->dp);
     }
     launch_feistel_perm(ix->seed, ix->n, wp, st);
+    launch_invert_perm(wp, ix->n, wi, st);
     launch_gather_rows(ix->X, ix->dp, wp, ix->n, xp, st);
     CK(cudaGetLastError());
     ix->wperm = wp;
+    ix->wpinv = wi;
     ix->XP = xp;
   }
   if (perm_out == nullptr) return KDE_OK;
@@ -807,6 +865,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   c.need_out = host;
   c.need_nbr = k > 0 && (host || nbr == nullptr);
   c.need_s1 = k > 0;
+  c.window = o->sample_mode == 2;
   CallBufs cb;
   TRY(prepare_call(ix, c, cb));
   TRY(stage_queries(ix, Y, nq, host, cb, st));
@@ -816,10 +875,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   a.s1_in = k > 0 ? cb.s1 : nullptr;
   a.out = host ? cb.out : out;
   a.rs = k == 0 ? 1 : 0;
-  {
-    StageTimer t(ix, ST_ESTIMATE, st, 1);
-    launch_estimate(a, st);
-  }
+  run_estimate(ix, cb, a, st);
   if (host) {
     TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
     if (nbr && k > 0) TRY(copy_out(nbr, nb, sizeof(int32_t) * nq * k, true, st));
@@ -848,6 +904,7 @@ kde_status kde_query_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
   c.host = host;
   c.need_out = host;
   c.need_nbr = host && k > 0;
+  c.window = o->sample_mode == 2;
   CallBufs cb;
   TRY(prepare_call(ix, c, cb));
   TRY(stage_queries(ix, Y, nq, host, cb, st));
@@ -858,10 +915,7 @@ kde_status kde_query_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
   }
   SampleArgs a = sample_args(ix, cb, nq, k > 0 ? nb : nullptr, k, m, seed, o);
   a.out = host ? cb.out : out;
-  {
-    StageTimer t(ix, ST_ESTIMATE, st, 1);
-    launch_estimate(a, st);
-  }
+  run_estimate(ix, cb, a, st);
   if (host) TRY(copy_out(out, cb.out, sizeof(float) * nq, true, st));
   return finish_call(ix, host, st);
 }
@@ -1157,6 +1211,7 @@ kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t 
     c.grad = variant == 2;
     c.exact = variant == 3;
     c.exact_tc = variant == 3 && ix->xs_ok;
+    c.window = variant == 0;  // sample_mode 2
     Bump cnt;
     CallBufs dummy;
     carve_call(cnt, ix, c, dummy);

@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #define KDE_KERN_GAUSSIAN 0
@@ -91,6 +92,7 @@ struct kde_index {
   // permuted sampling (Algorithm 2): pi and the dataset in pi order,
   // XP[i] = X[pi(i)]; built by kde_prepare_permuted
   int32_t* wperm = nullptr;   // [n] window position -> original id
+  int32_t* wpinv = nullptr;   // [n] original id -> window position (pi^-1)
   float* XP = nullptr;        // [n x dp]
   uint32_t* err = nullptr;    // device error words [4]
   float* xmax_d = nullptr;    // device max |x|^2
@@ -138,6 +140,7 @@ void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L,
                         void* dst, int dpb, float* xcn, float* rad, cudaStream_t s);
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s);
 void launch_feistel_perm(uint64_t seed, int64_t n, int32_t* out, cudaStream_t s);
+void launch_invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
 
 // ---- tiles.cu (SIMT distance tiles) ---------------------------------------
 void launch_exact_simt(const float* Y, const float* Yn, int64_t nq, const float* X,
@@ -236,6 +239,8 @@ struct SampleArgs {
   int mode;                  // 0 reject, 1 drop, 2 permuted window (Algorithm 2)
   const float* XP;           // mode 2: the dataset in pi order
   const int32_t* wperm;      // mode 2: pi
+  const int32_t* wpinv;      // mode 2: pi^-1
+  int64_t win_period;        // mode 2: n / gcd(n, m), queries this far apart share a window
   const float* s1_in;        // precomputed neighbour sums (nullable)
   const int32_t* kcount_in;  // matching k' (nullable)
   float* out;                // [nq] estimates (nullable)
@@ -248,6 +253,49 @@ struct SampleArgs {
   uint32_t* err;
 };
 void launch_estimate(const SampleArgs& a, cudaStream_t s);
+
+// ---- window.cu + sample.cu: permuted windows shared by many queries --------
+// Queries whose ids agree mod P = n / gcd(n, m) read the same window; a batch
+// with nq = A P + B holds A or A + 1 queries per residue class.  With
+// A >= kWindowMinShare the estimator runs as dense (queries x window rows)
+// tiles instead of per-query gathers.
+constexpr int64_t kWindowMinShare = 16;
+struct WindowPlan {
+  int64_t P = 1, A = 0, B = 0;
+  int64_t groups = 0;        // min(P, nq) residue classes
+  int Tq = 0;                // 64-query tiles per class
+  int rs = 64;               // window positions per row slice (multiple of 64)
+  int nslices = 0;
+};
+int64_t window_period(int64_t n, int64_t m);
+WindowPlan window_plan(int64_t nq, int64_t n, int m);
+bool window_tiled(const WindowPlan& p);
+struct WindowTileArgs {
+  const float* Y;            // [nq x dp] staged queries
+  int dp;
+  int64_t nq;
+  const float* XP;           // permuted dataset
+  int64_t n;
+  int m;
+  WindowPlan p;
+  uint64_t qid_offset;
+  const uint64_t* dev_qid;
+  const int32_t* drops;      // [nq x dstride] sorted window positions of X_1 members
+  int dstride;
+  const int32_t* dcnt;       // [nq]
+  int kern;
+  float h;
+  double* part;              // [nq x p.nslices] partial window sums
+};
+void launch_window_tile(const WindowTileArgs& w, cudaStream_t s);
+// Per query: X_1 (sorted, deduplicated), s1 (unless a.s1_in), and the sorted
+// window positions of X_1's members; kk[q] = -1 flags a bad neighbour id.
+void launch_window_prep(const SampleArgs& a, int32_t* drops, int dstride, int32_t* dcnt,
+                        int32_t* kk, float* s1, cudaStream_t s);
+// out[q] = (s1 + ((n - k') / m') s2) / n with s2 the slice partials' sum.
+void launch_window_finish(const SampleArgs& a, const WindowPlan& p, const int32_t* dcnt,
+                          const int32_t* kk, const float* s1, const double* part,
+                          cudaStream_t s);
 void launch_estimate_grad(const SampleArgs& a, cudaStream_t s);
 void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,
                               int64_t nq, float h, cudaStream_t s);

@@ -53,6 +53,26 @@ __device__ __forceinline__ bool is_member(const int* nb, int kk, int64_t id) {
   return lo < kk && nb[lo] == id;
 }
 
+// Ascending bitonic sort of v[0..P2) (P2 a power of two) by the whole CTA;
+// ends with a barrier.
+__device__ void block_bitonic_sort(int* v, int P2) {
+  const int tid = threadIdx.x;
+  for (int size = 2; size <= P2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < P2 / 2; i += kNT) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const int a = v[lo], b = v[hi];
+        if ((a > b) == up) {
+          v[lo] = b;
+          v[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+}
+
 // Loads, sorts and deduplicates the neighbour row into sm.nb; sets sm.kk, or
 // sm.status = 1 when an id is >= n.
 __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t n, EstSmem& sm,
@@ -74,20 +94,7 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
     tmp[i] = v;
   }
   __syncthreads();
-  for (int size = 2; size <= P2; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = tid; i < P2 / 2; i += kNT) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = ((lo & size) == 0);
-        const int a = tmp[lo], b = tmp[hi];
-        if ((a > b) == up) {
-          tmp[lo] = b;
-          tmp[hi] = a;
-        }
-      }
-      __syncthreads();
-    }
+  block_bitonic_sort(tmp, P2);
   // compact the distinct valid ids, keeping sorted order
   int base = 0;
   for (int b0 = 0; b0 < P2; b0 += kNT) {
@@ -268,13 +275,33 @@ __device__ float block_sum(float v, EstSmem& sm) {
   return t;
 }
 
+// Permuted mode: the queries of a batch whose rows agree mod P = n / gcd(n, m)
+// read the same window.  Block b serves the b-th query in (q mod P, q) order,
+// so the blocks that share a window are scheduled together and its rows come
+// from HBM about once, the other reads hitting L2.  A bijection of [0, nq):
+// with nq = A P + B, the first B residue classes hold A + 1 queries, the rest A.
+__device__ __forceinline__ int64_t window_order(int64_t b, int64_t nq, int64_t P) {
+  if (P >= nq) return b;
+  const int64_t A = nq / P, B = nq % P;
+  int64_t s, j;
+  if (b < B * (A + 1)) {
+    s = b / (A + 1);
+    j = b % (A + 1);
+  } else {
+    const int64_t c = b - B * (A + 1);
+    s = B + c / A;
+    j = c % A;
+  }
+  return s + j * P;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   __shared__ EstSmem sm;
   __shared__ int tmp[kMaxK];
   extern __shared__ float4 ys4[];
   float* ys = reinterpret_cast<float*>(ys4);
-  const int64_t q = blockIdx.x;
+  const int64_t q = a.mode == 2 ? window_order(blockIdx.x, a.nq, a.win_period) : blockIdx.x;
   const int tid = threadIdx.x;
   const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
@@ -371,6 +398,107 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
     if (sampled == false && a.samples)
       for (int i = 0; i < a.m; ++i) a.samples[q * a.m + i] = -1;
   }
+}
+
+// Permuted windows shared by many queries (the tiled path): per query, the
+// neighbour set, s1, and the sorted window positions of the members of X_1.
+// A member x_id sits at window position (pi^-1(id) - ell) mod n when that is
+// below m.
+template <int G>
+__global__ void __launch_bounds__(kNT, 4)
+    k_window_prep(SampleArgs a, int32_t* __restrict__ drops, int dstride,
+                  int32_t* __restrict__ dcnt, int32_t* __restrict__ kko,
+                  float* __restrict__ s1o) {
+  __shared__ EstSmem sm;
+  __shared__ int tmp[kMaxK];
+  extern __shared__ float4 ys4[];
+  float* ys = reinterpret_cast<float*>(ys4);
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
+  const bool need_s1 = a.s1_in == nullptr;
+  if (need_s1)
+    for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
+  const int k = a.rs ? 0 : a.k;
+  if (k > 0) {
+    load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
+  } else {
+    if (tid == 0) {
+      sm.kk = 0;
+      sm.status = 0;
+    }
+    __syncthreads();
+  }
+  if (sm.status) {
+    if (tid == 0) {
+      atomicOr(a.err, KDE_ERRBIT_BADNBR);
+      kko[q] = -1;
+      dcnt[q] = 0;
+      s1o[q] = 0.f;
+    }
+    return;
+  }
+  const int kk = sm.kk;
+  float s1 = 0.f;
+  if (!need_s1) {
+    s1 = a.s1_in[q];
+  } else if (kk > 0) {
+    s1 = block_sum(gather_sum_k<G>(a.X, a.dp, ys, sm.nb, kk, a.kern, kernel_inv(a.kern, a.h)),
+                   sm);
+  }
+  const int64_t w0 = (int64_t)(((qid % (uint64_t)a.n) * (uint64_t)a.m) % (uint64_t)a.n);
+  int cnt = 0;
+  for (int b0 = 0; b0 < kk; b0 += kNT) {
+    const int t = b0 + tid;
+    bool in = false;
+    int pos = 0;
+    if (t < kk) {
+      int64_t pp = (int64_t)a.wpinv[sm.nb[t]] - w0;
+      if (pp < 0) pp += a.n;
+      in = pp < (int64_t)a.m;
+      pos = (int)pp;
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) sm.warp_cnt[warp] = __popc(mk);
+    __syncthreads();
+    int off = cnt, tot = 0;
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) off += sm.warp_cnt[w];
+      tot += sm.warp_cnt[w];
+    }
+    if (in) tmp[off + __popc(mk & ((1u << lane) - 1u))] = pos;
+    cnt += tot;
+    __syncthreads();
+  }
+  int P2 = 1;
+  while (P2 < cnt) P2 <<= 1;
+  for (int i = cnt + tid; i < P2; i += kNT) tmp[i] = 0x7fffffff;
+  __syncthreads();
+  block_bitonic_sort(tmp, P2);
+  for (int i = tid; i < cnt; i += kNT) drops[q * dstride + i] = tmp[i];
+  if (tid == 0) {
+    dcnt[q] = cnt;
+    kko[q] = kk;
+    s1o[q] = s1;
+  }
+}
+
+__global__ void k_window_finish(int64_t nq, int64_t n, int m, int nslices,
+                                const int32_t* __restrict__ dcnt, const int32_t* __restrict__ kko,
+                                const float* __restrict__ s1o, const double* __restrict__ part,
+                                float* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int kk = kko[q];
+  if (kk < 0) {
+    out[q] = __int_as_float(0x7fc00000);
+    return;
+  }
+  double s2 = 0.0;
+  for (int sl = 0; sl < nslices; ++sl) s2 += part[q * nslices + sl];
+  const int kept = m - dcnt[q];  // k' = n leaves every window entry in X_1
+  const double nn = (double)n, s1 = (double)s1o[q];
+  out[q] = (float)(kept > 0 ? (s1 + (nn - (double)kk) / (double)kept * s2) / nn : s1 / nn);
 }
 
 // ---------------------------------------------------------------------------
@@ -594,6 +722,27 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s) {
     case 16: k_estimate<16><<<grid, kNT, dyn, s>>>(a); break;
     default: k_estimate<32><<<grid, kNT, dyn, s>>>(a); break;
   }
+}
+
+void launch_window_prep(const SampleArgs& a, int32_t* drops, int dstride, int32_t* dcnt,
+                        int32_t* kk, float* s1, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  const size_t dyn = sizeof(float) * a.dp;
+  const unsigned grid = (unsigned)a.nq;
+  switch (group_lanes(a.dp)) {
+    case 4: k_window_prep<4><<<grid, kNT, dyn, s>>>(a, drops, dstride, dcnt, kk, s1); break;
+    case 8: k_window_prep<8><<<grid, kNT, dyn, s>>>(a, drops, dstride, dcnt, kk, s1); break;
+    case 16: k_window_prep<16><<<grid, kNT, dyn, s>>>(a, drops, dstride, dcnt, kk, s1); break;
+    default: k_window_prep<32><<<grid, kNT, dyn, s>>>(a, drops, dstride, dcnt, kk, s1); break;
+  }
+}
+
+void launch_window_finish(const SampleArgs& a, const WindowPlan& p, const int32_t* dcnt,
+                          const int32_t* kk, const float* s1, const double* part,
+                          cudaStream_t s) {
+  if (a.nq <= 0) return;
+  k_window_finish<<<(unsigned)((a.nq + 255) / 256), 256, 0, s>>>(a.nq, a.n, a.m, p.nslices,
+                                                                  dcnt, kk, s1, part, a.out);
 }
 
 void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,

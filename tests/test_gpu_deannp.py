@@ -159,3 +159,62 @@ def test_deannp_argument_errors(pkg):
     with pytest.raises(pkg.KDEError) as e:
         index.query_rs(_dev(Y), 10, sample_mode=3)
     assert e.value.status == 1
+
+
+# --------------------------------------------- windows shared by many queries --
+# With A = nq / P >= 16 queries per window (P = n / gcd(n, m)) the estimator
+# runs as dense (queries x window rows) tiles.
+@pytest.mark.parametrize("n,m,nq", [(4096, 512, 300),    # P = 8, A = 37: one query tile
+                                    (2000, 1000, 300),   # P = 2, A = 150: three query tiles
+                                    (3001, 3001, 40),    # P = 1: the full window
+                                    (6000, 1500, 200)])  # P = 4, A = 50
+@pytest.mark.parametrize("kernel", ["gaussian", "exponential", "laplacian"])
+def test_tiled_windows_match_oracle(pkg, n, m, nq, kernel):
+    d = 17 if kernel != "gaussian" else 128
+    X, Y = _data(n, d, nq, seed=n + nq)
+    h = _bandwidth(d) if kernel != "laplacian" else 0.5 * d
+    k = 50
+    nbr, _ = oracle.knn(X, Y, k)
+    nbr[::5, 3] = nbr[::5, 2]   # duplicates count once
+    nbr[2::7, -4:] = -1         # padding
+    index = pkg.KDEIndex(_dev(X), kernel, h, seed=31)
+    index.prepare_permuted()
+    perm = oracle.feistel_perm(31, n)
+    for qoff in (0, 123457):
+        got = index.query_with_neighbors(_dev(Y), _dev(nbr), m, sample_mode=2,
+                                         qid_offset=qoff).cpu().numpy()
+        want, _ = oracle.deannp(X, Y, kernel, h, perm, nbr, m, ell0=(qoff * m) % n)
+        assert_kde_close(got, want)
+    # host pointers take the same path
+    got_h = index.query_with_neighbors(torch.from_numpy(Y), torch.from_numpy(nbr), m,
+                                       sample_mode=2).numpy()
+    want0, _ = oracle.deannp(X, Y, kernel, h, perm, nbr, m, ell0=0)
+    assert_kde_close(got_h, want0)
+
+
+def test_tiled_windows_rsp_and_search(pkg):
+    n, m, nq = 8192, 1024, 400  # P = 8, A = 50
+    X, Y, _ = workloads.mixture_iso(n=n, d=16, nq=nq)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=8, seed=4)
+    index.prepare_permuted()
+    perm = oracle.feistel_perm(4, n)
+    got = index.query_rs(_dev(Y), m, sample_mode=2, qid_offset=3).cpu().numpy()
+    want, _ = oracle.deannp(X, Y, "gaussian", 2.0, perm, None, m, ell0=(3 * m) % n)
+    assert_kde_close(got, want)
+    out, nbr = index.query(_dev(Y), 40, m, nprobe=4, sample_mode=2, precision=1,
+                           return_neighbors=True)
+    want, _ = oracle.deannp(X, Y, "gaussian", 2.0, perm, nbr.cpu().numpy(), m, ell0=0)
+    assert_kde_close(out.cpu().numpy(), want)
+
+
+def test_tiled_windows_under_graph_replays(pkg):
+    n, m, k = 4096, 512, 20  # P = 8; capacity 256 gives A = 32
+    X, Y = _data(n, 32, 600, seed=12)
+    h = _bandwidth(32)
+    index = pkg.KDEIndex(_dev(X), "gaussian", h, nlist=4, seed=6)
+    index.prepare_permuted()
+    g = pkg.GraphedQuery(index, 256, k, m, nprobe=4, sample_mode=2)
+    for off, (a, b) in ((0, (0, 256)), (256, (256, 512)), (1000, (100, 356))):
+        got = g(_dev(Y[a:b]), qid_offset=off).clone()
+        want = index.query(_dev(Y[a:b]), k, m, nprobe=4, sample_mode=2, qid_offset=off)
+        assert torch.equal(got, want)
