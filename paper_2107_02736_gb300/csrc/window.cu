@@ -22,24 +22,28 @@ namespace deann {
 
 namespace {
 
-constexpr int kKC = 32;            // dims per chunk
-constexpr int kLdA = kTile + 4;    // A row stride (floats)
-constexpr int kLdB = 2 * kTile + 4;  // B row stride: every row value stored twice
+constexpr int kKC = 32;            // dims per staged chunk of window rows
+constexpr int kResMaxDp = 320;     // query tile resident in shared memory up to this width
 
 enum { WMODE_SQ = 0, WMODE_ABS = 1 };
 
+// Shared layouts, both XOR-swizzled on 16-byte groups so that the transposed
+// staging stores and the fragment reads are free of bank conflicts:
+//   queries A[dim][64]: query r of dim c at ((r >> 2) ^ sw(c)) * 4 + (r & 3);
+//   rows B[dim][128]: every value twice; rows 4t, 4t + 1 of dim c fill group
+//     t ^ sw(c) as (x, x, x', x'), rows 4t + 2, 4t + 3 group (16 + t) ^ sw(c).
+__device__ __forceinline__ int sw(int c) { return (c >> 2) & 7; }
+__device__ __forceinline__ int acol(int r, int c) { return (((r >> 2) ^ sw(c)) << 2) + (r & 3); }
+__device__ __forceinline__ int bcol(int r, int c) {
+  const int g = ((r & 2) ? 16 : 0) + (r >> 2);
+  return ((g ^ sw(c)) << 2) + 2 * (r & 1);
+}
+
 struct alignas(16) WinSmem {
-  float A[kKC][kLdA];              // queries, transposed
-  float B[kKC][kLdB];              // window rows, transposed and duplicated
+  float A[kKC][kTile];             // streamed query chunk (wide rows only)
+  float B[kKC][2 * kTile];         // window rows of the current chunk
   uint64_t mask[2][kTile];         // per query slot: X_1 members among the tile's rows
 };
-
-// Column of row r's copy e (0, 1) in a B line: thread tx reads rows 4tx..4tx+1
-// as one 16-byte chunk at 4tx and rows 4tx+2..4tx+3 at 64 + 4tx, so a warp's
-// reads are contiguous.
-__device__ __forceinline__ int bcol(int r, int e) {
-  return ((r & 2) ? kTile : 0) + 4 * (r >> 2) + 2 * (r & 1) + e;
-}
 
 __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
   uint64_t r;
@@ -67,11 +71,28 @@ __device__ __forceinline__ float4 ld4(const float* p, int k, int dp) {
   return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// acc[i][j]: distance between query slot ty*4+i and row slot tx*4+j.
-template <int MODE>
+__device__ __forceinline__ void store_a(float* A, int r, int c, float4 v) {
+  A[(c + 0) * kTile + acol(r, c + 0)] = v.x;
+  A[(c + 1) * kTile + acol(r, c + 1)] = v.y;
+  A[(c + 2) * kTile + acol(r, c + 2)] = v.z;
+  A[(c + 3) * kTile + acol(r, c + 3)] = v.w;
+}
+
+__device__ __forceinline__ void store_b(WinSmem& sm, int r, int c, float4 v) {
+  *reinterpret_cast<float2*>(&sm.B[c + 0][bcol(r, c + 0)]) = make_float2(v.x, v.x);
+  *reinterpret_cast<float2*>(&sm.B[c + 1][bcol(r, c + 1)]) = make_float2(v.y, v.y);
+  *reinterpret_cast<float2*>(&sm.B[c + 2][bcol(r, c + 2)]) = make_float2(v.z, v.z);
+  *reinterpret_cast<float2*>(&sm.B[c + 3][bcol(r, c + 3)]) = make_float2(v.w, v.w);
+}
+
+// acc[i][j]: distance between query slot ty*4+i and row slot tx*4+j.  RES:
+// the queries sit in Ares[dp][64] for the CTA's lifetime; otherwise they are
+// streamed chunk by chunk with the rows.
+template <int MODE, bool RES>
 __device__ __forceinline__ void win_mainloop(const float* const (&aptr)[2],
                                              const float* const (&bptr)[2], int dp,
-                                             WinSmem& sm, float (&acc)[4][4]) {
+                                             WinSmem& sm, const float* Ares,
+                                             float (&acc)[4][4]) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   int srow[2], sc4[2];
@@ -93,40 +114,36 @@ __device__ __forceinline__ void win_mainloop(const float* const (&aptr)[2],
   float4 ra[2], rb[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    ra[s] = ld4(aptr[s], 4 * sc4[s], dp);
+    if (!RES) ra[s] = ld4(aptr[s], 4 * sc4[s], dp);
     rb[s] = ld4(bptr[s], 4 * sc4[s], dp);
   }
   for (int k0 = 0; k0 < dp; k0 += kKC) {
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const int r = srow[s], c = 4 * sc4[s];
-      sm.A[c + 0][r] = ra[s].x;
-      sm.A[c + 1][r] = ra[s].y;
-      sm.A[c + 2][r] = ra[s].z;
-      sm.A[c + 3][r] = ra[s].w;
-      const int b0 = bcol(r, 0);
-      *reinterpret_cast<float2*>(&sm.B[c + 0][b0]) = make_float2(rb[s].x, rb[s].x);
-      *reinterpret_cast<float2*>(&sm.B[c + 1][b0]) = make_float2(rb[s].y, rb[s].y);
-      *reinterpret_cast<float2*>(&sm.B[c + 2][b0]) = make_float2(rb[s].z, rb[s].z);
-      *reinterpret_cast<float2*>(&sm.B[c + 3][b0]) = make_float2(rb[s].w, rb[s].w);
+      if (!RES) store_a(&sm.A[0][0], srow[s], 4 * sc4[s], ra[s]);
+      store_b(sm, srow[s], 4 * sc4[s], rb[s]);
     }
     __syncthreads();
     const int kn = k0 + kKC;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      ra[s] = ld4(aptr[s], kn + 4 * sc4[s], dp);
+      if (!RES) ra[s] = ld4(aptr[s], kn + 4 * sc4[s], dp);
       rb[s] = ld4(bptr[s], kn + 4 * sc4[s], dp);
     }
+    const float* Ab = RES ? Ares + (size_t)k0 * kTile : &sm.A[0][0];
     if (MODE == WMODE_SQ) {
       uint64_t part[2][4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) part[0][j] = part[1][j] = 0ull;
 #pragma unroll 8
       for (int kk = 0; kk < kKC; ++kk) {
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(&sm.A[kk][ty * 4]);
-        const ulonglong2 b01 = *reinterpret_cast<const ulonglong2*>(&sm.B[kk][4 * tx]);
-        const ulonglong2 b23 = *reinterpret_cast<const ulonglong2*>(&sm.B[kk][kTile + 4 * tx]);
+        const int z = sw(kk);  // k0 is a multiple of 32: sw(k0 + kk) = sw(kk)
+        const ulonglong2 a =
+            *reinterpret_cast<const ulonglong2*>(Ab + kk * kTile + ((ty ^ z) << 2));
+        const ulonglong2 b01 = *reinterpret_cast<const ulonglong2*>(&sm.B[kk][(tx ^ z) << 2]);
+        const ulonglong2 b23 =
+            *reinterpret_cast<const ulonglong2*>(&sm.B[kk][((16 + tx) ^ z) << 2]);
         const uint64_t av[2] = {a.x, a.y};
         const uint64_t bv[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
@@ -149,9 +166,10 @@ __device__ __forceinline__ void win_mainloop(const float* const (&aptr)[2],
         for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
 #pragma unroll 8
       for (int kk = 0; kk < kKC; ++kk) {
-        const float4 a = *reinterpret_cast<const float4*>(&sm.A[kk][ty * 4]);
-        const float4 b01 = *reinterpret_cast<const float4*>(&sm.B[kk][4 * tx]);
-        const float4 b23 = *reinterpret_cast<const float4*>(&sm.B[kk][kTile + 4 * tx]);
+        const int z = sw(kk);
+        const float4 a = *reinterpret_cast<const float4*>(Ab + kk * kTile + ((ty ^ z) << 2));
+        const float4 b01 = *reinterpret_cast<const float4*>(&sm.B[kk][(tx ^ z) << 2]);
+        const float4 b23 = *reinterpret_cast<const float4*>(&sm.B[kk][((16 + tx) ^ z) << 2]);
         const float av[4] = {a.x, a.y, a.z, a.w};
         const float bv[4] = {b01.x, b01.z, b23.x, b23.z};
 #pragma unroll
@@ -184,9 +202,11 @@ __device__ __forceinline__ void win_mainloop(const float* const (&aptr)[2],
 
 // grid.x: (residue class s, 64-query tile of its queries); grid.y: slices of
 // p.rs window positions.  Class s holds queries s, s + P, s + 2P, ... < nq.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_window_tile(WindowTileArgs w) {
+template <int MODE, bool RES>
+__global__ void __launch_bounds__(256, RES ? 3 : 2) k_window_tile(WindowTileArgs w) {
   __shared__ WinSmem sm;
+  extern __shared__ float4 ares4[];  // RES: the query tile, [roundup(dp, 32)][64] swizzled
+  float* Ares = reinterpret_cast<float*>(ares4);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const WindowPlan& p = w.p;
@@ -205,6 +225,15 @@ __global__ void __launch_bounds__(256) k_window_tile(WindowTileArgs w) {
   for (int s2 = 0; s2 < 2; ++s2) {
     const int64_t jj = j0 + ((tid + 256 * s2) >> 3);
     aptr[s2] = jj < cs ? w.Y + (s + jj * p.P) * w.dp : nullptr;
+  }
+  if (RES) {
+    for (int k0 = 0; k0 < w.dp; k0 += kKC)
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int idx = tid + 256 * s2;
+        const int c = k0 + 4 * (idx & 7);
+        store_a(Ares, idx >> 3, c, ld4(aptr[s2], c, w.dp));
+      }
   }
   // query slot tid (< 64): cursor into its sorted X_1 window positions
   const int32_t* dl = nullptr;
@@ -245,7 +274,7 @@ __global__ void __launch_bounds__(256) k_window_tile(WindowTileArgs w) {
       }
     }
     float acc[4][4];
-    win_mainloop<MODE>(aptr, bptr, w.dp, sm, acc);  // starts with a barrier
+    win_mainloop<MODE, RES>(aptr, bptr, w.dp, sm, Ares, acc);  // starts with a barrier
     float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -307,10 +336,31 @@ bool window_tiled(const WindowPlan& p) { return p.A >= kWindowMinShare; }
 void launch_window_tile(const WindowTileArgs& w, cudaStream_t s) {
   if (w.p.groups <= 0 || w.m <= 0) return;
   dim3 grid((unsigned)(w.p.groups * w.p.Tq), (unsigned)w.p.nslices);
-  if (w.kern == KDE_KERN_LAPLACIAN)
-    k_window_tile<WMODE_ABS><<<grid, 256, 0, s>>>(w);
-  else
-    k_window_tile<WMODE_SQ><<<grid, 256, 0, s>>>(w);
+  const bool res = w.dp <= kResMaxDp;
+  // the resident tile is staged in whole 32-dim chunks: round its rows up
+  const int dres = (w.dp + kKC - 1) / kKC * kKC;
+  const size_t dyn = res ? sizeof(float) * (size_t)dres * kTile : 0;
+  if (res) {
+    // the resident query tile needs up to 80 KB beyond the static 24.5 KB
+    static bool attr_set[2] = {false, false};
+    auto f0 = k_window_tile<WMODE_SQ, true>;
+    auto f1 = k_window_tile<WMODE_ABS, true>;
+    if (!attr_set[0]) {
+      cudaFuncSetAttribute(f0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float) * kResMaxDp * kTile));
+      cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float) * kResMaxDp * kTile));
+      attr_set[0] = attr_set[1] = true;
+    }
+    if (w.kern == KDE_KERN_LAPLACIAN)
+      f1<<<grid, 256, dyn, s>>>(w);
+    else
+      f0<<<grid, 256, dyn, s>>>(w);
+  } else if (w.kern == KDE_KERN_LAPLACIAN) {
+    k_window_tile<WMODE_ABS, false><<<grid, 256, 0, s>>>(w);
+  } else {
+    k_window_tile<WMODE_SQ, false><<<grid, 256, 0, s>>>(w);
+  }
 }
 
 }  // namespace deann
