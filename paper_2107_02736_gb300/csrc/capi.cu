@@ -186,7 +186,8 @@ constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of q
 
 void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
   const int L = ix->nlist;
-  const size_t per_q = (size_t)P * (size_t)std::max<int64_t>(ix->max_list, 1) * sizeof(float);
+  // each query's candidate segment is padded to a multiple of 4 floats
+  const size_t per_q = ((size_t)P * (size_t)std::max<int64_t>(ix->max_list, 1) + 4) * sizeof(float);
   int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
   qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
   s.qc = qc;
@@ -203,7 +204,7 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.tile_off = b.take<int64_t>(L + 1);
   s.pair_q = b.take<int32_t>((size_t)qc * P);
   s.pair_dst = b.take<int64_t>((size_t)qc * P);
-  s.cand = b.take<float>((size_t)qc * P * std::max<int64_t>(ix->max_list, 1));
+  s.cand = b.take<float>((size_t)qc * ((size_t)P * std::max<int64_t>(ix->max_list, 1) + 4));
 }
 
 struct CallBufs {
@@ -410,6 +411,7 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.XP = ix->XP;
   a.wperm = ix->wperm;
   a.wpinv = ix->wpinv;
+  a.nbr_distinct = 0;
   a.win_period = window_period(ix->n, m);
   a.s1_in = nullptr;
   a.kcount_in = nullptr;
@@ -873,6 +875,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st, true));
   SampleArgs a = sample_args(ix, cb, nq, nb, k, m, seed, o);
   a.s1_in = k > 0 ? cb.s1 : nullptr;
+  a.nbr_distinct = 1;
   a.out = host ? cb.out : out;
   a.rs = k == 0 ? 1 : 0;
   run_estimate(ix, cb, a, st);

@@ -240,6 +240,7 @@ struct SampleArgs {
   const float* XP;           // mode 2: the dataset in pi order
   const int32_t* wperm;      // mode 2: pi
   const int32_t* wpinv;      // mode 2: pi^-1
+  int nbr_distinct;          // 1: nbr rows hold distinct ids or -1 (the search's output)
   int64_t win_period;        // mode 2: n / gcd(n, m), queries this far apart share a window
   const float* s1_in;        // precomputed neighbour sums (nullable)
   const int32_t* kcount_in;  // matching k' (nullable)

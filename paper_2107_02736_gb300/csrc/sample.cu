@@ -420,8 +420,12 @@ __global__ void __launch_bounds__(kNT, 4)
   if (need_s1)
     for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;
-  if (k > 0) {
-    load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
+  // ids that come from the search are distinct (and s1 comes with them): no
+  // sort or deduplication is needed, only the count of valid ids
+  const bool fast = a.nbr_distinct && k > 0 && !need_s1;
+  const int32_t* row = k > 0 ? a.nbr + q * a.k : nullptr;
+  if (k > 0 && !fast) {
+    load_neighbours(row, k, a.n, sm, tmp);
   } else {
     if (tid == 0) {
       sm.kk = 0;
@@ -438,38 +442,49 @@ __global__ void __launch_bounds__(kNT, 4)
     }
     return;
   }
-  const int kk = sm.kk;
   float s1 = 0.f;
   if (!need_s1) {
     s1 = a.s1_in[q];
-  } else if (kk > 0) {
-    s1 = block_sum(gather_sum_k<G>(a.X, a.dp, ys, sm.nb, kk, a.kern, kernel_inv(a.kern, a.h)),
-                   sm);
+  } else if (sm.kk > 0) {
+    s1 = block_sum(
+        gather_sum_k<G>(a.X, a.dp, ys, sm.nb, sm.kk, a.kern, kernel_inv(a.kern, a.h)), sm);
   }
   const int64_t w0 = (int64_t)(((qid % (uint64_t)a.n) * (uint64_t)a.m) % (uint64_t)a.n);
-  int cnt = 0;
-  for (int b0 = 0; b0 < kk; b0 += kNT) {
+  __shared__ int vcnt[kNW];
+  const int kscan = fast ? k : sm.kk;
+  int cnt = 0, nvalid = 0;
+  for (int b0 = 0; b0 < kscan; b0 += kNT) {
     const int t = b0 + tid;
-    bool in = false;
+    bool in = false, valid = false;
     int pos = 0;
-    if (t < kk) {
-      int64_t pp = (int64_t)a.wpinv[sm.nb[t]] - w0;
-      if (pp < 0) pp += a.n;
-      in = pp < (int64_t)a.m;
-      pos = (int)pp;
+    if (t < kscan) {
+      const int32_t id = fast ? row[t] : sm.nb[t];
+      valid = id >= 0 && (int64_t)id < a.n;
+      if (valid) {
+        int64_t pp = (int64_t)a.wpinv[id] - w0;
+        if (pp < 0) pp += a.n;
+        in = pp < (int64_t)a.m;
+        pos = (int)pp;
+      }
     }
     const unsigned mk = __ballot_sync(0xffffffffu, in);
-    if (lane == 0) sm.warp_cnt[warp] = __popc(mk);
+    const unsigned mv = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) {
+      sm.warp_cnt[warp] = __popc(mk);
+      vcnt[warp] = __popc(mv);
+    }
     __syncthreads();
     int off = cnt, tot = 0;
     for (int w = 0; w < kNW; ++w) {
       if (w < warp) off += sm.warp_cnt[w];
       tot += sm.warp_cnt[w];
+      nvalid += vcnt[w];
     }
     if (in) tmp[off + __popc(mk & ((1u << lane) - 1u))] = pos;
     cnt += tot;
     __syncthreads();
   }
+  const int kk = fast ? nvalid : sm.kk;
   int P2 = 1;
   while (P2 < cnt) P2 <<= 1;
   for (int i = cnt + tid; i < P2; i += kNT) tmp[i] = 0x7fffffff;

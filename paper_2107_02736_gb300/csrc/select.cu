@@ -153,28 +153,79 @@ __device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, in
   return thr;
 }
 
-// Collects, in index order, the indices of all keys <= thr into
-// sm.slot[0..cap).  Returns the total count, which may exceed cap (then the
-// slots hold only the first cap).
+// A query's candidate values start on a 16-byte boundary (segments are
+// padded to multiples of 4 floats); entries at cnt and beyond are padding.
+// Calls f(i, v) for this thread's candidates, kU float4 loads in flight.
+constexpr int kU = 4;
+template <typename F>
+__device__ __forceinline__ void for_each_cand(const float* __restrict__ vals, int64_t cnt, F f) {
+  const float4* v4 = reinterpret_cast<const float4*>(vals);
+  const int64_t n4 = (cnt + 3) >> 2;
+  for (int64_t b = threadIdx.x; b < n4; b += (int64_t)kU * kNT) {
+    float4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i4 = b + (int64_t)u * kNT;
+      v[u] = i4 < n4 ? v4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = (b + (int64_t)u * kNT) * 4;
+      if (i + 0 < cnt) f(i + 0, v[u].x);
+      if (i + 1 < cnt) f(i + 1, v[u].y);
+      if (i + 2 < cnt) f(i + 2, v[u].z);
+      if (i + 3 < cnt) f(i + 3, v[u].w);
+    }
+  }
+}
+
+// Collects the indices of all keys <= thr into sm.slot[0..cap) in a fixed
+// order (rounds of kU * kNT float4s; within a round, thread by thread).
+// Returns the total count, which may exceed cap (then the slots hold only
+// the first cap).
 __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uint32_t thr, int cap,
                                 SelectSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float4* v4 = reinterpret_cast<const float4*>(vals);
+  const int64_t n4 = (cnt + 3) >> 2;
   int base = 0;
-  for (int64_t b0 = 0; b0 < cnt; b0 += kNT) {
-    const int64_t i = b0 + tid;
-    const bool take = i < cnt && dist_key(vals[i]) <= thr;
-    const unsigned mt = __ballot_sync(0xffffffffu, take);
-    if (lane == 0) sm.warp_a[warp] = __popc(mt);
+  for (int64_t r0 = 0; r0 < n4; r0 += (int64_t)kU * kNT) {
+    float4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i4 = r0 + (int64_t)u * kNT + tid;
+      v[u] = i4 < n4 ? v4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    unsigned take = 0u;  // bit 4u + c: component c of load u
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = (r0 + (int64_t)u * kNT + tid) * 4;
+      const float c4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (i + c < cnt && dist_key(c4[c]) <= thr) take |= 1u << (4 * u + c);
+    }
+    const int mine = __popc(take);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sm.warp_a[warp] = incl;
     __syncthreads();
-    int off = base, tot = 0;
+    int before = 0, tot = 0;
 #pragma unroll
     for (int w = 0; w < kNW; ++w) {
-      if (w < warp) off += sm.warp_a[w];
+      if (w < warp) before += sm.warp_a[w];
       tot += sm.warp_a[w];
     }
-    if (take) {
-      const int r = off + __popc(mt & ((1u << lane) - 1u));
-      if (r < cap) sm.slot[r] = (int)i;
+    int r = base + before + incl - mine;
+    while (take != 0u) {
+      const int bit = __ffs(take) - 1;
+      take &= take - 1u;
+      if (r < cap) sm.slot[r] = (int)((r0 + (int64_t)(bit >> 2) * kNT + tid) * 4 + (bit & 3));
+      ++r;
     }
     base += tot;
     __syncthreads();
@@ -195,17 +246,10 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
   __shared__ float s_lo, s_hi;
   int* hist = reinterpret_cast<int*>(sm.key);  // 16 KiB, free until rescoring
   float mn = __int_as_float(0x7f800000), mx = 0.f;
-  for (int64_t i0 = tid; i0 < cnt; i0 += 4 * kNT) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t i = i0 + u * kNT;
-      if (i < cnt) {
-        const float v = vals[i];
-        mn = fminf(mn, v);
-        mx = fmaxf(mx, v);
-      }
-    }
-  }
+  for_each_cand(vals, cnt, [&](int64_t, float v) {
+    mn = fminf(mn, v);
+    mx = fmaxf(mx, v);
+  });
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -224,16 +268,10 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
     mx = fmaxf(mx, s_mx[w]);
   }
   const float scale = mx > mn ? (float)kBins / (mx - mn) : 0.f;
-  for (int64_t i0 = tid; i0 < cnt; i0 += 4 * kNT) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t i = i0 + u * kNT;
-      if (i < cnt) {
-        const int bin = min(kBins - 1, max(0, (int)((vals[i] - mn) * scale)));
-        atomicAdd(&hist[bin], 1);
-      }
-    }
-  }
+  for_each_cand(vals, cnt, [&](int64_t, float v) {
+    const int bin = min(kBins - 1, max(0, (int)((v - mn) * scale)));
+    atomicAdd(&hist[bin], 1);
+  });
   __syncthreads();
   // thread t owns bins [16 t, 16 t + 16)
   constexpr int kPer = kBins / kNT;
@@ -435,15 +473,17 @@ __global__ void k_plan_tiles(const int64_t* __restrict__ list_cnt, int L, int qt
 }
 
 // Single-block exclusive scan; out has count + 1 entries (the last = total).
+// Each input is first rounded up to a multiple of `align`.
 __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restrict__ in,
                                                          int64_t count,
-                                                         int64_t* __restrict__ out) {
+                                                         int64_t* __restrict__ out,
+                                                         int64_t align) {
   __shared__ int64_t part[1024];
   const int tid = threadIdx.x;
   const int64_t per = (count + 1023) / 1024;
   const int64_t b = tid * per, e = min(count, b + per);
   int64_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += in[i];
+  for (int64_t i = b; i < e; ++i) s += (in[i] + align - 1) / align * align;
   part[tid] = s;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {
@@ -454,7 +494,7 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
   }
   int64_t run = part[tid] - s;
   for (int64_t i = b; i < e; ++i) {
-    const int64_t v = in[i];
+    const int64_t v = (in[i] + align - 1) / align * align;
     out[i] = run;
     run += v;
   }
@@ -521,25 +561,55 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
     }
   }
-  // rescore in plain FP32 difference form: 8 lanes per candidate, so each
-  // warp has 4 candidate rows in flight
+  // rescore in plain FP32 difference form: an 8-lane group per row, 16-byte
+  // loads, kRows rows per group in flight (16 per warp)
   {
+    constexpr int kRows = 4;
     const int grp = lane >> 3, lig = lane & 7;
-    for (int j0 = warp * 4; j0 < K; j0 += kNW * 4) {
-      const int j = j0 + grp;
-      const bool valid = j < K;
-      int64_t pos = 0;
-      if (valid) {
-        const int s = sm.slot[j];
-        int lo = 0, hi = a.P - 1;  // last segment with start <= s
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+    const int dp4 = a.dp >> 2;
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    const float4* X4 = reinterpret_cast<const float4*>(a.XL);
+    for (int j0 = warp * 4 * kRows; j0 < K; j0 += kNW * 4 * kRows) {
+      int64_t pos[kRows];
+      float acc[kRows];
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        const int j = j0 + grp * kRows + u;
+        pos[u] = -1;
+        acc[u] = 0.f;
+        if (j < K) {
+          const int s = sm.slot[j];
+          int lo = 0, hi = a.P - 1;  // last segment with start <= s
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+          }
+          pos[u] = s_lstart[lo] + (s - s_seg[lo]);
         }
-        pos = s_lstart[lo] + (s - s_seg[lo]);
       }
-      const float d2 = plain_sq_dist<8>(a.XL + pos * a.dp, y, a.d, lig);
-      if (valid && lig == 0) sm.key[j] = pack_key(d2, a.perm[pos]);
+#pragma unroll 2
+      for (int c4 = lig; c4 < dp4; c4 += 8) {
+        const float4 yv = y4[c4];
+        float4 xv[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u)
+          xv[u] = pos[u] >= 0 ? __ldg(X4 + pos[u] * dp4 + c4) : yv;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+          const float t0 = xv[u].x - yv.x, t1 = xv[u].y - yv.y, t2 = xv[u].z - yv.z,
+                      t3 = xv[u].w - yv.w;
+          acc[u] = fmaf(t0, t0, acc[u]);
+          acc[u] = fmaf(t1, t1, acc[u]);
+          acc[u] = fmaf(t2, t2, acc[u]);
+          acc[u] = fmaf(t3, t3, acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        const float d2 = group_sum<8>(acc[u]);
+        if (pos[u] >= 0 && lig == 0)
+          sm.key[j0 + grp * kRows + u] = pack_key(d2, a.perm[pos[u]]);
+      }
     }
   }
   __syncthreads();
@@ -724,7 +794,7 @@ void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStre
 }
 
 void launch_exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, cudaStream_t s) {
-  k_exclusive_scan<<<1, 1024, 0, s>>>(in, count, out);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(in, count, out, 1);
 }
 
 void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
@@ -746,14 +816,14 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
   cudaMemsetAsync(bucket_fill, 0, sizeof(int64_t) * L, s);
   k_plan_segments<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(probes, nq, P, list_off, q_count,
                                                               seg_off, list_cnt);
-  k_exclusive_scan<<<1, 1024, 0, s>>>(q_count, nq, q_off);
-  k_exclusive_scan<<<1, 1024, 0, s>>>(list_cnt, L, bucket_off);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(q_count, nq, q_off, 4);  // 16-byte segments
+  k_exclusive_scan<<<1, 1024, 0, s>>>(list_cnt, L, bucket_off, 1);
   const int64_t np = nq * P;
   k_plan_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(probes, nq, P, q_off, seg_off,
                                                            bucket_off, bucket_fill, pair_q,
                                                            pair_dst);
   k_plan_tiles<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(list_cnt, L, qtile, tile_cnt);
-  k_exclusive_scan<<<1, 1024, 0, s>>>(tile_cnt, L, tile_off);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(tile_cnt, L, tile_off, 1);
 }
 
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
