@@ -179,6 +179,8 @@ struct SearchBufs {
   int64_t *tile_cnt = nullptr, *tile_off = nullptr;
   int32_t* pair_q = nullptr;
   int64_t* pair_dst = nullptr;
+  int64_t *ord_cnt = nullptr, *ord_off = nullptr, *ord_fill = nullptr;
+  int32_t* order = nullptr;
   float* cand = nullptr;
 };
 
@@ -204,6 +206,10 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.tile_off = b.take<int64_t>(L + 1);
   s.pair_q = b.take<int32_t>((size_t)qc * P);
   s.pair_dst = b.take<int64_t>((size_t)qc * P);
+  s.ord_cnt = b.take<int64_t>(L);
+  s.ord_off = b.take<int64_t>(L + 1);
+  s.ord_fill = b.take<int64_t>(L);
+  s.order = b.take<int32_t>(qc);
   s.cand = b.take<float>((size_t)qc * ((size_t)P * std::max<int64_t>(ix->max_list, 1) + 4));
 }
 
@@ -331,10 +337,11 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       return fail(KDE_ECUDA, "the BF16 tensor map could not be encoded on this driver");
     const int qtile = tcore ? scan_tc_bn(ix->dpb) : kTile;
     {
-      StageTimer t(ix, ST_PLAN, st, 6);
+      StageTimer t(ix, ST_PLAN, st, 9);
       launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
                         s.tile_cnt, s.tile_off, qtile, st);
+      launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
     }
     ScanPlan plan;
     plan.pair_q = s.pair_q;
@@ -353,6 +360,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     }
     StageTimer tsel(ix, ST_SELECT, st, 1);
     SelectArgs a;
+    a.order = s.order;
     a.cand = s.cand;
     a.q_off = s.q_off;
     a.q_count = s.q_count;

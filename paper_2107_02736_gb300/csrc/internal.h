@@ -187,7 +187,10 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
                        int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
                        cudaStream_t s);
+void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_t* ord_cnt,
+                         int64_t* ord_off, int64_t* ord_fill, int32_t* order, cudaStream_t s);
 struct SelectArgs {
+  const int32_t* order;      // [nq] processing order (nullable: row order)
   const float* cand;
   const int64_t* q_off;
   const int64_t* q_count;

@@ -466,6 +466,28 @@ __global__ void k_plan_fill(const int32_t* __restrict__ probes, int64_t nq, int 
   pair_dst[slot] = q_off[q] + seg_off[i];
 }
 
+// Selection order: queries grouped by their nearest probed list, so that the
+// queries that rescore rows of the same list run together and share them in
+// L2.  Only the schedule changes; each query's result does not depend on it.
+__global__ void k_order_count(const int32_t* __restrict__ probes, int64_t nq, int P,
+                              int64_t* __restrict__ cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int l = max(0, probes[q * P]);
+  atomicAdd(reinterpret_cast<unsigned long long*>(cnt + l), 1ull);
+}
+
+__global__ void k_order_fill(const int32_t* __restrict__ probes, int64_t nq, int P,
+                             const int64_t* __restrict__ off, int64_t* __restrict__ fill,
+                             int32_t* __restrict__ order) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int l = max(0, probes[q * P]);
+  const int64_t slot =
+      off[l] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(fill + l), 1ull);
+  order[slot] = (int32_t)q;
+}
+
 __global__ void k_plan_tiles(const int64_t* __restrict__ list_cnt, int L, int qtile,
                              int64_t* __restrict__ tile_cnt) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -509,7 +531,7 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
   __shared__ int64_t s_seg[kMaxProbe + 1];
   __shared__ int64_t s_lstart[kMaxProbe];
   __shared__ float s_red[kNW];
-  const int64_t q = blockIdx.x;
+  const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t cnt = a.q_count[q];
   const float* vals = a.cand + a.q_off[q];
@@ -824,6 +846,17 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
                                                            pair_dst);
   k_plan_tiles<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(list_cnt, L, qtile, tile_cnt);
   k_exclusive_scan<<<1, 1024, 0, s>>>(tile_cnt, L, tile_off, 1);
+}
+
+void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_t* ord_cnt,
+                         int64_t* ord_off, int64_t* ord_fill, int32_t* order, cudaStream_t s) {
+  if (nq <= 0) return;
+  cudaMemsetAsync(ord_cnt, 0, sizeof(int64_t) * L, s);
+  cudaMemsetAsync(ord_fill, 0, sizeof(int64_t) * L, s);
+  const unsigned g = (unsigned)((nq + 255) / 256);
+  k_order_count<<<g, 256, 0, s>>>(probes, nq, P, ord_cnt);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(ord_cnt, L, ord_off, 1);
+  k_order_fill<<<g, 256, 0, s>>>(probes, nq, P, ord_off, ord_fill, order);
 }
 
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
