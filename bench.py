@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--kernel", default="gaussian")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    p.add_argument("--profile-case", type=int, default=0, metavar="NQ",
+                   help="run one call of each query-path kernel on NQ queries of the workload "
+                        "(for a profiler) and exit")
     return p.parse_args()
 
 
@@ -340,11 +343,33 @@ def roofline(stage, prof, calls, nq, n, d, nlist, k, m, P, peaks, peak_kind):
     return r
 
 
+def profile_case(args):
+    """One batch of args.profile_case queries through each path at the bench's
+    schedule (k = 1024, m = 8000, nprobe = 8, BF16 scan, h = 12.85): DEANN,
+    DEANNP (tiled windows), and the tensor-core exact KDE; one launch each of
+    k_scan_tc, k_select_neighbors, k_estimate, k_window_tile, k_exact_tc."""
+    import torch
+    import paper_2107_02736_gb300 as pkg
+    dev = torch.device("cuda", 0)
+    n = int(1_000_000 * args.scale)
+    X, Y, _ = workloads.mixture_embed(n=n, nq=args.profile_case)
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), args.kernel, 12.85, nlist=1024, seed=1)
+    index.prepare_permuted()
+    Yd = torch.from_numpy(Y).to(dev)
+    a = index.query(Yd, 1024, 8000, nprobe=8, seed=1, precision=1)
+    b = index.query(Yd, 1024, 8000, nprobe=8, seed=1, precision=1, sample_mode=2)
+    c = index.exact(Yd[:1024], path="tensor")
+    torch.cuda.synchronize()
+    print("profile case ok", float(a.mean()), float(b.mean()), float(c.mean()))
+
+
 def main():
     args = parse()
     rank, world, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile_case:
+        return profile_case(args)
 
     import torch
     import paper_2107_02736_gb300 as pkg
