@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--kernel", default="gaussian")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    p.add_argument("--no-schedules", dest="schedules", action="store_false",
+                   help="skip the recall / k = m / fixed-parameter runs (untimed extras)")
     p.add_argument("--profile-case", type=int, default=0, metavar="NQ",
                    help="run one call of each query-path kernel on NQ queries of the workload "
                         "(for a profiler) and exit")
@@ -62,6 +64,24 @@ def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, world, device=None):
+    """Max of a per-rank float over all ranks: a step of the job lasts as long
+    as its slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_per_step):
+    """Whole-job units/s: every rank serves its own batch (replicas), and the
+    step time is the slowest rank's."""
+    return units_per_rank * world / (ms_per_step / 1000.0)
 
 
 def rel_err(est, exact):
@@ -205,6 +225,35 @@ def tune(index, Yv_d, exact_v, torch, precision):
     return best, results
 
 
+def choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args):
+    """The schedule of the measured configuration: per scan precision the
+    cheapest (k, m, nprobe) whose validation error meets the target, then the
+    precision whose schedule serves the test queries fastest."""
+    nq = Yd.shape[0]
+    spec = workloads.CONFIGS[2]
+    sched, tuned = {}, {}
+    for name, prec in PRECISIONS.items():
+        if args.no_tune:
+            sched[name] = dict(k=spec["k"], m=spec["m"], nprobe=spec["nprobe"], val_ms=0.0,
+                               val_err=None)
+            tuned[name] = []
+        else:
+            sched[name], tuned[name] = tune(index, Yv_d, exact_v, torch, prec)
+    variants = {}
+    for name, prec in PRECISIONS.items():
+        s = sched[name]
+        ms = time_calls(lambda: index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=5,
+                                            precision=prec), 3, torch)
+        err = rel_err(index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=6,
+                                  precision=prec).cpu().numpy(), exact_t)
+        variants[name] = dict(k=s["k"], m=s["m"], nprobe=s["nprobe"], qps=nq / (ms / 1e3),
+                              test_rel_err=err, val_rel_err=s["val_err"])
+    ok = [v for v in variants if variants[v]["val_rel_err"] is not None
+          and variants[v]["val_rel_err"] <= TARGET_ERR]
+    head = max(ok or variants, key=lambda v: variants[v]["qps"])
+    return head, sched, tuned, variants
+
+
 def deannp_variant(index, Yd, Yv_d, exact_v, exact_t, s, prec, torch):
     """DEANNP (Algorithm 2: permuted windows instead of independent draws)
     with the headline's k and nprobe; m doubles until the validation error
@@ -240,6 +289,74 @@ def deannp_variant(index, Yd, Yv_d, exact_v, exact_t, s, prec, torch):
             "val_rel_err": err, "test_rel_err": test_err, "estimate_ms": est_ms,
             "estimate_gbs_algorithmic": Yd.shape[0] * m * index.d * 4 / (est_ms / 1e3) / 1e9,
             "prepare_s": prep_s}
+
+
+def recall_at_k(index, brute, Yv_d, k, nprobe, precision):
+    """Average recall R = mean_q |NN_k(q) & NN~_k(q)| / |NN_k(q)| of the IVF
+    search against the exact k nearest neighbours (an nlist = 1 index scanning
+    every point, FP32)."""
+    got, _ = index.search(Yv_d, k, nprobe=nprobe, precision=precision)
+    want, _ = brute.search(Yv_d, k, nprobe=1, precision=0)
+    got, want = got.cpu().numpy(), want.cpu().numpy()
+    r = [len(np.intersect1d(g[g >= 0], w[w >= 0])) / max(1, (w >= 0).sum())
+         for g, w in zip(got, want)]
+    return float(np.mean(r))
+
+
+def schedules_and_recall(index, X, Yd, Yv_d, exact_v, head_sched, prec, h, torch, pkg, dev):
+    """The robustness experiments of the paper's appendix, replayed on this
+    workload: recall of the ANN at the measured schedule; tuning restricted to
+    k = m (DEANN and DEANNP); and the fixed parameters k = 100, m = 1000,
+    512 lists, one probe with the exponential kernel (bandwidth bisected to the
+    same mean KDE), against that kernel's own tuned schedule."""
+    nq = Yd.shape[0]
+    out = {}
+    Xd = torch.from_numpy(X).to(dev)
+    brute = pkg.KDEIndex(Xd, "gaussian", h, nlist=1, seed=1)
+    index.prepare_permuted()
+    k, P = head_sched["k"], head_sched["nprobe"]
+    out["recall"] = {"k": k, "nprobe": P, "queries": int(Yv_d.shape[0]),
+                     "R": recall_at_k(index, brute, Yv_d, k, P, prec)}
+    # k = m: cheapest k = m (and nprobe) meeting the target, else the most accurate
+    for mode, name in ((0, "deann"), (2, "deannp")):
+        best = None
+        for Pp in (8, 16):
+            for km in (100, 200, 400, 800, 1024):
+                err = rel_err(index.query(Yv_d, km, km, nprobe=Pp, precision=prec,
+                                          sample_mode=mode).cpu().numpy(), exact_v)
+                ms = time_calls(lambda: index.query(Yd, km, km, nprobe=Pp, precision=prec,
+                                                    sample_mode=mode), 2, torch)
+                cand = {"k": km, "m": km, "nprobe": Pp, "val_rel_err": err,
+                        "qps": nq / (ms / 1e3)}
+                if best is None or (err <= TARGET_ERR and (best["val_rel_err"] > TARGET_ERR
+                                                          or cand["qps"] > best["qps"])) or \
+                        (best["val_rel_err"] > TARGET_ERR and err < best["val_rel_err"]):
+                    best = cand
+        out[f"k_eq_m_{name}"] = best
+    # fixed parameters, exponential kernel
+    spec = workloads.CONFIGS[2]
+    ex = pkg.KDEIndex(Xd, "exponential", 1.0, nlist=512, seed=1)
+    hx, _ = fit_bandwidth(ex, Yv_d, spec["target_mu"])
+    ex.prepare_permuted()
+    ev = ex.exact(Yv_d).cpu().numpy()
+    et = ex.exact(Yd).cpu().numpy()
+    fixed = {"kernel": "exponential", "h": hx, "nlist": 512, "k": 100, "m": 1000, "nprobe": 1}
+    for mode, name in ((2, "deannp"), (0, "deann")):
+        run = lambda: ex.query(Yd, 100, 1000, nprobe=1, precision=prec, sample_mode=mode)
+        ms = time_calls(run, 3, torch)
+        fixed[name] = {"qps": nq / (ms / 1e3), "test_rel_err": rel_err(run().cpu().numpy(), et)}
+    fixed["recall"] = recall_at_k(ex, brute, Yv_d, 100, 1, prec)
+    tuned_x, _ = tune(ex, Yv_d, ev, torch, prec)
+    run = lambda: ex.query(Yd, tuned_x["k"], tuned_x["m"], nprobe=tuned_x["nprobe"],
+                           precision=prec)
+    ms = time_calls(run, 3, torch)
+    fixed["tuned_deann"] = {"k": tuned_x["k"], "m": tuned_x["m"], "nprobe": tuned_x["nprobe"],
+                            "qps": nq / (ms / 1e3),
+                            "test_rel_err": rel_err(run().cpu().numpy(), et)}
+    out["fixed_parameters"] = fixed
+    ex.close()
+    brute.close()
+    return out
 
 
 def tune_rs(index, Yv_d, exact_v, ms_list):
@@ -282,13 +399,18 @@ def run_reference(args, rank, world):
     oracle.build()
     X, Y, Yval = make_workload(args)
     spec = workloads.CONFIGS[2]
-    k, m, P = spec["k"], spec["m"], spec["nprobe"]
     # The oracle searches an inverted file exported by the GPU library (its
-    # k-means is not part of the oracle); bandwidth as in the GPU arm.
+    # k-means is not part of the oracle); the bandwidth and the schedule
+    # (k, m, nprobe) are the ones the GPU arm measures with.
     import torch
     import paper_2107_02736_gb300 as pkg
     index = pkg.KDEIndex(torch.from_numpy(X).cuda(), args.kernel, 1.0, nlist=spec["nlist"], seed=1)
-    h, _ = fit_bandwidth(index, torch.from_numpy(Yval).cuda(), spec["target_mu"])
+    Yv_d, Yd = torch.from_numpy(Yval).cuda(), torch.from_numpy(Y).cuda()
+    h, _ = fit_bandwidth(index, Yv_d, spec["target_mu"])
+    exact_v = index.exact(Yv_d).cpu().numpy()
+    exact_t = index.exact(Yd).cpu().numpy()
+    head, sched, _, _ = choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args)
+    k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
     C, assign = index.export_ivf()
     C, assign = C.numpy(), assign.numpy()
     index.close()
@@ -316,31 +438,65 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def roofline(stage, prof, calls, nq, n, d, nlist, k, m, P, peaks, peak_kind):
+def fp32_alu_tflops(sm_mhz=2070.0):
+    """FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes
+    x 2 flops per FMA."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def stage_work(stage, nq, n, d, nlist, k, m, cbar):
+    """Algorithmic (bytes, flops) of one call of a query-path stage: what the
+    method must move or compute, not padded tile work.  cbar = mean candidates
+    per query (the probed lists' sizes)."""
+    dpb = (d + 63) // 64 * 64
+    if stage == "estimate":   # m sampled FP32 rows (+ query, neighbour ids, output)
+        return nq * (m * d * 4 + d * 4 + k * 4 + 4), 0.0
+    if stage == "select":     # candidate values, and the k neighbours' FP32 rows
+        return nq * (cbar * 4 + k * d * 4 + k * 4), 0.0
+    if stage == "scan":       # BF16 lists read once, candidate values written
+        return n * dpb * 2 + nq * cbar * 4, 2.0 * nq * cbar * d
+    if stage == "coarse":     # query x centroid contraction (FP32 CUDA cores)
+        return nq * d * 4, 2.0 * nq * nlist * d
+    return 0, 0.0
+
+
+def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind):
     """Achieved vs peak for one stage of the query path, from its algorithmic
-    bytes or flops per call and its measured device time per call."""
+    bytes or flops per call and its measured device time per call; the bound
+    is whichever of the two takes longer at peak."""
     ms = prof[stage]["ms"] / calls
-    cbar = P * n / nlist
-    if stage == "estimate":
-        # m sampled FP32 rows (plus the query, the neighbour ids and the output)
-        work = nq * (m * d * 4 + d * 4 + k * 4 + 4)
-        r = {"bound": "hbm", "achieved": work / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-             "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
-    elif stage == "scan":
-        work = 2.0 * nq * cbar * d
-        r = {"bound": "tensor", "achieved": work / (ms / 1e3) / 1e12,
-             "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-             "peak_source": f"{peak_kind} bf16_tflops (burst)"}
+    nbytes, flops = stage_work(stage, nq, n, d, nlist, k, m, cbar)
+    fpeak = fp32_alu_tflops() if stage == "coarse" else peaks["bf16_tflops"]
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    t_fl = flops / (fpeak * 1e12)
+    if t_fl > t_hbm:
+        r = {"bound": "alu" if stage == "coarse" else "tensor",
+             "achieved": flops / (ms / 1e3) / 1e12, "peak": fpeak, "unit": "TFLOP/s",
+             "peak_source": ("FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2070 MHz"
+                             if stage == "coarse" else f"{peak_kind} bf16_tflops (burst)")}
     else:
-        # candidate values written by the scan, read by the selection
-        work = nq * cbar * 4
-        r = {"bound": "hbm", "achieved": work / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+        r = {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
              "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
     r["frac"] = r["achieved"] / r["peak"]
     r["traffic"] = ncu_traffic(stage)
     r["stage"] = stage
     r["ms_per_call"] = ms
+    r["t_min_ms"] = 1e3 * max(t_hbm, t_fl)
     return r
+
+
+def mean_candidates(X, Y, C, assign, P):
+    """Mean number of candidates a query scans: the sizes of its P nearest
+    lists (host arithmetic on the exported inverted file)."""
+    sizes = np.bincount(assign, minlength=C.shape[0]).astype(np.float64)
+    Cn = (C.astype(np.float64) ** 2).sum(1)
+    tot = 0.0
+    for a in range(0, Y.shape[0], 2000):
+        Yb = Y[a:a + 2000].astype(np.float64)
+        D = Cn[None, :] - 2.0 * Yb @ C.astype(np.float64).T
+        near = np.argpartition(D, P - 1, axis=1)[:, :P]
+        tot += sizes[near].sum()
+    return tot / Y.shape[0]
 
 
 def profile_case(args):
@@ -395,27 +551,9 @@ def main():
     exact_v = index.exact(Yv_d).cpu().numpy()
     exact_t = index.exact(Yd).cpu().numpy()
 
-    # ---- schedule per precision, on the validation queries ------------------
-    sched, tuned = {}, {}
-    for name, prec in PRECISIONS.items():
-        if args.no_tune:
-            sched[name] = dict(k=spec["k"], m=spec["m"], nprobe=spec["nprobe"], val_ms=0.0,
-                               val_err=None)
-            tuned[name] = []
-        else:
-            sched[name], tuned[name] = tune(index, Yv_d, exact_v, torch, prec)
-    variants = {}
-    for name, prec in PRECISIONS.items():
-        s = sched[name]
-        ms = time_calls(lambda: index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=5,
-                                            precision=prec), 3, torch)
-        err = rel_err(index.query(Yd, s["k"], s["m"], nprobe=s["nprobe"], seed=6,
-                                  precision=prec).cpu().numpy(), exact_t)
-        variants[name] = dict(k=s["k"], m=s["m"], nprobe=s["nprobe"], qps=nq / (ms / 1e3),
-                              test_rel_err=err, val_rel_err=s["val_err"])
-    ok = [v for v in variants if variants[v]["val_rel_err"] is not None
-          and variants[v]["val_rel_err"] <= TARGET_ERR]
-    head = max(ok or variants, key=lambda v: variants[v]["qps"])
+    head, sched, tuned, variants = choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args)
+    prec = PRECISIONS[head]
+    k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
     permuted = deannp_variant(index, Yd, Yv_d, exact_v, exact_t, sched[head],
                               PRECISIONS[head], torch)
     prec = PRECISIONS[head]
@@ -446,13 +584,10 @@ def main():
     index.profile(False)
     prof = index.profile_read(reset=True)
     index.sync()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     errs = [rel_err(o.cpu().numpy(), exact_t) for o in outs]
-    value = nq * world / (ms_step / 1000.0)
+    value = job_throughput(nq, world, ms_step)
 
     # ---- end to end through the host-pointer API ----------------------------
     Yh = torch.from_numpy(Y).pin_memory()
@@ -469,7 +604,8 @@ def main():
 
     # ---- baselines on the same GPU -----------------------------------------
     ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
-    rs_m, _ = tune_rs(index, Yv_d, exact_v, [4000, 16000, 64000, 256000, 1024000])
+    # the paper's grid for m: 10 sqrt(2)^i
+    rs_m, _ = tune_rs(index, Yv_d, exact_v, [int(round(10 * 2 ** (i / 2))) for i in range(0, 43)])
     ms_rs = time_calls(lambda: index.query_rs(Yd, rs_m, seed=3), 2, torch)
     rs_err = rel_err(index.query_rs(Yd, rs_m, seed=4).cpu().numpy(), exact_t)
 
@@ -477,10 +613,22 @@ def main():
     peaks, peak_kind = load_peaks()
     stages = {s: v["ms"] / args.steps for s, v in prof.items() if v["timed"]}
     dom = max(stages, key=stages.get)
-    roof = roofline(dom, prof, args.steps, nq, n, d, spec["nlist"], k, m, P, peaks, peak_kind)
-    others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, P, peaks,
-                          peak_kind) for s in ("scan", "estimate", "select") if s in stages}
+    C_ivf, assign_ivf = index.export_ivf()
+    cbar = mean_candidates(X, Y, C_ivf.numpy(), assign_ivf.numpy(), P)
+    roof = roofline(dom, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks, peak_kind)
+    others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks,
+                          peak_kind) for s in ("coarse", "scan", "select", "estimate")
+              if s in stages}
+    # whole query path: the sum of the stages' times at peak over the step time
+    path_roof = {"t_min_ms": sum(o["t_min_ms"] for o in others.values()),
+                 "t_measured_ms": ms_step, "mean_candidates": cbar}
+    path_roof["frac"] = path_roof["t_min_ms"] / ms_step
     launches = sum(v["launches"] for v in prof.values())
+
+    extras = None
+    if args.schedules and rank == 0:
+        extras = schedules_and_recall(index, X, Yd, Yv_d, exact_v, sched[head], prec, h, torch,
+                                      pkg, dev)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -503,8 +651,9 @@ def main():
         "mean_rel_err": statistics.mean(errs), "max_step_rel_err": max(errs),
         "meets_target": max(errs) <= TARGET_ERR,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
-        "stage_ms_per_step": stages, "stage_rooflines": others, "cpu_baseline": cpu,
-        "build_s": build_s, "variants": variants, "deannp": permuted,
+        "stage_ms_per_step": stages, "stage_rooflines": others, "path_roofline": path_roof,
+        "cpu_baseline": cpu,
+        "build_s": build_s, "variants": variants, "deannp": permuted, "schedules": extras,
         "baselines": {"exact_qps": nq / (ms_exact / 1e3), "rs_qps": nq / (ms_rs / 1e3),
                       "rs_m": rs_m, "rs_rel_err": rs_err},
         "margin_failures": index.margin_failures(),
