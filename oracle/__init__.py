@@ -86,6 +86,11 @@ def _load():
         lib.or_deannp.restype = i32
         lib.or_feistel_perm.argtypes = [u64, i64, i64]
         lib.or_feistel_perm.restype = i64
+        lib.or_loo_exact.argtypes = [P, i64, i32, P, i64, i32, f64, P, P, P]
+        lib.or_loo_exact.restype = i32
+        lib.or_fit_bandwidth.argtypes = [P, i64, i32, P, i64, i32, f64, P, i32, i32, u64, i32,
+                                         f64, P, P]
+        lib.or_fit_bandwidth.restype = i32
         _lib = lib
         return lib
 
@@ -237,6 +242,37 @@ def deann_grad(X, Y, kernel, h, nbr, m, seed, qid_offset=0, gout=None):
                                m, seed, qid_offset, _ptr(g), _ptr(out), _ptr(dY), _ptr(dl))
     _check(st, "deann_grad")
     return out, dY, dl
+
+
+def loo_exact(X, zid, kernel, h):
+    """Exact leave-one-out log-likelihood l(h) (up to a constant) at the
+    training points X[zid] and dl/dlog h; returns (l, dl, points used)."""
+    X = _f32(X)
+    zid = _i32(zid)
+    ll = np.zeros(1)
+    dll = np.zeros(1)
+    used = np.zeros(1, dtype=np.int64)
+    st = _load().or_loo_exact(_ptr(X), X.shape[0], X.shape[1], _ptr(zid), zid.size,
+                              _kern(kernel), float(h), _ptr(ll), _ptr(dll), _ptr(used))
+    _check(st, "loo_exact")
+    return float(ll[0]), float(dll[0]), int(used[0])
+
+
+def fit_bandwidth(X, zid, kernel, h0, nbr, m, seed, iters, lr):
+    """Gradient ascent on log h of the leave-one-out likelihood with the
+    DEANN estimate (X_1 rows in nbr, which should hold each training point
+    itself).  Returns (h_trace[iters + 1], ll_trace[iters])."""
+    X = _f32(X)
+    zid = _i32(zid)
+    nz = zid.size
+    nbr = _i32(nbr).reshape(nz, -1)
+    ht = np.zeros(iters + 1)
+    lt = np.zeros(max(iters, 1))
+    st = _load().or_fit_bandwidth(_ptr(X), X.shape[0], X.shape[1], _ptr(zid), nz, _kern(kernel),
+                                  float(h0), _ptr(nbr), nbr.shape[1], m, seed, iters, float(lr),
+                                  _ptr(ht), _ptr(lt))
+    _check(st, "fit_bandwidth")
+    return ht, lt[:iters]
 
 
 def feistel_perm(seed: int, n: int, idx=None):

@@ -589,3 +589,115 @@ int64_t or_feistel_perm(uint64_t seed, int64_t n, int64_t i) {
   } while ((int64_t)x >= n);
   return (int64_t)x;
 }
+
+/* ------------------------------------------------------------------------
+ * Bandwidth fitting by the leave-one-out likelihood (gradient ascent on
+ * log h with the estimator's derivative in log h; the paper tunes h by
+ * bisection only, this is the fitting loop the adjoint serves).
+ *
+ * The kernels carry no normalising constant; each normalises as c h^d
+ * (Gaussian (2 pi)^{d/2} h^d, exponential and Laplacian a constant times
+ * h^d), so up to a constant the log-likelihood of a held-out point z under
+ * the density built from X \ {z} is
+ *     log KDE_{-z}(z) - d log h,   KDE_{-z}(z) = (n KDE(z) - 1) / (n - 1),
+ * since K(z, z) = 1 for the three kernels.  Its derivative in log h is
+ *     (n / (n - 1)) dKDE(z)/dlog h / KDE_{-z}(z) - d.
+ * l(h) averages over training points z_j = x_{zid[j]}.  A point whose own
+ * term is nearly all of its estimate (n KDE(z) - 1 <= 1e-3 n KDE(z)) has no
+ * usable held-out density and is left out of both averages.
+ * ---------------------------------------------------------------------- */
+static void loo_terms(int64_t n, int64_t nz, const double* out, const double* dlogh,
+                      double* sum_log, double* sum_ratio, int64_t* used) {
+  double sl = 0.0, sr = 0.0;
+  int64_t u = 0;
+  for (int64_t j = 0; j < nz; ++j) {
+    const double nk = (double)n * out[j];
+    if (nk - 1.0 <= 1e-3 * nk) continue;
+    const double loo = (nk - 1.0) / (double)(n - 1);
+    const double dloo = (double)n * dlogh[j] / (double)(n - 1);
+    sl += log(loo);
+    sr += dloo / loo;
+    ++u;
+  }
+  *sum_log = sl;
+  *sum_ratio = sr;
+  *used = u;
+}
+
+static float* gather_rows_f(const float* X, int d, const int32_t* zid, int64_t nz) {
+  float* Y = (float*)malloc(sizeof(float) * (size_t)nz * (size_t)d);
+  for (int64_t j = 0; j < nz; ++j)
+    memcpy(Y + j * (int64_t)d, X + (int64_t)zid[j] * d, sizeof(float) * (size_t)d);
+  return Y;
+}
+
+/* Exact l(h) and dl/dlog h (Section 2 definition for KDE(z)). */
+int or_loo_exact(const float* X, int64_t n, int d, const int32_t* zid, int64_t nz, int kern,
+                 double h, double* ll, double* dll, int64_t* used) {
+  if (n < 2 || nz < 1) return OR_EINVAL;
+  for (int64_t j = 0; j < nz; ++j)
+    if (zid[j] < 0 || zid[j] >= n) return OR_EINVAL;
+  float* Y = gather_rows_f(X, d, zid, nz);
+  double* out = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* dl = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* dY = (double*)malloc(sizeof(double) * (size_t)nz * (size_t)d);
+  or_exact(X, n, d, Y, nz, kern, h, out);
+  or_exact_grad(X, n, d, Y, nz, kern, h, dY, dl);
+  double sl, sr;
+  int64_t u;
+  loo_terms(n, nz, out, dl, &sl, &sr, &u);
+  int status = OR_OK;
+  if (u == 0) {
+    status = OR_EINVAL;
+  } else {
+    *ll = sl / (double)u - (double)d * log(h);
+    *dll = sr / (double)u - (double)d;
+  }
+  if (used) *used = u;
+  free(Y);
+  free(out);
+  free(dl);
+  free(dY);
+  return status;
+}
+
+/* Gradient ascent on log h with the DEANN estimate: X_1 of z_j is row j of
+ * nbr (nz x kw, -1 pads; it should contain z_j itself, so that KDE_{-z}
+ * follows from the estimate); iteration t draws its samples with seed + t
+ * and query ids j; log h <- log h + lr g_t.  h_trace[0..iters],
+ * ll_trace[0..iters) (l at the h before each update). */
+int or_fit_bandwidth(const float* X, int64_t n, int d, const int32_t* zid, int64_t nz, int kern,
+                     double h0, const int32_t* nbr, int kw, int m, uint64_t seed, int iters,
+                     double lr, double* h_trace, double* ll_trace) {
+  if (n < 2 || nz < 1 || !(h0 > 0.0) || iters < 0) return OR_EINVAL;
+  for (int64_t j = 0; j < nz; ++j)
+    if (zid[j] < 0 || zid[j] >= n) return OR_EINVAL;
+  float* Y = gather_rows_f(X, d, zid, nz);
+  double* out = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* dl = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* dY = (double*)malloc(sizeof(double) * (size_t)nz * (size_t)d);
+  double h = h0;
+  int status = OR_OK;
+  h_trace[0] = h;
+  for (int t = 0; t < iters && status == OR_OK; ++t) {
+    status = or_deann_grad(X, n, d, Y, nz, kern, h, nbr, kw, m, seed + (uint64_t)t, 0, NULL,
+                           out, dY, dl);
+    if (status != OR_OK) break;
+    double sl, sr;
+    int64_t u;
+    loo_terms(n, nz, out, dl, &sl, &sr, &u);
+    if (u == 0) {
+      status = OR_EINVAL;
+      break;
+    }
+    ll_trace[t] = sl / (double)u - (double)d * log(h);
+    const double g = sr / (double)u - (double)d;
+    h = exp(log(h) + lr * g);
+    h_trace[t + 1] = h;
+  }
+  free(Y);
+  free(out);
+  free(dl);
+  free(dY);
+  return status;
+}

@@ -494,3 +494,94 @@ def test_rsp_consecutive_windows_cover_dataset():
     out, ell = oracle.deannp(X, Yrep, "exponential", 0.5, perm, None, m=20, ell0=7)
     assert ell == 7
     assert math.isclose(out.mean(), oracle.exact(X, Y, "exponential", 0.5)[0], rel_tol=1e-13)
+
+
+# ------------------------------------------------------ bandwidth fitting ---
+def _mixture_2d(n=240, seed=21):
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal((3, 2)) * 3.0
+    X = (c[rng.integers(0, 3, n)] + rng.standard_normal((n, 2))).astype(np.float32)
+    return X
+
+
+def test_loo_shortcut_equals_deleting_the_point():
+    """KDE_{-z}(z) = (n KDE(z) - 1) / (n - 1): recompute the KDE over X with z
+    removed, for each kernel."""
+    X = _mixture_2d(60)
+    for kern in ("gaussian", "exponential", "laplacian"):
+        full = oracle.exact(X, X[:7], kern, 0.9)
+        for j in range(7):
+            rest = np.delete(X, j, axis=0)
+            loo = oracle.exact(rest, X[j:j + 1], kern, 0.9)[0]
+            assert math.isclose((60 * full[j] - 1.0) / 59.0, loo, rel_tol=1e-12)
+
+
+def test_loo_likelihood_is_the_normalised_gaussian_density():
+    """For the Gaussian kernel l(h) - (d/2) log(2 pi) is the mean log of the
+    textbook leave-one-out density (1/(n-1)) sum_{i != j} N(z_j; x_i, h^2 I)."""
+    X = _mixture_2d(80)
+    zid = np.arange(0, 80, 3, dtype=np.int32)
+    h = 0.7
+    ll, _, used = oracle.loo_exact(X, zid, "gaussian", h)
+    assert used == zid.size
+    Xd = X.astype(np.float64)
+    logs = []
+    for j in zid:
+        d2 = ((np.delete(Xd, j, axis=0) - Xd[j]) ** 2).sum(1)
+        p = np.exp(-d2 / (2 * h * h)).sum() / (79 * (2 * math.pi * h * h))
+        logs.append(math.log(p))
+    assert math.isclose(ll - math.log(2 * math.pi), np.mean(logs), rel_tol=1e-12, abs_tol=1e-12)
+
+
+@pytest.mark.parametrize("kern", ["gaussian", "exponential", "laplacian"])
+def test_loo_derivative_matches_central_differences(kern):
+    X = _mixture_2d(120)
+    zid = np.arange(0, 120, 2, dtype=np.int32)
+    h, eps = 0.8, 1e-5
+    _, dll, _ = oracle.loo_exact(X, zid, kern, h)
+    lp, _, _ = oracle.loo_exact(X, zid, kern, h * math.exp(eps))
+    lm, _, _ = oracle.loo_exact(X, zid, kern, h * math.exp(-eps))
+    assert math.isclose(dll, (lp - lm) / (2 * eps), rel_tol=1e-6, abs_tol=1e-8)
+
+
+def test_fit_with_all_points_as_neighbours_is_exact_and_converges():
+    """X_1 = X makes the estimate exact: the first step follows the exact
+    gradient, and the ascent ends at the maximiser of the exact l(h), found
+    independently by golden-section search."""
+    X = _mixture_2d(150)
+    n = X.shape[0]
+    zid = np.arange(0, n, 3, dtype=np.int32)
+    nbr = np.tile(np.arange(n, dtype=np.int32), (zid.size, 1))
+    # every training point keeps a held-out density for h >= 0.4 on this data
+    h0, lr = 0.45, 0.5
+    ht, lt = oracle.fit_bandwidth(X, zid, "gaussian", h0, nbr, 50, 5, 40, lr)
+    ll0, dll0, _ = oracle.loo_exact(X, zid, "gaussian", h0)
+    assert math.isclose(lt[0], ll0, rel_tol=1e-12)
+    assert math.isclose(ht[1], h0 * math.exp(lr * dll0), rel_tol=1e-12)
+    f = lambda lh: -oracle.loo_exact(X, zid, "gaussian", math.exp(lh))[0]
+    a, b = math.log(0.4), math.log(3.0)
+    g = (math.sqrt(5) - 1) / 2
+    for _ in range(80):
+        c, d = b - g * (b - a), a + g * (b - a)
+        if f(c) < f(d):
+            b = d
+        else:
+            a = c
+    h_star = math.exp((a + b) / 2)
+    assert math.isclose(ht[-1], h_star, rel_tol=1e-3)
+    assert np.all(np.diff(lt) > -1e-12)  # the likelihood never decreases on this path
+    assert oracle.loo_exact(X, zid, "gaussian", 0.35)[2] < zid.size  # the guard is live below
+
+
+def test_fit_with_sampling_tracks_the_exact_optimum():
+    """With k near neighbours (plus the point itself) and m samples, the
+    noisy ascent still settles near the exact maximiser."""
+    X = _mixture_2d(600, seed=3)
+    n = X.shape[0]
+    zid = np.arange(0, n, 5, dtype=np.int32)
+    nb, _ = oracle.knn(X, X[zid], 40)  # holds the point itself first
+    ht, _ = oracle.fit_bandwidth(X, zid, "gaussian", 0.3, nb, 400, 9, 60, 0.5)
+    f = lambda h: oracle.loo_exact(X, zid, "gaussian", h)[0]
+    hs = np.exp(np.linspace(math.log(0.3), math.log(3.0), 200))
+    h_star = hs[int(np.argmax([f(h) for h in hs]))]
+    assert abs(math.log(np.mean(ht[-20:]) / h_star)) < 0.1
