@@ -229,6 +229,36 @@ kde_status kde_mean_shift(kde_index* index, float* Y, int64_t nq, int32_t steps,
                           int32_t m, int32_t nprobe, uint64_t seed, float* est,
                           const kde_opts* opts);
 
+/* kde_fit_bandwidth -- fit h by gradient ascent on the leave-one-out
+ * log-likelihood of the normalised KDE (the paper sets h by bisection on a
+ * target KDE value; this is the fitting loop that the estimator's derivative
+ * in log h serves).  All three kernels normalise as a constant times h^d, so
+ * up to a constant
+ *   l(h) = mean_j log KDE_{-z_j}(z_j) - d log h,
+ *   KDE_{-z}(z) = (n KDE(z) - 1) / (n - 1)            (K(z, z) = 1),
+ *   dl/dlog h = mean_j (n / (n - 1)) dKDE(z_j)/dlog h / KDE_{-z_j}(z_j) - d,
+ * with KDE and its derivative the DEANN estimate and its adjoint, X_1 of z_j =
+ * {z_j} and its k nearest points from kde_search (so that the point's own
+ * term is exact and the held-out value follows), samples drawn with
+ * seed + t at iteration t and query ids j.  The library evaluates the
+ * held-out estimate directly (the point's own term left out of the neighbour
+ * sum, weights over n - 1 points), which is the same value without the
+ * cancellation of n KDE - 1.  A point with no held-out density (every other
+ * kernel value underflowed) is left out of the means.  Step:
+ * log h <- log h + lr dl/dlog h; the index keeps the final h.
+ *   zid       nz training point ids (rows of the indexed X), host or device.
+ *   k         0 <= k <= 1023 search neighbours (nprobe as in kde_search).
+ *   m         samples per training point (sample_mode 0 or 1).
+ *   h_trace   HOST, iters + 1 floats: h before the first and after each step.
+ *   ll_trace  HOST or NULL, iters doubles: l(h) before each step.
+ *   nbr_out   NULL, or nz x (k + 1) ids (host or device): the X_1 rows used.
+ * Synchronous.  Errors: EINVAL (arguments, no usable training point, a step
+ * leaving h > 0 finite), ELIMIT, ECUDA. */
+kde_status kde_fit_bandwidth(kde_index* index, const int32_t* zid, int64_t nz, int32_t k,
+                             int32_t m, int32_t nprobe, uint64_t seed, int32_t iters, float lr,
+                             float* h_trace, double* ll_trace, int32_t* nbr_out,
+                             const kde_opts* opts);
+
 /* kde_sync -- wait for the index's work on opts->stream and report (then
  * clear) errors raised by kernels of earlier device-pointer calls:
  * KDE_ELIMIT (draw cap), KDE_EINVAL (neighbour id >= n). */

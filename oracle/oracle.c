@@ -602,9 +602,9 @@ int64_t or_feistel_perm(uint64_t seed, int64_t n, int64_t i) {
  *     log KDE_{-z}(z) - d log h,   KDE_{-z}(z) = (n KDE(z) - 1) / (n - 1),
  * since K(z, z) = 1 for the three kernels.  Its derivative in log h is
  *     (n / (n - 1)) dKDE(z)/dlog h / KDE_{-z}(z) - d.
- * l(h) averages over training points z_j = x_{zid[j]}.  A point whose own
- * term is nearly all of its estimate (n KDE(z) - 1 <= 1e-3 n KDE(z)) has no
- * usable held-out density and is left out of both averages.
+ * l(h) averages over training points z_j = x_{zid[j]}.  A point with no
+ * held-out density (KDE_{-z}(z) <= 0: every other kernel value underflowed)
+ * is left out of both averages.
  * ---------------------------------------------------------------------- */
 static void loo_terms(int64_t n, int64_t nz, const double* out, const double* dlogh,
                       double* sum_log, double* sum_ratio, int64_t* used) {
@@ -612,7 +612,7 @@ static void loo_terms(int64_t n, int64_t nz, const double* out, const double* dl
   int64_t u = 0;
   for (int64_t j = 0; j < nz; ++j) {
     const double nk = (double)n * out[j];
-    if (nk - 1.0 <= 1e-3 * nk) continue;
+    if (!(nk - 1.0 > 0.0)) continue;
     const double loo = (nk - 1.0) / (double)(n - 1);
     const double dloo = (double)n * dlogh[j] / (double)(n - 1);
     sl += log(loo);

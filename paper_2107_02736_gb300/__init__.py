@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import numpy as np
 
 import torch
 
@@ -89,6 +90,7 @@ def load_library():
         "kde_stats": [P, P, O],
         "kde_reserve": [P, i64, i32, i32, i32, O],
         "kde_prepare_permuted": [P, P, O],
+        "kde_fit_bandwidth": [P, P, i64, i32, i32, i32, u64, i32, f32, P, P, P, O],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +221,25 @@ class KDEIndex:
         with torch.cuda.device(self._device):
             _check(_lib.kde_prepare_permuted(self._h, _ptr(perm), ctypes.byref(self._opts())))
         return perm
+
+    def fit_bandwidth(self, zid, k, m, nprobe=1, seed=0, iters=20, lr=0.5, precision=0,
+                      sample_mode=0):
+        """Gradient ascent on log h of the leave-one-out likelihood at the
+        training points X[zid] with the DEANN estimate and its adjoint.
+        Returns (h_trace, ll_trace, X_1 rows) as CPU arrays; the index keeps the
+        final h."""
+        zid = _i32(zid).cpu().contiguous()
+        nz = zid.numel()
+        ht = np.zeros(iters + 1, dtype=np.float32)
+        lt = np.zeros(max(iters, 1), dtype=np.float64)
+        nb = torch.empty((nz, k + 1), dtype=torch.int32)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_fit_bandwidth(
+                self._h, _ptr(zid), nz, int(k), int(m), int(nprobe), int(seed) & (2**64 - 1),
+                int(iters), float(lr), ht.ctypes.data_as(ctypes.c_void_p),
+                lt.ctypes.data_as(ctypes.c_void_p), _ptr(nb),
+                ctypes.byref(self._opts(precision, sample_mode, host=True))))
+        return ht, lt[:iters], nb.numpy()
 
     def sync(self):
         with torch.cuda.device(self._device):

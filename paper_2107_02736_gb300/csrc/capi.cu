@@ -234,6 +234,10 @@ struct CallBufs {
   int32_t* win_kk = nullptr;
   float* win_s1 = nullptr;
   double* win_part = nullptr;    // nq x nslices
+  // bandwidth fitting
+  int32_t* fit_zid = nullptr;    // nq training point ids
+  int32_t* fit_nbr = nullptr;    // nq x fit_k search neighbours
+  double* fit_red = nullptr;     // leave-one-out sums
   SearchBufs search;
 };
 
@@ -251,6 +255,7 @@ struct CallShape {
   bool exact = false;
   bool exact_tc = false;   // tensor-core exact: BF16 parts of the queries
   bool window = false;     // permuted-window estimator (sample_mode 2)
+  int fit_k = -1;          // >= 0: bandwidth fitting with fit_k search neighbours
 };
 
 void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -281,6 +286,11 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
       cb.win_s1 = b.take<float>(nq);
       cb.win_part = b.take<double>((size_t)nq * cb.win.nslices);
     }
+  }
+  if (c.fit_k >= 0) {
+    cb.fit_zid = b.take<int32_t>(nq);
+    cb.fit_nbr = b.take<int32_t>((size_t)nq * std::max(c.fit_k, 1));
+    cb.fit_red = b.take<double>(4);
   }
   if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
 }
@@ -426,6 +436,7 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.out = nullptr;
   a.samples = nullptr;
   a.rs = 0;
+  a.loo = 0;
   a.gout = nullptr;
   a.dY = nullptr;
   a.dlogh = nullptr;
@@ -1144,6 +1155,98 @@ kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, in
                        host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
   if (est) TRY(copy_out(est, cb.out, sizeof(float) * nq, host, st));
   return finish_call(ix, host, st);
+}
+
+kde_status kde_fit_bandwidth(kde_index* ix, const int32_t* zid, int64_t nz, int32_t k, int32_t m,
+                             int32_t nprobe, uint64_t seed, int32_t iters, float lr,
+                             float* h_trace, double* ll_trace, int32_t* nbr_out,
+                             const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  if (o->sample_mode == 2)
+    return fail(KDE_EINVAL, "bandwidth fitting supports sample_mode 0 and 1");
+  if (nz < 1 || nz > INT32_MAX) return fail(KDE_EINVAL, "nz must be in [1, 2^31 - 1]");
+  if (k < 0 || k > kMaxK - 1)
+    return fail(KDE_EINVAL, "k must be in [0, %d] (X_1 holds the point and k neighbours)",
+                kMaxK - 1);
+  TRY(check_est_args(ix, nz, k + 1, m, o));
+  if (k > 0) TRY(check_search_args(ix, nz, k, nprobe));
+  if (ix->n < 2) return fail(KDE_EINVAL, "leave-one-out needs n >= 2");
+  if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
+  if (iters < 0) return fail(KDE_EINVAL, "iters must be >= 0");
+  if (!std::isfinite(lr)) return fail(KDE_EINVAL, "lr must be finite");
+  if (zid == nullptr || h_trace == nullptr) return fail(KDE_EINVAL, "zid and h_trace must not be NULL");
+  DeviceGuard g(ix->device);
+  const Space zs = space_of(zid, ix->device);
+  if (zs == SPACE_FOREIGN) return fail(KDE_ESTATE, "zid lives on another device");
+  cudaStream_t st = stream_of(o);
+  std::vector<int32_t> hz((size_t)nz);
+  if (zs == SPACE_HOST) {
+    std::copy(zid, zid + nz, hz.begin());
+  } else {
+    CK(cudaMemcpyAsync(hz.data(), zid, sizeof(int32_t) * nz, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  for (int64_t j = 0; j < nz; ++j)
+    if (hz[j] < 0 || (int64_t)hz[j] >= ix->n) return fail(KDE_EINVAL, "zid[%lld] out of range", (long long)j);
+  CallShape c;
+  c.nq = nz;
+  c.k = k + 1;
+  c.m = m;
+  c.P = std::max(1, nprobe);
+  c.search = k > 0;
+  c.host = true;
+  c.need_out = true;
+  c.need_nbr = true;
+  c.grad = true;
+  c.fit_k = k;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  CK(cudaMemcpyAsync(cb.fit_zid, hz.data(), sizeof(int32_t) * nz, cudaMemcpyHostToDevice, st));
+  {
+    StageTimer t(ix, ST_STAGE, st, 2);
+    launch_gather_rows(ix->X, ix->dp, cb.fit_zid, nz, cb.Yp, st);
+    launch_query_norms(cb.Yp, nz, ix->dp, cb.Yn, st);
+  }
+  if (k > 0)
+    TRY(run_search(ix, cb, nz, k, nprobe, o->precision, cb.fit_nbr, nullptr, nullptr, st, true));
+  launch_prepend_self(cb.fit_zid, cb.fit_nbr, nz, k, cb.nbr, st);
+  float h = ix->h;
+  h_trace[0] = h;
+  for (int t = 0; t < iters; ++t) {
+    SampleArgs a = sample_args(ix, cb, nz, cb.nbr, k + 1, m, seed + (uint64_t)t, o);
+    a.loo = 1;  // out, dlogh: the estimate over X \ {z} at z and its derivative
+    a.out = cb.out;
+    a.dY = cb.dY;
+    a.dlogh = cb.dlogh;
+    {
+      StageTimer tm(ix, ST_GRAD, st, 2);
+      launch_estimate_grad(a, st);
+      launch_loo_reduce(cb.out, cb.dlogh, nz, cb.fit_red, st);
+    }
+    double red[3];
+    CK(cudaMemcpyAsync(red, cb.fit_red, sizeof red, cudaMemcpyDeviceToHost, st));
+    int64_t margin = 0;
+    kde_status es = collect_errors(ix, st, &margin);  // synchronises the stream
+    ix_margin_accumulate(ix, margin);
+    if (es != KDE_OK) return es;
+    if (red[2] < 1.0)
+      return fail(KDE_EINVAL, "no training point keeps a held-out density at h = %g", (double)h);
+    const double ll = red[0] / red[2] - (double)ix->d * std::log((double)h);
+    const double gr = red[1] / red[2] - (double)ix->d;
+    if (ll_trace) ll_trace[t] = ll;
+    h = (float)std::exp(std::log((double)h) + (double)lr * gr);
+    if (!(h > 0.f) || !std::isfinite(h)) return fail(KDE_EINVAL, "the step left h > 0 finite");
+    ix->h = h;
+    h_trace[t + 1] = h;
+  }
+  if (nbr_out) {
+    const Space ns = space_of(nbr_out, ix->device);
+    if (ns == SPACE_FOREIGN) return fail(KDE_ESTATE, "nbr_out lives on another device");
+    TRY(copy_out(nbr_out, cb.nbr, sizeof(int32_t) * nz * (k + 1), ns == SPACE_HOST, st));
+  }
+  return finish_call(ix, true, st);
 }
 
 kde_status kde_sync(kde_index* ix, const kde_opts* opts) {

@@ -250,6 +250,7 @@ struct SampleArgs {
   float* out;                // [nq] estimates (nullable)
   int32_t* samples;          // [nq x m] sample indices (nullable)
   int rs;                    // 1: plain random sampling (ignore nbr)
+  int loo;                   // adjoint: estimate KDE over X minus the row's first id, at it
   // adjoint
   const float* gout;         // [nq] (grad only)
   float* dY;                 // [nq x d] (grad only)
@@ -303,5 +304,10 @@ void launch_window_finish(const SampleArgs& a, const WindowPlan& p, const int32_
 void launch_estimate_grad(const SampleArgs& a, cudaStream_t s);
 void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,
                               int64_t nq, float h, cudaStream_t s);
+// bandwidth fitting: X_1 rows [z, its k neighbours], and the leave-one-out sums
+void launch_prepend_self(const int32_t* zid, const int32_t* nbr, int64_t nz, int k, int32_t* out,
+                         cudaStream_t s);
+void launch_loo_reduce(const float* loo, const float* dloo, int64_t nz, double* red,
+                       cudaStream_t s);
 
 }  // namespace deann

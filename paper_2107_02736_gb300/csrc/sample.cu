@@ -638,12 +638,32 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) gacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   float est = 0.f, sl = 0.f;
-  const float w1 = a.rs ? 0.f : (float)(1.0 / nd);
-  if (kk > 0) grad_rows<G, NV>(a.X, a.dp, ys, sm.nb, kk, a.kern, a.h, w1, gacc, est, sl);
+  // Held-out mode: the row's first id z is the query point itself.  The
+  // estimate is of KDE over X \ {z} at z: z stays in X_1 (never sampled) but
+  // its own term is left out, and the weights use n - 1 points.
+  const double nw = a.loo ? nd - 1.0 : nd;
+  const int* rows1 = sm.nb;
+  int k1 = kk;
+  if (a.loo && k > 0) {
+    const int32_t z = a.nbr[q * a.k];
+    int w = 0;
+    if (tid == 0) {
+      for (int t = 0; t < kk; ++t)
+        if (sm.nb[t] != z) tmp[w++] = sm.nb[t];
+      sm.cnt = w;
+    }
+    __syncthreads();
+    rows1 = tmp;
+    k1 = sm.cnt;
+    __syncthreads();
+  }
+  const float w1 = a.rs ? 0.f : (float)(1.0 / nw);
+  if (k1 > 0) grad_rows<G, NV>(a.X, a.dp, ys, rows1, k1, a.kern, a.h, w1, gacc, est, sl);
   bool ok = true;
   if (sampled) {
-    const float w2 = a.mode == 1 || a.rs ? (float)(1.0 / (double)a.m)
-                                         : (float)((nd - (double)kk) / (nd * (double)a.m));
+    const float w2 = a.rs ? (float)(1.0 / (double)a.m)
+                     : a.mode == 1 ? (float)(nd / (nw * (double)a.m))
+                                   : (float)((nd - (double)kk) / (nw * (double)a.m));
     const int64_t cap = a.mode == 1 ? (int64_t)a.m : 64 * (int64_t)a.m + 4096;
     int64_t t0 = 0;
     int got = 0;
@@ -758,6 +778,68 @@ void launch_window_finish(const SampleArgs& a, const WindowPlan& p, const int32_
   if (a.nq <= 0) return;
   k_window_finish<<<(unsigned)((a.nq + 255) / 256), 256, 0, s>>>(a.nq, a.n, a.m, p.nslices,
                                                                   dcnt, kk, s1, part, a.out);
+}
+
+namespace {
+// Row j of X_1 for bandwidth fitting: the training point itself, then its k
+// search neighbours (a repeat of the point counts once).
+__global__ void k_prepend_self(const int32_t* __restrict__ zid, const int32_t* __restrict__ nbr,
+                               int64_t nz, int k, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t w = (int64_t)k + 1;
+  if (i >= nz * w) return;
+  const int64_t j = i / w, c = i % w;
+  out[i] = c == 0 ? zid[j] : nbr[j * k + (c - 1)];
+}
+
+// Leave-one-out sums over the training points, in a fixed order (one CTA):
+// red[0] = sum log KDE_{-z}, red[1] = sum dKDE_{-z}/dlog h / KDE_{-z},
+// red[2] = points used; loo[j] is the held-out estimate at z_j, dloo[j] its
+// derivative.  A point with no held-out density (loo <= 0: every other kernel
+// value underflowed) is left out.
+__global__ void __launch_bounds__(1024) k_loo_reduce(const float* __restrict__ loo,
+                                                     const float* __restrict__ dloo, int64_t nz,
+                                                     double* __restrict__ red) {
+  __shared__ double s0[1024], s1[1024], s2[1024];
+  const int tid = threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int64_t j = tid; j < nz; j += 1024) {
+    const double v = (double)loo[j];
+    if (!(v > 0.0)) continue;
+    a += log(v);
+    b += (double)dloo[j] / v;
+    c += 1.0;
+  }
+  s0[tid] = a;
+  s1[tid] = b;
+  s2[tid] = c;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (tid < o) {
+      s0[tid] += s0[tid + o];
+      s1[tid] += s1[tid + o];
+      s2[tid] += s2[tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    red[0] = s0[0];
+    red[1] = s1[0];
+    red[2] = s2[0];
+  }
+}
+}  // namespace
+
+void launch_prepend_self(const int32_t* zid, const int32_t* nbr, int64_t nz, int k, int32_t* out,
+                         cudaStream_t s) {
+  const int64_t total = nz * ((int64_t)k + 1);
+  if (total <= 0) return;
+  k_prepend_self<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(zid, nbr, nz, k, out);
+}
+
+void launch_loo_reduce(const float* loo, const float* dloo, int64_t nz, double* red,
+                       cudaStream_t s) {
+  k_loo_reduce<<<1, 1024, 0, s>>>(loo, dloo, nz, red);
 }
 
 void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,

@@ -392,3 +392,46 @@ def test_draw_cap_reported(pkg):
     nbr = np.tile(np.arange(999, dtype=np.int32), (2, 1))
     with pytest.raises(pkg.KDEError, match="ELIMIT"):
         index.query_with_neighbors(torch.from_numpy(Y), torch.from_numpy(nbr), 10)
+
+
+# ------------------------------------------------------ bandwidth fitting ---
+@pytest.mark.parametrize("kernel", ["gaussian", "exponential", "laplacian"])
+def test_fit_bandwidth_matches_oracle_trace(pkg, kernel):
+    """The library's gradient-ascent loop on the leave-one-out likelihood
+    follows the oracle's trace step by step, given the same X_1 rows."""
+    X, _, _ = workloads.mixture_iso(n=4000, d=8, nq=1)
+    zid = np.arange(0, 4000, 17, dtype=np.int32)
+    h0 = {"gaussian": 1.0, "exponential": 1.0, "laplacian": 3.0}[kernel]
+    index = pkg.KDEIndex(_dev(X), kernel, h0, nlist=16, seed=2)
+    ht, lt, nb = index.fit_bandwidth(zid, 30, 300, nprobe=4, seed=5, iters=8, lr=0.3)
+    assert np.all(nb[:, 0] == zid)
+    wh, wl = oracle.fit_bandwidth(X, zid, kernel, h0, nb, 300, 5, 8, 0.3)
+    # FP32 estimates against FP64: each step moves log h by lr * g, and g
+    # carries about 1e-6 relative error
+    assert np.allclose(ht, wh, rtol=1e-4)
+    assert np.allclose(lt, wl, rtol=1e-5, atol=1e-5)
+    assert index.h == pytest.approx(float(ht[-1]))
+
+
+def test_fit_bandwidth_reaches_exact_optimum(pkg):
+    """Run to convergence, the fitted h lies at the exact leave-one-out
+    maximiser (the oracle's exact l(h) on a grid)."""
+    X, _, _ = workloads.mixture_iso(n=3000, d=4, nq=1)
+    zid = np.arange(0, 3000, 10, dtype=np.int32)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 0.5, nlist=8, seed=3)
+    ht, _, _ = index.fit_bandwidth(zid, 100, 2000, nprobe=8, seed=1, iters=60, lr=0.4)
+    hs = np.exp(np.linspace(np.log(0.2), np.log(3.0), 120))
+    ll = [oracle.loo_exact(X, zid, "gaussian", h)[0] for h in hs]
+    h_star = hs[int(np.argmax(ll))]
+    assert abs(np.log(np.mean(ht[-10:]) / h_star)) < 0.05
+
+
+def test_fit_bandwidth_argument_errors(pkg):
+    X, _, _ = workloads.mixture_iso(n=500, d=4, nq=1)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 1.0)
+    with pytest.raises(pkg.KDEError):
+        index.fit_bandwidth(np.array([0, 500], np.int32), 5, 10)   # id out of range
+    with pytest.raises(pkg.KDEError):
+        index.fit_bandwidth(np.array([0, 1], np.int32), 1024, 10)  # k > 1023
+    with pytest.raises(pkg.KDEError):
+        index.fit_bandwidth(np.array([0, 1], np.int32), 5, 10, sample_mode=2)
