@@ -359,6 +359,54 @@ def schedules_and_recall(index, X, Yd, Yv_d, exact_v, head_sched, prec, h, torch
     return out
 
 
+def differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev):
+    """The adjoint and what it serves, measured beside the headline: the
+    gradient call on the headline workload and schedule (its rows are the
+    forward's, regathered), 20 mean-shift steps on the anisotropic-mixture
+    workload, and 20 steps of leave-one-out bandwidth fitting on 10,000 points
+    of the headline dataset (untimed extras; h is restored afterwards)."""
+    nq, d = Yd.shape
+    out = {}
+    _, nbr = index.query(Yd, k, m, nprobe=P, seed=3, precision=prec, return_neighbors=True)
+    run = lambda: index.grad_with_neighbors(Yd, nbr, m, seed=3)
+    ms = time_calls(run, 3, torch)
+    nbytes = nq * ((k + m) * d * 4 + 2 * d * 4 + k * 4)
+    out["adjoint"] = {"k": k, "m": m, "qps": nq / (ms / 1e3), "ms_per_call": ms,
+                      "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                      "frac": nbytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    w = workloads.make(4)
+    sp = workloads.CONFIGS[4]
+    ms_index = pkg.KDEIndex(torch.from_numpy(w.X).to(dev), "gaussian", w.h, nlist=sp["nlist"],
+                            seed=1)
+    Y4 = torch.from_numpy(w.Y).to(dev)
+    ms_index.mean_shift(Y4.clone(), 1, sp["k"], sp["m"], nprobe=sp["nprobe"], seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms_index.mean_shift(Y4.clone(), 20, sp["k"], sp["m"], nprobe=sp["nprobe"], seed=2)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["mean_shift"] = {"workload": w.name, "queries": int(w.Y.shape[0]), "steps": 20,
+                         "k": sp["k"], "m": sp["m"], "nprobe": sp["nprobe"], "seconds": sec,
+                         "query_steps_per_s": w.Y.shape[0] * 20 / sec}
+    ms_index.close()
+    rng = np.random.default_rng(77)
+    zid = np.sort(rng.choice(X.shape[0], 10_000, replace=False)).astype(np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lr = 0.3 / d  # dl/dlog h scales with d
+    ht, lt, _ = index.fit_bandwidth(zid, 100, 1000, nprobe=P, seed=9, iters=20, lr=lr,
+                                    precision=prec)
+    sec = time.perf_counter() - t0
+    out["bandwidth_fit"] = {"points": int(zid.size), "k": 100, "m": 1000, "iters": 20,
+                            "lr": lr, "seconds": sec, "ms_per_iter": 1e3 * sec / 20,
+                            "h_start": float(ht[0]), "h_final": float(ht[-1]),
+                            "loo_loglik_first": float(lt[0]), "loo_loglik_last": float(lt[-1]),
+                            "note": "leave-one-out maximum-likelihood h; the headline h is "
+                                    "bisected to a mean KDE of 1e-3 instead"}
+    index.set_bandwidth(h)
+    return out
+
+
 def tune_rs(index, Yv_d, exact_v, ms_list):
     err = None
     for m in ms_list:
@@ -625,10 +673,11 @@ def main():
     path_roof["frac"] = path_roof["t_min_ms"] / ms_step
     launches = sum(v["launches"] for v in prof.values())
 
-    extras = None
+    extras = forms = None
     if args.schedules and rank == 0:
         extras = schedules_and_recall(index, X, Yd, Yv_d, exact_v, sched[head], prec, h, torch,
                                       pkg, dev)
+        forms = differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -654,6 +703,7 @@ def main():
         "stage_ms_per_step": stages, "stage_rooflines": others, "path_roofline": path_roof,
         "cpu_baseline": cpu,
         "build_s": build_s, "variants": variants, "deannp": permuted, "schedules": extras,
+        "forms": forms,
         "baselines": {"exact_qps": nq / (ms_exact / 1e3), "rs_qps": nq / (ms_rs / 1e3),
                       "rs_m": rs_m, "rs_rel_err": rs_err},
         "margin_failures": index.margin_failures(),

@@ -245,7 +245,8 @@ kde_status kde_mean_shift(kde_index* index, float* Y, int64_t nq, int32_t steps,
  * sum, weights over n - 1 points), which is the same value without the
  * cancellation of n KDE - 1.  A point with no held-out density (every other
  * kernel value underflowed) is left out of the means.  Step:
- * log h <- log h + lr dl/dlog h; the index keeps the final h.
+ * log h <- log h + lr dl/dlog h (dl/dlog h grows with d: lr of order 1/d
+ * keeps the steps stable); the index keeps the final h.
  *   zid       nz training point ids (rows of the indexed X), host or device.
  *   k         0 <= k <= 1023 search neighbours (nprobe as in kde_search).
  *   m         samples per training point (sample_mode 0 or 1).
