@@ -407,6 +407,40 @@ def differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev
     return out
 
 
+def nn_contribution_map(torch, pkg, dev, R=4096):
+    """The k/m trade-off on the power-law construction of the Lemma on the
+    contribution of nearest neighbours (n = 1M, d = 32, alpha = 1, beta = 1/2,
+    h^2 = (alpha/2) n^-beta, the query at the origin, the exact top k = the
+    first k ids): for each (k, m), the mean relative error and spread of the
+    DEANN estimate over R query ids, next to the exact spread
+    ((n - k)/n) sigma_{X minus X_1} / sqrt(m) / KDE and the share delta of the
+    KDE left outside the top k (the quantity the dominance lemma's sample
+    bound scales with)."""
+    n, d = 1_000_000, 32
+    X, y, h = workloads.powerlaw_nn(n=n, d=d)
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), "gaussian", h, nlist=1)
+    Kv = np.exp(-((X.astype(np.float64) - y) ** 2).sum(1) / (2 * h * h))
+    mu = Kv.mean()
+    Yr = torch.from_numpy(np.repeat(y[None], R, axis=0)).to(dev)
+    rows = []
+    for k in (0, 8, 32, 128, 512):
+        delta = float(Kv[k:].sum() / Kv.sum())
+        nbr = torch.arange(max(k, 1), dtype=torch.int32, device=dev).repeat(R, 1)[:, :k]
+        for m in (100, 1000, 10_000):
+            run = ((lambda: index.query_with_neighbors(Yr, nbr, m, seed=7)) if k
+                   else (lambda: index.query_rs(Yr, m, seed=7)))
+            ms = time_calls(run, 2, torch)
+            est = run().cpu().numpy().astype(np.float64)
+            pred = (n - k) / n * np.sqrt(Kv[k:].var() / m) / mu
+            rows.append({"k": k, "m": m, "delta": delta,
+                         "mean_rel_err": float(np.mean(np.abs(est - mu)) / mu),
+                         "rel_std": float(est.std(ddof=1) / mu), "rel_std_exact": float(pred),
+                         "qps": R / (ms / 1e3)})
+    index.close()
+    return {"workload": "powerlaw_nn n=1M d=32 alpha=1 beta=0.5", "h": h, "kde": float(mu),
+            "replicates": R, "table": rows}
+
+
 def tune_rs(index, Yv_d, exact_v, ms_list):
     err = None
     for m in ms_list:
@@ -678,6 +712,7 @@ def main():
         extras = schedules_and_recall(index, X, Yd, Yv_d, exact_v, sched[head], prec, h, torch,
                                       pkg, dev)
         forms = differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev)
+        extras["nn_contribution"] = nn_contribution_map(torch, pkg, dev)
 
     cpu = None
     if rank == 0 and world == 1:

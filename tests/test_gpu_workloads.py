@@ -208,3 +208,29 @@ def test_graph_replays_serve_uneven_batches(pkg):
         assert torch.equal(got, want), b
         start += int(b)
     assert len(server.graphs) >= 3
+
+
+def test_powerlaw_nn_contribution_map(pkg):
+    """The Lemma's power-law construction: DEANN with the exact top k (the
+    first k ids) matches the oracle draw for draw, and across 8,192 query ids
+    the spread of the estimate is the exact ((n - k)/n) sigma / sqrt(m)."""
+    X, y, h = workloads.powerlaw_nn(n=50_000, d=16)
+    n = X.shape[0]
+    index = pkg.KDEIndex(_dev(X), "gaussian", h, nlist=1)
+    Kv = np.exp(-((X.astype(np.float64) - y) ** 2).sum(1) / (2 * h * h))
+    for k, m in ((0, 2000), (16, 500), (128, 200)):
+        Y = np.repeat(y[None], 64, axis=0)
+        nbr = np.tile(np.arange(max(k, 1), dtype=np.int32), (64, 1))[:, :k]
+        got = (index.query_with_neighbors(_dev(Y), _dev(nbr), m, seed=4).cpu().numpy() if k
+               else index.query_rs(_dev(Y), m, seed=4).cpu().numpy())
+        want = (oracle.deann(X, Y, "gaussian", h, nbr, m, 4) if k
+                else oracle.rs(X, Y, "gaussian", h, m, 4))
+        assert_kde_close(got, want)
+        R = 8192
+        Yr = np.repeat(y[None], R, axis=0)
+        nbr_r = np.tile(np.arange(max(k, 1), dtype=np.int32), (R, 1))[:, :k]
+        est = (index.query_with_neighbors(_dev(Yr), _dev(nbr_r), m, seed=5) if k
+               else index.query_rs(_dev(Yr), m, seed=5)).cpu().numpy().astype(np.float64)
+        var = ((n - k) / n) ** 2 * Kv[k:].var() / m
+        assert abs(est.var(ddof=1) / var - 1) < 0.1
+        assert abs(est.mean() - Kv.mean()) < 6 * np.sqrt(var / R)

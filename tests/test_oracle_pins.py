@@ -584,3 +584,73 @@ def test_fit_with_sampling_tracks_the_exact_optimum():
     hs = np.exp(np.linspace(math.log(0.1), math.log(3.0), 200))
     h_star = hs[int(np.argmax([f(h) for h in hs]))]
     assert abs(math.log(np.mean(ht[-20:]) / h_star)) < 0.1
+
+
+# ------------------------------------- nearest-neighbour contribution lemma ---
+def _powerlaw(n=20_000, d=16):
+    import workloads
+    return workloads.powerlaw_nn(n=n, d=d)
+
+
+def test_powerlaw_construction_gives_the_closed_form():
+    """At y = 0 with h^2 = (alpha/2) n^-beta the Gaussian KDE is
+    (1/n) sum_i exp(-(i + 1)^beta) (the Lemma's proof)."""
+    X, y, h = _powerlaw()
+    n = X.shape[0]
+    want = np.exp(-np.sqrt(np.arange(n) + 1.0)).mean()
+    assert math.isclose(oracle.exact(X, y[None], "gaussian", h)[0], want, rel_tol=1e-6)
+
+
+def test_powerlaw_top_neighbours_dominate():
+    """Lemma part (a): the first Theta(log^(1/beta) n) neighbours carry all but
+    a vanishing part of the KDE; the fraction grows with the constant."""
+    X, y, h = _powerlaw()
+    n = X.shape[0]
+    tot = oracle.exact(X, y[None], "gaussian", h)[0] * n
+    fr = []
+    for c in (0.5, 1.0, 2.0):
+        k = int(math.ceil(c * math.log(n) ** 2))  # 1/beta = 2
+        fr.append(oracle.exact(X[:k], y[None], "gaussian", h)[0] * k / tot)
+    assert fr[0] > 0.99 and fr[1] > 0.999 and fr[2] > 0.99998
+    assert fr[0] < fr[1] < fr[2] < 1.0
+
+
+def test_powerlaw_bandwidth_limits():
+    """Lemma part (b): h^2 <= (alpha/2) n^-beta / ln(1/tau) gives KDE <= tau.
+    Part (c) as its proof derives it for K = exp(-r^2/(2h^2)): the AM-GM step
+    bounds the KDE below by exp(-alpha/(2 beta h^2)), so
+    h^2 >= alpha / (2 beta ln(1/(1 - delta))) gives KDE >= 1 - delta.  The
+    printed condition h^2 >= ln(1/(1 - delta)) alpha/(2 beta) (logarithm in the
+    numerator) does not: it fails here for delta = 0.1."""
+    X, y, h = _powerlaw()
+    n, alpha, beta = X.shape[0], 1.0, 0.5
+    for tau in (0.1, 1e-2, 1e-4):
+        hb = math.sqrt(alpha / 2 * n ** -beta / math.log(1 / tau))
+        assert oracle.exact(X, y[None], "gaussian", hb)[0] <= tau
+    for delta in (0.5, 0.1, 0.01):
+        hc = math.sqrt(alpha / (2 * beta * math.log(1 / (1 - delta))))
+        kde = oracle.exact(X, y[None], "gaussian", hc)[0]
+        assert kde >= 1 - delta
+        # the AM-GM bound itself
+        assert kde >= math.exp(-alpha / (2 * beta * hc * hc)) - 1e-12
+    printed = math.sqrt(math.log(1 / 0.9) * alpha / (2 * beta))
+    assert oracle.exact(X, y[None], "gaussian", printed)[0] < 0.9
+
+
+def test_deann_variance_formula_given_the_neighbours():
+    """With X_1 fixed the estimate's variance is ((n - k)/n)^2 sigma^2 / m,
+    sigma^2 the population variance of K over X minus X_1 (draws with
+    repetition): 4,000 seeds against the formula (chi-square, 4,000 dof)."""
+    X, y, h = _powerlaw(n=2000, d=8)
+    n, k, m = 2000, 20, 50
+    Kv = np.exp(-((X.astype(np.float64) - y) ** 2).sum(1) / (2 * h * h))
+    rest = Kv[k:]
+    var = ((n - k) / n) ** 2 * rest.var() / m
+    Y = np.repeat(y[None], 4000, axis=0)
+    nbr = np.tile(np.arange(k, dtype=np.int32), (4000, 1))
+    est = oracle.deann(X, Y, "gaussian", h, nbr, m, 3)
+    s2 = est.var(ddof=1)
+    # 4,000 draws: s2 / var within +-8 % (about 5 standard errors of the
+    # variance for the kurtosis of these kernel values)
+    assert abs(s2 / var - 1) < 0.08
+    assert math.isclose(est.mean(), Kv.mean(), rel_tol=6 * math.sqrt(var / 4000) / Kv.mean())

@@ -163,6 +163,21 @@ def unit_powerlaw(n=4_000_000, d=300, nq=100_000, n_centres=5_000, seed=1005):
     return X, Y, Yval
 
 
+def powerlaw_nn(n=1_000_000, d=32, alpha=1.0, beta=0.5, seed=1006):
+    """The construction of the Lemma on the contribution of nearest
+    neighbours: around the query y = 0, point i (in index order) lies at squared
+    distance alpha ((i + 1) / n)^beta in a uniformly random direction.  With
+    h^2 = (alpha / 2) n^-beta its Gaussian kernel value is exp(-(i + 1)^beta).
+    Returns (X [n x d] float32, y [d] float32, h)."""
+    rng = np.random.default_rng(seed)
+    r = np.sqrt(alpha * ((np.arange(n, dtype=np.float64) + 1.0) / n) ** beta)
+    u = rng.standard_normal((n, d))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    X = (u * r[:, None]).astype(np.float32)
+    h = float(np.sqrt(alpha / 2.0 * n ** (-beta)))
+    return X, np.zeros(d, dtype=np.float32), h
+
+
 def uneven_batches(total=100_000, nbatch=64, lo=16, hi=8192, seed=5005):
     """Batch sizes log-uniform in [lo, hi], forced to include lo and hi, adjusted
     to sum to ``total``."""
