@@ -247,10 +247,39 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
         }
       }
     }
+    if (G == 32) {
+      // reduce-scatter of the kUnroll = 8 rows over the warp: three halving
+      // exchanges leave lane l with a partial of row 4 b4 + 2 b3 + b2 (b_i
+      // its bits), two butterflies finish it; the kernel is then evaluated
+      // once per row, on 8 lanes at once
+      static_assert(kUnroll == 8, "the reduce-scatter splits 8 rows");
+      const int lane = tid & 31;
+      float v4[4], v2[2], v1;
+      const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const float dist = group_sum<G>(acc[u]);
-      if (lig == 0 && base + u < cnt) part += kernel_from_dist(kern, dist, inv);
+      for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? acc[i + 4] : acc[i], send = h4 ? acc[i] : acc[i + 4];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? v4[i + 2] : v4[i], send = h3 ? v4[i] : v4[i + 2];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      {
+        const float keep = h2 ? v2[1] : v2[0], send = h2 ? v2[0] : v2[1];
+        v1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+      const int row = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+      if ((lane & 3) == 0 && base + row < cnt) part += kernel_from_dist(kern, v1, inv);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const float dist = group_sum<G>(acc[u]);
+        if (lig == 0 && base + u < cnt) part += kernel_from_dist(kern, dist, inv);
+      }
     }
   }
   return part;
