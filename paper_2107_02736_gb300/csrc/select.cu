@@ -583,22 +583,21 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
     }
   }
-  // rescore in plain FP32 difference form: an 8-lane group per row, 16-byte
-  // loads, kRows rows per group in flight (16 per warp)
+  // rescore in plain FP32 difference form: a warp takes 8 rows at once, each
+  // lane one 16-byte piece of every row, all 8 loads issued together; a
+  // reduce-scatter over the warp leaves row 4 b4 + 2 b3 + b2 (b_i the lane's
+  // bits) on the lanes with b1 = b0 = 0, which write its key
   {
-    constexpr int kRows = 4;
-    const int grp = lane >> 3, lig = lane & 7;
     const int dp4 = a.dp >> 2;
     const float4* y4 = reinterpret_cast<const float4*>(y);
     const float4* X4 = reinterpret_cast<const float4*>(a.XL);
-    for (int j0 = warp * 4 * kRows; j0 < K; j0 += kNW * 4 * kRows) {
-      int64_t pos[kRows];
-      float acc[kRows];
-#pragma unroll
-      for (int u = 0; u < kRows; ++u) {
-        const int j = j0 + grp * kRows + u;
-        pos[u] = -1;
-        acc[u] = 0.f;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    const int myrow = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+    for (int j0 = warp * 8; j0 < K; j0 += kNW * 8) {
+      // lane u (u < 8) locates row j0 + u in the candidate segments
+      int64_t p_own = -1;
+      {
+        const int j = j0 + (lane & 7);
         if (j < K) {
           const int s = sm.slot[j];
           int lo = 0, hi = a.P - 1;  // last segment with start <= s
@@ -606,18 +605,24 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
           }
-          pos[u] = s_lstart[lo] + (s - s_seg[lo]);
+          p_own = s_lstart[lo] + (s - s_seg[lo]);
         }
       }
-#pragma unroll 2
-      for (int c4 = lig; c4 < dp4; c4 += 8) {
+      int64_t pos[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pos[u] = __shfl_sync(0xffffffffu, p_own, u);
+      const int64_t p_mine = __shfl_sync(0xffffffffu, p_own, myrow);
+      const int32_t id = (lane & 3) == 0 && p_mine >= 0 ? a.perm[p_mine] : 0;
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+      for (int c4 = lane; c4 < dp4; c4 += 32) {
         const float4 yv = y4[c4];
-        float4 xv[kRows];
+        float4 xv[8];
 #pragma unroll
-        for (int u = 0; u < kRows; ++u)
-          xv[u] = pos[u] >= 0 ? __ldg(X4 + pos[u] * dp4 + c4) : yv;
+        for (int u = 0; u < 8; ++u) xv[u] = pos[u] >= 0 ? __ldg(X4 + pos[u] * dp4 + c4) : yv;
 #pragma unroll
-        for (int u = 0; u < kRows; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const float t0 = xv[u].x - yv.x, t1 = xv[u].y - yv.y, t2 = xv[u].z - yv.z,
                       t3 = xv[u].w - yv.w;
           acc[u] = fmaf(t0, t0, acc[u]);
@@ -626,12 +631,24 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
           acc[u] = fmaf(t3, t3, acc[u]);
         }
       }
+      float v4[4], v2[2], v1;
 #pragma unroll
-      for (int u = 0; u < kRows; ++u) {
-        const float d2 = group_sum<8>(acc[u]);
-        if (pos[u] >= 0 && lig == 0)
-          sm.key[j0 + grp * kRows + u] = pack_key(d2, a.perm[pos[u]]);
+      for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? acc[i + 4] : acc[i], send = h4 ? acc[i] : acc[i + 4];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
       }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? v4[i + 2] : v4[i], send = h3 ? v4[i] : v4[i + 2];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      {
+        const float keep = h2 ? v2[1] : v2[0], send = h2 ? v2[0] : v2[1];
+        v1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+      if ((lane & 3) == 0 && p_mine >= 0) sm.key[j0 + myrow] = pack_key(v1, id);
     }
   }
   __syncthreads();
