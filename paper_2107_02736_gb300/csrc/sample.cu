@@ -567,6 +567,90 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
   const int dp4 = dp >> 2;
   const float4* y4 = reinterpret_cast<const float4*>(ys);
   const float inv = kernel_inv(kern, h);
+  if (G == 32 && NV == 1) {
+    // d <= 128: eight rows per warp in flight, one 16-byte piece per lane; a
+    // reduce-scatter leaves row 4 b4 + 2 b3 + b2 (b_i the lane's bits) on a
+    // 4-lane group, each lane evaluates its row's kernel value and factors,
+    // and shuffles hand every row's coefficient back to all lanes
+    const int lane = tid & 31;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    const int myrow = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+    const float4 yv = lane < dp4 ? y4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    for (int wb = warp * 8; wb < cnt; wb += kNW * 8) {
+      float4 diff[8];
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int rid = wb + u < cnt ? ids[wb + u] : -1;
+        const float4 xv = rid >= 0 && lane < dp4 ? __ldg(X4 + (size_t)rid * dp4 + lane) : yv;
+        diff[u] = make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (kern == KDE_KERN_LAPLACIAN) {
+          acc[u] = (fabsf(diff[u].x) + fabsf(diff[u].y)) + (fabsf(diff[u].z) + fabsf(diff[u].w));
+        } else {
+          float t = diff[u].x * diff[u].x;
+          t = fmaf(diff[u].y, diff[u].y, t);
+          t = fmaf(diff[u].z, diff[u].z, t);
+          acc[u] = fmaf(diff[u].w, diff[u].w, t);
+        }
+      }
+      float v4[4], v2[2], dist;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? acc[i + 4] : acc[i], send = h4 ? acc[i] : acc[i + 4];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? v4[i + 2] : v4[i], send = h3 ? v4[i] : v4[i + 2];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      {
+        const float keep = h2 ? v2[1] : v2[0], send = h2 ? v2[0] : v2[1];
+        dist = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      dist += __shfl_xor_sync(0xffffffffu, dist, 2);
+      dist += __shfl_xor_sync(0xffffffffu, dist, 1);
+      const float K = kernel_from_dist(kern, dist, inv);
+      float gs, sv;
+      if (kern == KDE_KERN_GAUSSIAN) {
+        gs = 1.f / (h * h);
+        sv = dist / (h * h);
+      } else if (kern == KDE_KERN_EXPONENTIAL) {
+        const float r = sqrtf(fmaxf(dist, 0.f));
+        gs = r > 0.f ? 1.f / (h * r) : 0.f;
+        sv = r / h;
+      } else {
+        gs = 1.f / h;
+        sv = dist / h;
+      }
+      const float wk = wb + myrow < cnt ? w * K : 0.f;
+      if ((lane & 3) == 0) {
+        est += wk;
+        sl += wk * sv;
+      }
+      const float coef = wk * gs;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float c = __shfl_sync(0xffffffffu, coef, ((u >> 2) << 4) | (((u >> 1) & 1) << 3) | ((u & 1) << 2));
+        if (kern == KDE_KERN_LAPLACIAN) {
+          gacc[0].x += c * (diff[u].x > 0.f ? 1.f : (diff[u].x < 0.f ? -1.f : 0.f));
+          gacc[0].y += c * (diff[u].y > 0.f ? 1.f : (diff[u].y < 0.f ? -1.f : 0.f));
+          gacc[0].z += c * (diff[u].z > 0.f ? 1.f : (diff[u].z < 0.f ? -1.f : 0.f));
+          gacc[0].w += c * (diff[u].w > 0.f ? 1.f : (diff[u].w < 0.f ? -1.f : 0.f));
+        } else {
+          gacc[0].x = fmaf(c, diff[u].x, gacc[0].x);
+          gacc[0].y = fmaf(c, diff[u].y, gacc[0].y);
+          gacc[0].z = fmaf(c, diff[u].z, gacc[0].z);
+          gacc[0].w = fmaf(c, diff[u].w, gacc[0].w);
+        }
+      }
+    }
+    return;
+  }
   // warp-uniform trip count (group reductions need all lanes)
   for (int wb = warp * kGpw; wb < cnt; wb += kNW * kGpw) {
     const int r = wb + gw;
@@ -885,7 +969,7 @@ void launch_estimate_grad(const SampleArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)a.nq;
   const int G = group_lanes(a.dp);
   const int dp4 = a.dp / 4;
-  if (G < 32) {
+  if (G < 32) {  // d <= 64: shorter lane groups (measured faster than the warp-wide path)
     switch (G) {
       case 4: k_estimate_grad<4, 1><<<grid, kNT, dyn, s>>>(a); break;
       case 8: k_estimate_grad<8, 1><<<grid, kNT, dyn, s>>>(a); break;
