@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     p.add_argument("--no-schedules", dest="schedules", action="store_false",
                    help="skip the recall / k = m / fixed-parameter runs (untimed extras)")
+    p.add_argument("--fp8-study", type=int, default=0, metavar="NQ",
+                   help="emulate an FP8-e4m3 list scan on NQ queries of the workload and "
+                        "report its distance error, certified band and recall, next to BF16")
     p.add_argument("--profile-case", type=int, default=0, metavar="NQ",
                    help="run one call of each query-path kernel on NQ queries of the workload "
                         "(for a profiler) and exit")
@@ -581,6 +584,101 @@ def mean_candidates(X, Y, C, assign, P):
     return tot / Y.shape[0]
 
 
+def round_e4m3(v):
+    """Round to the nearest FP8-e4m3 value (ties to even; 3 mantissa bits,
+    exponent bias 7, normals from 2^-6, subnormal spacing 2^-9, saturating
+    at 448), elementwise in FP64."""
+    a = np.abs(v)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
+    step = np.where(a >= 2.0 ** -6, 2.0 ** (e - 3), 2.0 ** -9)
+    q = np.minimum(np.round(a / step) * step, 448.0)  # np.round: half to even
+    return np.sign(v) * q
+
+
+def round_bf16(v):
+    """Round to the nearest BF16 value (8 significant bits, ties to even)."""
+    f = np.asarray(v, np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def fp8_study(args):
+    """Emulates the centred list scan with FP8-e4m3 operands (per-row and
+    per-query scales to the e4m3 range, exact accumulation, as a tcgen05
+    kind::f8f6f4 MMA with FP32 accumulation would give up to its rounding) and
+    with BF16 operands, on the bench workload's own inverted file: distance
+    error against FP64, the rigorous error band each precision needs for a
+    certified top k, and the recall of the top k without certification (the
+    k smallest approximate distances, and the k + 25 % smallest rescored in
+    FP32)."""
+    import torch
+    import paper_2107_02736_gb300 as pkg
+    dev = torch.device("cuda", 0)
+    X, Y, _ = make_workload(args)
+    spec = workloads.CONFIGS[2]
+    k, P = 1024, 8
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), args.kernel, 12.85, nlist=spec["nlist"],
+                         seed=1)
+    C, assign = index.export_ivf()
+    C, assign = C.numpy().astype(np.float64), assign.numpy()
+    index.close()
+    order = np.argsort(assign, kind="stable")
+    starts = np.searchsorted(assign[order], np.arange(C.shape[0] + 1))
+    rng = np.random.default_rng(11)
+    qs = rng.choice(Y.shape[0], args.fp8_study, replace=False)
+    res = {p: {"max_abs_err_rel_r2": 0.0, "bound_rel_r2": 0.0, "band": [], "recall_plain": [],
+               "recall_margin": []} for p in ("fp8_e4m3", "bf16")}
+    u = {"fp8_e4m3": 2.0 ** -4, "bf16": 2.0 ** -8}
+    for q in qs:
+        y = Y[q].astype(np.float64)
+        probes = np.argsort(((C - y) ** 2).sum(1))[:P]
+        ids, d2x, d2a = [], [], {p: [] for p in res}
+        r_max = 0.0
+        for l in probes:
+            mem = order[starts[l]:starts[l + 1]]
+            xt = X[mem].astype(np.float64) - C[l]
+            yt = y - C[l]
+            ex = ((xt - yt) ** 2).sum(1)
+            ids.append(mem)
+            d2x.append(ex)
+            r_max = max(r_max, np.sqrt((xt ** 2).sum(1)).max() + np.sqrt((yt ** 2).sum()))
+            for p in res:
+                if p == "fp8_e4m3":
+                    # a row equal to its centroid has scale 0; any positive scale keeps it 0
+                    sx = np.maximum(np.abs(xt).max(1, keepdims=True) / 448.0, 1e-30)
+                    sy = max(np.abs(yt).max() / 448.0, 1e-30)
+                    dot = (round_e4m3(xt / sx) * sx) @ (round_e4m3(yt / sy) * sy)
+                else:
+                    dot = round_bf16(xt) @ round_bf16(yt)
+                d2a[p].append((xt ** 2).sum(1) + (yt ** 2).sum() - 2.0 * dot)
+        ids = np.concatenate(ids)
+        ex = np.concatenate(d2x)
+        true_top = set(ids[np.argsort(ex, kind="stable")[:k]])
+        for p in res:
+            ap = np.concatenate(d2a[p])
+            err = np.abs(ap - ex).max() / r_max ** 2
+            res[p]["max_abs_err_rel_r2"] = max(res[p]["max_abs_err_rel_r2"], float(err))
+            E = 2.0 * (2 * u[p] + u[p] ** 2) * r_max ** 2  # |<x,y> error| <= (2u + u^2)|x||y|
+            res[p]["bound_rel_r2"] = 2.0 * (2 * u[p] + u[p] ** 2)
+            tk = np.sort(ap)[k - 1]
+            res[p]["band"].append(int((ap <= tk + 2 * E).sum()))
+            top = ids[np.argsort(ap, kind="stable")[:k]]
+            res[p]["recall_plain"].append(len(true_top.intersection(top)) / k)
+            cand = np.argsort(ap, kind="stable")[:k + k // 4]
+            resc = cand[np.argsort(ex[cand], kind="stable")[:k]]
+            res[p]["recall_margin"].append(len(true_top.intersection(ids[resc])) / k)
+    out = {"study": "fp8_e4m3 list scan, exact emulation", "queries": int(len(qs)), "k": k,
+           "nprobe": P}
+    for p, r in res.items():
+        out[p] = {"max_abs_err_over_r2": r["max_abs_err_rel_r2"],
+                  "certified_bound_over_r2": r["bound_rel_r2"],
+                  "certified_band_mean": float(np.mean(r["band"])),
+                  "recall_topk_uncertified": float(np.mean(r["recall_plain"])),
+                  "recall_topk_margin25_rescored": float(np.mean(r["recall_margin"]))}
+    print(json.dumps(out), flush=True)
+
+
 def profile_case(args):
     """One batch of args.profile_case queries through each path at the bench's
     schedule (k = 1024, m = 8000, nprobe = 8, BF16 scan, h = 12.85): DEANN,
@@ -608,6 +706,8 @@ def main():
         return run_reference(args, rank, world)
     if args.profile_case:
         return profile_case(args)
+    if args.fp8_study:
+        return fp8_study(args)
 
     import torch
     import paper_2107_02736_gb300 as pkg
