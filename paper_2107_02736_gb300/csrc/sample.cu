@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kNW = kNT / 32;
-constexpr int kChunk = 1024;   // samples staged per gather round
+constexpr int kChunk = 2048;   // samples staged per gather round
 constexpr int kUnroll = 8;     // rows in flight per lane group
 
 struct EstSmem {

@@ -238,18 +238,23 @@ __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uin
 // linear scale between them.  Returns lo <= (k-th smallest) <= hi, the bounds
 // of the bin that holds it, widened by a few units of rounding.
 __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, int k,
-                                  SelectSmem& sm, float& lo_out, float& hi_out) {
+                                  SelectSmem& sm, float& lo_out, float& hi_out,
+                                  float lo_hint, float hi_hint) {
   constexpr int kBins = 4096;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ float s_mn[kNW], s_mx[kNW];
   __shared__ int s_scan[kNW];
   __shared__ float s_lo, s_hi;
   int* hist = reinterpret_cast<int*>(sm.key);  // 16 KiB, free until rescoring
-  float mn = __int_as_float(0x7f800000), mx = 0.f;
-  for_each_cand(vals, cnt, [&](int64_t, float v) {
-    mn = fminf(mn, v);
-    mx = fmaxf(mx, v);
-  });
+  // the histogram spans [mn, mx]: the caller's bounds on every value when
+  // it has them (0 <= lo_hint <= hi_hint), else a min/max pass
+  const bool hinted = lo_hint >= 0.f && hi_hint >= lo_hint;
+  float mn = hinted ? lo_hint : __int_as_float(0x7f800000), mx = hinted ? hi_hint : 0.f;
+  if (!hinted)
+    for_each_cand(vals, cnt, [&](int64_t, float v) {
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+    });
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -304,6 +309,12 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
       const float lo = mn + (float)bin / scale, hi = mn + (float)(bin + 1) / scale;
       s_lo = fmaxf(0.f, lo - fabsf(lo) * 1e-6f - 1e-30f);
       s_hi = hi + fabsf(hi) * 1e-6f + 1e-30f;
+      // end bins also hold any value beyond the bounds: open them
+      if (bin == 0) s_lo = 0.f;
+      if (bin == kBins - 1) s_hi = __int_as_float(0x7f800000);
+    } else if (hinted) {
+      s_lo = 0.f;
+      s_hi = __int_as_float(0x7f800000);
     } else {
       s_lo = mn;
       s_hi = mx;
@@ -544,7 +555,7 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
   // Error bound E of the scan's distances for this query: |approx - exact|
   // <= err_scale r^2 with r = |x| + |y| (|x| <= the dataset's largest norm),
   // or, for the centred scan, r = |x~| + |y~| <= list radius + |y - c_probe|.
-  __shared__ float s_E;
+  __shared__ float s_E, s_hint_lo, s_hint_hi;
   if (tid == 0) {
     s_seg[a.P] = cnt;
     float r = a.xmax + sqrtf(a.Yn[q]);
@@ -556,6 +567,19 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
     }
     s_E = a.err_scale * r * r;
+    // every candidate of list l is within rad_l of c_l, so its exact distance
+    // lies in [(|y - c_l| - rad_l)^2, (|y - c_l| + rad_l)^2], and the scan's
+    // value within E of it: bounds for the histogram of t_k
+    float lo = __int_as_float(0x7f800000), hi = 0.f;
+    for (int p = 0; p < a.P; ++p) {
+      const int l = a.probes[q * a.P + p];
+      if (l < 0) continue;
+      const float dc = sqrtf(a.probe_d2[q * a.P + p]);
+      lo = fminf(lo, fmaxf(0.f, dc - a.rad[l]));
+      hi = fmaxf(hi, dc + a.rad[l]);
+    }
+    s_hint_lo = hi >= lo ? fmaxf(0.f, lo * lo * (1.f - 1e-5f) - s_E) : -1.f;
+    s_hint_hi = hi >= lo ? hi * hi * (1.f + 1e-5f) + s_E : -1.f;
   }
   __syncthreads();
   // Candidates to rescore: every one whose approximate distance is within 2E
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     __syncthreads();
   } else {
     float tk_lo, tk_hi;  // t_k lies in [tk_lo, tk_hi]
-    block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi);
+    block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi, s_hint_lo, s_hint_hi);
     const uint32_t thr = dist_key(tk_hi + 2.f * s_E);
     K = block_collect_le(vals, cnt, thr, kSelectCap, sm);
     if (K > kSelectCap) {
