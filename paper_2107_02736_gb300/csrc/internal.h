@@ -31,6 +31,16 @@ constexpr int kTile = 64;            // SIMT distance tile edge
 // multiple of 4 so rows start on 16-byte boundaries; padding is zero.
 inline int padded_dim(int d) { return (d + 3) & ~3; }
 
+// Raises a kernel's dynamic shared-memory limit on the current device.  The
+// limit is a per-device attribute, and the 48 KB default counts static and
+// dynamic shared memory together, so it is set before every launch that takes
+// dynamic shared memory (one cheap driver call per launch).
+inline bool set_dynamic_smem(const void* kernel, size_t bytes) {
+  if (bytes == 0) return true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess;
+}
+
 // Bump allocator over one device buffer owned by an index.  Calls on one
 // index are stream-ordered, so scratch is reused call after call.
 struct Arena {

@@ -167,5 +167,22 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t fmt) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// The driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once per
+// process through the runtime (thread-safe static initialisation); null when
+// the driver does not provide it.
+using EncodeTiledFn = decltype(&cuTensorMapEncodeTiled);
+inline EncodeTiledFn tensor_map_encoder() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return static_cast<EncodeTiledFn>(nullptr);
+  }();
+  return fn;
+}
+
 }  // namespace tc
 }  // namespace deann

@@ -247,23 +247,9 @@ __global__ void k_exact_finish_tc(const double* __restrict__ acc, int64_t nq, do
   if (q < nq) out[q] = (float)(acc[q] * inv_n);
 }
 
-using EncodeTiledFn = decltype(&cuTensorMapEncodeTiled);
-
-EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  if (fn == nullptr) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
 
 bool encode_parts_map(CUtensorMap* map, const void* base, int64_t rows_total, int dpb) {
-  EncodeTiledFn enc = encoder();
+  tc::EncodeTiledFn enc = tc::tensor_map_encoder();
   if (enc == nullptr) return false;
   cuuint64_t dims[2] = {(cuuint64_t)dpb, (cuuint64_t)rows_total};
   cuuint64_t strides[1] = {(cuuint64_t)dpb * 2};
@@ -298,13 +284,8 @@ bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_
                      float* out, uint32_t* err, cudaStream_t s) {
   CUtensorMap tmap_y;
   if (!encode_parts_map(&tmap_y, Ys, kParts * nqp, dpb)) return false;
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(k_exact_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)exact_tc_smem()) != cudaSuccess)
-      return false;
-    configured = true;
-  }
+  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_exact_tc), exact_tc_smem()))
+    return false;
   cudaMemsetAsync(acc, 0, sizeof(double) * nq, s);
   const int64_t qtiles = (nq + kQM - 1) / kQM;
   // about two waves of the 152 SMs (one CTA per SM), slices of whole tiles

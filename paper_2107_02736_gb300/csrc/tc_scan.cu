@@ -248,22 +248,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// the driver's tensor-map encoder, resolved at run time (no libcuda link)
-using EncodeTiledFn = decltype(&cuTensorMapEncodeTiled);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (fn == nullptr) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 }  // namespace
 
 int scan_tc_bn(int dpb) {
@@ -278,7 +262,7 @@ size_t scan_tc_smem(int dpb, int BN) {
 }
 
 bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb) {
-  EncodeTiledFn enc = encode_fn();
+  tc::EncodeTiledFn enc = tc::tensor_map_encoder();
   if (enc == nullptr) return false;
   CUtensorMap* map = reinterpret_cast<CUtensorMap*>(map_out);
   cuuint64_t dims[2] = {(cuuint64_t)dpb, (cuuint64_t)rows};
@@ -297,13 +281,7 @@ bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, c
                     float* cand, uint32_t* err, cudaStream_t s) {
   if (plan.max_tiles <= 0) return true;
   const size_t smem = scan_tc_smem(dpb, BN);
-  static size_t configured = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return false;
-    configured = smem;
-  }
+  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_scan_tc), smem)) return false;
   k_scan_tc<<<(unsigned)plan.max_tiles, kThreads, smem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(tmap),
       Yp, C, dp, XLcn, list_off, L, dpb, BN, plan.pair_q,

@@ -341,17 +341,10 @@ void launch_window_tile(const WindowTileArgs& w, cudaStream_t s) {
   const int dres = (w.dp + kKC - 1) / kKC * kKC;
   const size_t dyn = res ? sizeof(float) * (size_t)dres * kTile : 0;
   if (res) {
-    // the resident query tile needs up to 80 KB beyond the static 24.5 KB
-    static bool attr_set[2] = {false, false};
+    // the resident query tile takes up to 80 KB beside the static 25 KB
     auto f0 = k_window_tile<WMODE_SQ, true>;
     auto f1 = k_window_tile<WMODE_ABS, true>;
-    if (!attr_set[0]) {
-      cudaFuncSetAttribute(f0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float) * kResMaxDp * kTile));
-      cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float) * kResMaxDp * kTile));
-      attr_set[0] = attr_set[1] = true;
-    }
+    set_dynamic_smem(reinterpret_cast<const void*>(w.kern == KDE_KERN_LAPLACIAN ? f1 : f0), dyn);
     if (w.kern == KDE_KERN_LAPLACIAN)
       f1<<<grid, 256, dyn, s>>>(w);
     else
