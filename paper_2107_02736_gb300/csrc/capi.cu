@@ -174,7 +174,7 @@ struct SearchBufs {
   float* D = nullptr;
   int32_t* probes = nullptr;
   float* probe_d2 = nullptr;  // |y - c_probe|^2, rescored
-  int64_t *q_count = nullptr, *q_off = nullptr, *seg_off = nullptr;
+  int64_t *q_count = nullptr, *q_real = nullptr, *q_off = nullptr, *seg_off = nullptr;
   int64_t *list_cnt = nullptr, *bucket_off = nullptr, *bucket_fill = nullptr;
   int64_t *tile_cnt = nullptr, *tile_off = nullptr;
   int32_t* pair_q = nullptr;
@@ -188,8 +188,8 @@ constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of q
 
 void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
   const int L = ix->nlist;
-  // each query's candidate segment is padded to a multiple of 4 floats
-  const size_t per_q = ((size_t)P * (size_t)std::max<int64_t>(ix->max_list, 1) + 4) * sizeof(float);
+  // each (query, probe) candidate segment is padded to a multiple of 32 floats
+  const size_t per_q = ((size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32)) * sizeof(float);
   int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
   qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
   s.qc = qc;
@@ -197,6 +197,7 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.probes = b.take<int32_t>((size_t)qc * P);
   s.probe_d2 = b.take<float>((size_t)qc * P);
   s.q_count = b.take<int64_t>(qc);
+  s.q_real = b.take<int64_t>(qc);
   s.q_off = b.take<int64_t>(qc + 1);
   s.seg_off = b.take<int64_t>((size_t)qc * P);
   s.list_cnt = b.take<int64_t>(L);
@@ -210,7 +211,7 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.ord_off = b.take<int64_t>(L + 1);
   s.ord_fill = b.take<int64_t>(L);
   s.order = b.take<int32_t>(qc);
-  s.cand = b.take<float>((size_t)qc * ((size_t)P * std::max<int64_t>(ix->max_list, 1) + 4));
+  s.cand = b.take<float>((size_t)qc * (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
 }
 
 struct CallBufs {
@@ -348,7 +349,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     const int qtile = tcore ? scan_tc_bn(ix->dpb) : kTile;
     {
       StageTimer t(ix, ST_PLAN, st, 9);
-      launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_off, s.seg_off,
+      launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_real, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
                         s.tile_cnt, s.tile_off, qtile, st);
       launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
@@ -374,6 +375,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.cand = s.cand;
     a.q_off = s.q_off;
     a.q_count = s.q_count;
+    a.q_real = s.q_real;
     a.seg_off = s.seg_off;
     a.probes = s.probes;
     a.P = P;
@@ -382,6 +384,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.XLn = ix->XLn;
     a.perm = ix->perm;
     a.X = ix->X;
+    a.n = ix->n;
     a.xmax = ix->xmax;
     a.Y = Yc;
     a.Yn = Ync;

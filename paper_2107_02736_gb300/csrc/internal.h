@@ -193,7 +193,8 @@ void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int
                           const float* C, int nprobe, int margin, int32_t* probes,
                           float* probe_d2, cudaStream_t s);
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
-                       int64_t* q_count, int64_t* q_off, int64_t* seg_off, int64_t* list_cnt,
+                       int64_t* q_count, int64_t* q_real, int64_t* q_off, int64_t* seg_off,
+                       int64_t* list_cnt,
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
                        int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
                        cudaStream_t s);
@@ -203,7 +204,8 @@ struct SelectArgs {
   const int32_t* order;      // [nq] processing order (nullable: row order)
   const float* cand;
   const int64_t* q_off;
-  const int64_t* q_count;
+  const int64_t* q_count;    // padded candidate slots per query (+inf in the padding)
+  const int64_t* q_real;     // candidates per query
   const int64_t* seg_off;    // [nq x P]
   const int32_t* probes;     // [nq x P]
   int P;
@@ -212,6 +214,7 @@ struct SelectArgs {
   const float* XLn;
   const int32_t* perm;
   const float* X;            // original order (Laplacian neighbour sums)
+  int64_t n;                 // rows of X
   float xmax;                // max |x| over the dataset
   const float* Y;
   const float* Yn;

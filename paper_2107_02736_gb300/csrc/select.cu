@@ -179,7 +179,9 @@ __device__ __forceinline__ void for_each_cand(const float* __restrict__ vals, in
   }
 }
 
-// Collects the indices of all keys <= thr into sm.slot[0..cap) in a fixed
+constexpr uint32_t kInfKey = 0x7f800000u;  // dist_key(+inf)
+
+// Collects the indices of all finite keys <= thr into sm.slot[0..cap) in a fixed
 // order (rounds of kU * kNT float4s; within a round, thread by thread).
 // Returns the total count, which may exceed cap (then the slots hold only
 // the first cap).
@@ -202,8 +204,11 @@ __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uin
       const int64_t i = (r0 + (int64_t)u * kNT + tid) * 4;
       const float c4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (i + c < cnt && dist_key(c4[c]) <= thr) take |= 1u << (4 * u + c);
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t key = dist_key(c4[c]);
+        // +inf marks the padding of the candidate segments: never a candidate
+        if (i + c < cnt && key <= thr && key < kInfKey) take |= 1u << (4 * u + c);
+      }
     }
     const int mine = __popc(take);
     int incl = mine;
@@ -252,8 +257,10 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
   float mn = hinted ? lo_hint : __int_as_float(0x7f800000), mx = hinted ? hi_hint : 0.f;
   if (!hinted)
     for_each_cand(vals, cnt, [&](int64_t, float v) {
-      mn = fminf(mn, v);
-      mx = fmaxf(mx, v);
+      if (v < __int_as_float(0x7f800000)) {  // the +inf padding is no candidate
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
     });
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -274,7 +281,7 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
   }
   const float scale = mx > mn ? (float)kBins / (mx - mn) : 0.f;
   for_each_cand(vals, cnt, [&](int64_t, float v) {
-    const int bin = min(kBins - 1, max(0, (int)((v - mn) * scale)));
+    const int bin = v >= mx ? kBins - 1 : min(kBins - 1, max(0, (int)((v - mn) * scale)));
     atomicAdd(&hist[bin], 1);
   });
   __syncthreads();
@@ -441,22 +448,29 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
 // --------------------------------------------------------------------------
 // Work plan of the list-major scan.
 // --------------------------------------------------------------------------
+// Candidate segments: query q's values for probe p start at seg_off[q P + p]
+// within its region, each segment padded to a multiple of 32 floats (whole
+// 128-byte lines; the scans fill the padding with +inf).  q_count holds the
+// padded total, q_real the candidates.
 __global__ void k_plan_segments(const int32_t* __restrict__ probes, int64_t nq, int P,
                                 const int64_t* __restrict__ list_off,
-                                int64_t* __restrict__ q_count, int64_t* __restrict__ seg_off,
-                                int64_t* __restrict__ list_cnt) {
+                                int64_t* __restrict__ q_count, int64_t* __restrict__ q_real,
+                                int64_t* __restrict__ seg_off, int64_t* __restrict__ list_cnt) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  int64_t run = 0;
+  int64_t run = 0, real = 0;
   for (int p = 0; p < P; ++p) {
     const int l = probes[q * P + p];
     seg_off[q * P + p] = run;
     if (l >= 0) {
-      run += list_off[l + 1] - list_off[l];
+      const int64_t len = list_off[l + 1] - list_off[l];
+      run += (len + 31) & ~(int64_t)31;
+      real += len;
       atomicAdd(reinterpret_cast<unsigned long long*>(list_cnt + l), 1ull);
     }
   }
   q_count[q] = run;
+  q_real[q] = real;
 }
 
 __global__ void k_plan_fill(const int32_t* __restrict__ probes, int64_t nq, int P,
@@ -541,16 +555,19 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
   __shared__ SelectSmem sm;
   __shared__ int64_t s_seg[kMaxProbe + 1];
   __shared__ int64_t s_lstart[kMaxProbe];
+  __shared__ int64_t s_llen[kMaxProbe];
   __shared__ float s_red[kNW];
   const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t cnt = a.q_count[q];
+  const int64_t cnt = a.q_count[q];      // slots, with +inf in the padding
+  const int64_t cnt_real = a.q_real[q];  // candidates
   const float* vals = a.cand + a.q_off[q];
   const float* y = a.Y + q * a.dp;
   for (int p = tid; p < a.P; p += kNT) {
     const int l = a.probes[q * a.P + p];
     s_seg[p] = a.seg_off[q * a.P + p];
     s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
+    s_llen[p] = l >= 0 ? a.list_off[l + 1] - a.list_off[l] : 0;
   }
   // Error bound E of the scan's distances for this query: |approx - exact|
   // <= err_scale r^2 with r = |x| + |y| (|x| <= the dataset's largest norm),
@@ -589,10 +606,8 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
   // top k.  Beyond kSelectCap candidates the kSelectCap smallest are kept and
   // the query is counted as uncertified.
   int K;
-  if (cnt <= (int64_t)a.k) {
-    K = (int)cnt;
-    for (int i = tid; i < K; i += kNT) sm.slot[i] = i;
-    __syncthreads();
+  if (cnt_real <= (int64_t)a.k) {
+    K = block_collect_le(vals, cnt, kInfKey, kSelectCap, sm);  // every finite value
   } else {
     float tk_lo, tk_hi;  // t_k lies in [tk_lo, tk_hi]
     block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi, s_hint_lo, s_hint_hi);
@@ -629,7 +644,8 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
           }
-          p_own = s_lstart[lo] + (s - s_seg[lo]);
+          // a slot past its list (the segment's padding) is never a row
+          if (s - s_seg[lo] < s_llen[lo]) p_own = s_lstart[lo] + (s - s_seg[lo]);
         }
       }
       int64_t pos[8];
@@ -672,7 +688,8 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       }
       v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
       v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-      if ((lane & 3) == 0 && p_mine >= 0) sm.key[j0 + myrow] = pack_key(v1, id);
+      if ((lane & 3) == 0 && j0 + myrow < K)
+        sm.key[j0 + myrow] = p_mine >= 0 ? pack_key(v1, id) : ~0ull;  // ~0: +inf, id -1
     }
   }
   __syncthreads();
@@ -732,7 +749,9 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
         const int j = j0 + grp;
         const bool valid = j < n_amb;
         const int64_t id = valid ? (int64_t)(amb[j] & 0xffffffffu) : 0;
-        const float d2 = precise_sq_dist<8>(a.X + id * a.dp, y, a.d, lig);
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
+        if (!row) d2 = __int_as_float(0x7f800000);
         if (valid && lig == 0) amb[j] = pack_key(d2, (int)id);
       }
       __syncthreads();
@@ -791,7 +810,9 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
         const int j = j0 + grp;
         const bool valid = j < hi;
         const int64_t id = valid ? (int64_t)(sm.key[j] & 0xffffffffu) : 0;
-        const float d2 = precise_sq_dist<8>(a.X + id * a.dp, y, a.d, lig);
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
+        if (!row) d2 = __int_as_float(0x7f800000);
         if (valid && lig == 0) sm.key[j] = pack_key(d2, (int)id);
       }
       __syncthreads();
@@ -830,8 +851,9 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       // the IVF ranks by Euclidean distance; the Laplacian kernel needs L1
       for (int j = warp; j < kk; j += kNW) {
         const int64_t id = (int64_t)(sm.key[j] & 0xffffffffu);
-        const float l1 = precise_l1_dist<32>(a.X + id * a.dp, y, a.d, lane);
-        if (lane == 0) part += kernel_from_dist(a.kern, l1, inv);
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        const float l1 = precise_l1_dist<32>(a.X + (row ? id : 0) * a.dp, y, a.d, lane);
+        if (lane == 0 && row) part += kernel_from_dist(a.kern, l1, inv);
       }
     } else {
       for (int j = tid; j < kk; j += kNT)
@@ -871,15 +893,16 @@ void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int
 }
 
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
-                       int64_t* q_count, int64_t* q_off, int64_t* seg_off, int64_t* list_cnt,
+                       int64_t* q_count, int64_t* q_real, int64_t* q_off, int64_t* seg_off,
+                       int64_t* list_cnt,
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
                        int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
                        cudaStream_t s) {
   cudaMemsetAsync(list_cnt, 0, sizeof(int64_t) * L, s);
   cudaMemsetAsync(bucket_fill, 0, sizeof(int64_t) * L, s);
   k_plan_segments<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(probes, nq, P, list_off, q_count,
-                                                              seg_off, list_cnt);
-  k_exclusive_scan<<<1, 1024, 0, s>>>(q_count, nq, q_off, 4);  // 16-byte segments
+                                                              q_real, seg_off, list_cnt);
+  k_exclusive_scan<<<1, 1024, 0, s>>>(q_count, nq, q_off, 32);  // 128-byte aligned regions
   k_exclusive_scan<<<1, 1024, 0, s>>>(list_cnt, L, bucket_off, 1);
   const int64_t np = nq * P;
   k_plan_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(probes, nq, P, q_off, seg_off,

@@ -13,7 +13,8 @@
 //                      accumulator; warp 1 also owns the TMEM allocation;
 //   warps 2-5        : epilogue, one TMEM lane (= one list point) per thread:
 //                      D^2 = |x|^2 + |y|^2 - 2 acc, clamped at 0, written to
-//                      each query's candidate segment (coalesced along points).
+//                      each query's candidate segment (coalesced along points;
+//                      the segment's padding to 32 floats gets +inf).
 // Both operands are centred on the list's centroid c_l (x~ = x - c_l, stored
 // that way at build time; y~ = y - c_l, formed here), which leaves the
 // distances unchanged but shrinks the magnitudes that the BF16 rounding error
@@ -209,8 +210,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue: warps 2..5 ----------------
+    // one TMEM lane (= one list point) per thread; for each query the warp's
+    // 32 points go out as one coalesced 128-byte store.  Points past the list
+    // up to its 32-float padded length get +inf (the segment's padding).
     const int lg = (warp & 3) * 32;
     const int row = lg + lane;
+    const int64_t padlen = (len + 31) & ~(int64_t)31;
     for (int tt = 0; tt < ntiles; ++tt) {
       const int b = tt & 1;
       const uint32_t tph = (uint32_t)(tt >> 1) & 1u;
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       tc::tc_fence_after();
       const int64_t pt = (int64_t)tt * kBM + row;
-      const bool valid = pt < len;
+      const bool valid = pt < len, pad = !valid && pt < padlen;
       const float xn = valid ? XLcn[xb + pt] : 0.f;
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * BN);
       for (int c0 = 0; c0 < npairs; c0 += 16) {
@@ -229,15 +234,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = c0 + j;
-          if (valid && col < npairs) {
-            const float d2 = fmaxf(xn + sh.yn[col] - 2.f * __uint_as_float(v[j]), 0.f);
-            cand[sh.dst[col] + pt] = d2;
-          }
+          if ((valid || pad) && col < npairs)
+            cand[sh.dst[col] + pt] =
+                valid ? fmaxf(xn + sh.yn[col] - 2.f * __uint_as_float(v[j]), 0.f)
+                      : __int_as_float(0x7f800000);
         }
       }
+      // the accumulator was read synchronously (tcgen05.wait::ld): a relaxed
+      // arrive frees it without waiting for this tile's stores to land
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&sh.tempty[b]);
+      if (lane == 0) tc::mbar_arrive_relaxed(&sh.tempty[b]);
     }
   }
   __syncthreads();
@@ -258,6 +265,7 @@ int scan_tc_bn(int dpb) {
 }
 
 size_t scan_tc_smem(int dpb, int BN) {
+  // alignment slack, the A ring, the resident queries
   return 1024 + (size_t)kStages * kStageBytes + (size_t)(dpb / kBK) * BN * 128;
 }
 

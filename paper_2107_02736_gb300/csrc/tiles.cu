@@ -340,7 +340,15 @@ __global__ void __launch_bounds__(256) k_scan_simt(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t r = x0 + tx * 4 + j;
-      if (r >= xe) continue;
+      if (r >= xe) {
+        // the segment's padding to 32 floats holds +inf
+        if (r - xb < ((xe - xb + 31) & ~(int64_t)31)) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (dst[i] >= 0) cand[dst[i] + (r - xb)] = __int_as_float(0x7f800000);
+        }
+        continue;
+      }
       const float xn = XLn[r];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
