@@ -4,13 +4,15 @@
 Workload (the paper's mean-KDE-1e-3 setting on a dense-embedding stand-in):
 n = 1,000,000 points in d = 128 from a mixture of 1,000 Gaussians, 10,000
 test queries (90 % mixture, 10 % uniform in the bounding box), Gaussian
-kernel with h bisected so that the mean exact KDE of 1,000 validation queries
+kernel with h bisected so that the mean exact KDE of 4,000 validation queries
 is 1e-3 (+-1 %), IVF with 1,024 lists.  A step is one kde_query call over the
 10,000 test queries with inputs resident in HBM (the dataset, 512 MB, is
 larger than L2).  For each scan precision (FP32 SIMT, BF16 tcgen05) the
 schedule (k, m, nprobe) is the cheapest one whose mean relative error on the
-validation queries is <= 1e-2; the headline is the faster of the two, and the
-test-set error of every timed step is reported.
+validation queries is <= 0.9e-2 (a margin for the difference between the
+validation and test queries and the seed-to-seed spread of the timed steps);
+the headline is the faster of the two, and the test-set error of every timed
+step is reported.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (a bounded query sample per step).
@@ -36,9 +38,9 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 TARGET_ERR = 1e-2
-# the tuners aim 5 % below the target on the validation queries, so that every
-# timed step (each with its own seed) stays within it on the test queries
-TUNE_ERR = 0.95 * TARGET_ERR
+# the tuners aim 10 % below the target on the validation queries, so that
+# every timed step (each with its own seed) stays within it on the test queries
+TUNE_ERR = 0.9 * TARGET_ERR
 WORKLOAD = "mixture_embed n=1M d=128 nq=10k gaussian mean-KDE=1e-3 IVF nlist=1024"
 PRECISIONS = {"fp32": 0, "bf16": 1}
 
@@ -179,7 +181,7 @@ def ncu_traffic(stage):
 def make_workload(args):
     n = int(1_000_000 * args.scale)
     X, Y, Yval = workloads.mixture_embed(n=n)
-    return X, Y, Yval[:1000]
+    return X, Y, Yval[:4000]
 
 
 def fit_bandwidth(index, Yv_d, target):
@@ -220,8 +222,10 @@ def tune(index, Yv_d, exact_v, torch, precision):
     every (k, nprobe), m grows in quarter-octave steps until the target is met
     (more samples only cost more)."""
     results = []
-    for P in (8, 16, 32):
-        for k in (100, 200, 400, 800, 1024):
+    # smaller k (100 - 400) and nprobe = 32 never lead here: on this workload
+    # k <= 800 misses the target even at m = 64,000
+    for P in (8, 16):
+        for k in (800, 1024, 1536, 2048):
             for m in M_GRID:
                 est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=precision)
                 err = rel_err(est.cpu().numpy(), exact_v)
@@ -340,8 +344,9 @@ def schedules_and_recall(index, X, Yd, Yv_d, exact_v, head_sched, prec, h, torch
     brute = pkg.KDEIndex(Xd, "gaussian", h, nlist=1, seed=1)
     index.prepare_permuted()
     k, P = head_sched["k"], head_sched["nprobe"]
-    out["recall"] = {"k": k, "nprobe": P, "queries": int(Yv_d.shape[0]),
-                     "R": recall_at_k(index, brute, Yv_d, k, P, prec)}
+    Yr = Yv_d[:1000]
+    out["recall"] = {"k": k, "nprobe": P, "queries": int(Yr.shape[0]),
+                     "R": recall_at_k(index, brute, Yr, k, P, prec)}
     # k = m: cheapest k = m (and nprobe) meeting the target, else the most accurate
     for mode, name in ((0, "deann"), (2, "deannp")):
         best = None
@@ -370,7 +375,7 @@ def schedules_and_recall(index, X, Yd, Yv_d, exact_v, head_sched, prec, h, torch
         run = lambda: ex.query(Yd, 100, 1000, nprobe=1, precision=prec, sample_mode=mode)
         ms = time_calls(run, 3, torch)
         fixed[name] = {"qps": nq / (ms / 1e3), "test_rel_err": rel_err(run().cpu().numpy(), et)}
-    fixed["recall"] = recall_at_k(ex, brute, Yv_d, 100, 1, prec)
+    fixed["recall"] = recall_at_k(ex, brute, Yv_d[:1000], 100, 1, prec)
     tuned_x, _ = tune(ex, Yv_d, ev, torch, prec)
     run = lambda: ex.query(Yd, tuned_x["k"], tuned_x["m"], nprobe=tuned_x["nprobe"],
                            precision=prec)

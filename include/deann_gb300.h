@@ -142,7 +142,7 @@ kde_status kde_export_ivf(kde_index* index, float* centroids, int32_t* assign);
 /* kde_search -- the ANN subroutine of Algorithm 1, line 2: the k nearest
  * points (Euclidean) among the lists of the nprobe nearest centroids.
  *   Y      nq x d queries; nq >= 0.
- *   k      1 <= k <= 1024; 1 <= nprobe <= min(nlist, 256).
+ *   k      1 <= k <= 2048; 1 <= nprobe <= min(nlist, 256).
  *   nbr    nq x k original point ids sorted by (distance, id); -1 pads rows
  *          with fewer than k candidates.
  *   d2     nq x k squared distances (FP32, difference form) or NULL; +inf pads.
@@ -155,7 +155,7 @@ kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, i
  * neighbours' contribution is summed exactly; S = m draws uniform on X \ X_1
  * (with repetition, by rejection of draws in X_1; or opts.sample_mode = 1);
  * out = (1/n) [ sum_{X_1} K + ((n - k')/m) sum_S K ] with k' = |X_1|.
- *   k      0 <= k <= min(n, 1024) (k = 0 is plain random sampling);
+ *   k      0 <= k <= min(n, 2048) (k = 0 is plain random sampling);
  *   m      >= 0 (m = 0 keeps only the neighbours' exact contribution);
  *   nprobe 1 <= nprobe <= min(nlist, 256) (ignored when k = 0).
  *   out    nq estimates (FP32).
@@ -248,7 +248,7 @@ kde_status kde_mean_shift(kde_index* index, float* Y, int64_t nq, int32_t steps,
  * log h <- log h + lr dl/dlog h (dl/dlog h grows with d: lr of order 1/d
  * keeps the steps stable); the index keeps the final h.
  *   zid       nz training point ids (rows of the indexed X), host or device.
- *   k         0 <= k <= 1023 search neighbours (nprobe as in kde_search).
+ *   k         0 <= k <= 2047 search neighbours (nprobe as in kde_search).
  *   m         samples per training point (sample_mode 0 or 1).
  *   h_trace   HOST, iters + 1 floats: h before the first and after each step.
  *   ll_trace  HOST or NULL, iters doubles: l(h) before each step.

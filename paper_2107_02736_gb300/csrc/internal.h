@@ -22,9 +22,9 @@
 namespace deann {
 
 constexpr int kMaxDim = 4096;        // largest supported d
-constexpr int kMaxK = 1024;          // largest neighbour count k
+constexpr int kMaxK = 2048;          // largest neighbour count k
 constexpr int kMaxProbe = 256;       // largest nprobe
-constexpr int kSelectCap = 2048;     // largest candidate count kept for rescoring
+constexpr int kSelectCap = 4096;     // largest candidate count kept for rescoring
 constexpr int kTile = 64;            // SIMT distance tile edge
 
 // Row stride (in floats) of every FP32 row-major matrix: d rounded up to a

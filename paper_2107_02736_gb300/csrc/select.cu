@@ -419,7 +419,8 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
                                                        int nprobe, int kprime,
                                                        int32_t* __restrict__ probes,
                                                        float* __restrict__ probe_d2) {
-  __shared__ SelectSmem sm;
+  extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
+  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* vals = D + q * L;
@@ -552,7 +553,8 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
 // Neighbour selection from the scan's candidate buffer.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
-  __shared__ SelectSmem sm;
+  extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
+  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
   __shared__ int64_t s_seg[kMaxProbe + 1];
   __shared__ int64_t s_lstart[kMaxProbe];
   __shared__ int64_t s_llen[kMaxProbe];
@@ -888,7 +890,8 @@ void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int
   if (nq <= 0) return;
   int kprime = nprobe + margin;
   if (kprime > kSelectCap) kprime = kSelectCap;
-  k_select_probes<<<(unsigned)nq, kNT, 0, s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_probes), sizeof(SelectSmem));
+  k_select_probes<<<(unsigned)nq, kNT, sizeof(SelectSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
                                                probe_d2);
 }
 
@@ -925,7 +928,8 @@ void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_
 
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
-  k_select_neighbors<<<(unsigned)a.nq, kNT, 0, s>>>(a);
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), sizeof(SelectSmem));
+  k_select_neighbors<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a);
 }
 
 }  // namespace deann

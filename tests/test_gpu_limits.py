@@ -112,10 +112,27 @@ def test_sample_counts_around_chunks(pkg, m, mode):
 
 
 def test_k_equals_n_at_the_largest_k(pkg):
-    X, Y = _data(1024, 8, 30, seed=8)
+    X, Y = _data(2048, 8, 30, seed=8)
     index = pkg.KDEIndex(_dev(X), "laplacian", 3.0, nlist=4, seed=2)
-    out = index.query(_dev(Y), 1024, 100, nprobe=4, precision=1)
+    out = index.query(_dev(Y), 2048, 100, nprobe=4, precision=1)
     assert_kde_close(out.cpu().numpy(), oracle.exact(X, Y, "laplacian", 3.0))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_largest_k_search_and_estimate(pkg, precision):
+    """k = 2048 of n = 30,000 through the IVF: neighbours against the oracle's
+    search of the same lists, estimates against the oracle with them."""
+    X, Y = _data(30_000, 16, 40, seed=13)
+    h = _bandwidth(16)
+    index = pkg.KDEIndex(_dev(X), "gaussian", h, nlist=64, seed=3)
+    C, assign = index.export_ivf()
+    out, nbr = index.query(_dev(Y), 2048, 700, nprobe=16, precision=precision, seed=4,
+                           return_neighbors=True)
+    nbr = nbr.cpu().numpy()
+    _, want, wd2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, 16, 2048)
+    assert_neighbours_match(X, Y, nbr, want, wd2)
+    assert_kde_close(out.cpu().numpy(), oracle.deann(X, Y, "gaussian", h, nbr, 700, 4))
+    assert index.margin_failures() == 0
 
 
 @pytest.mark.parametrize("kernel", ["gaussian", "laplacian"])

@@ -432,6 +432,6 @@ def test_fit_bandwidth_argument_errors(pkg):
     with pytest.raises(pkg.KDEError):
         index.fit_bandwidth(np.array([0, 500], np.int32), 5, 10)   # id out of range
     with pytest.raises(pkg.KDEError):
-        index.fit_bandwidth(np.array([0, 1], np.int32), 1024, 10)  # k > 1023
+        index.fit_bandwidth(np.array([0, 1], np.int32), 2048, 10)  # k > 2047
     with pytest.raises(pkg.KDEError):
         index.fit_bandwidth(np.array([0, 1], np.int32), 5, 10, sample_mode=2)
