@@ -40,20 +40,25 @@ __global__ void k_query_norms(const float* __restrict__ Y, int64_t nq, int dp,
   if (lane == 0) out[q] = s;
 }
 
-struct SelectSmem {
+template <int Cap>
+struct SelectSmemT {
   int hist[256];
   int warp_a[kNW];
   int warp_b[kNW];
   int digit, before;
-  int slot[kSelectCap];
-  unsigned long long key[kSelectCap];
+  int slot[Cap];
+  unsigned long long key[Cap];
 };
+using SelectSmem = SelectSmemT<kSelectCap>;  // neighbour selection
+constexpr int kProbeCap = 512;               // probe selection: nprobe + margin <= 384
+using ProbeSmem = SelectSmemT<kProbeCap>;
 
 // Selects the K smallest of vals[0..cnt) (1 <= K <= min(cnt, kSelectCap)):
 // sm.slot[0..K) receives their indices (those strictly below the K-th key in
 // index order, then the lowest-index ties).  Returns the K-th key.
-__device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, int K,
-                                 SelectSmem& sm, bool collect = true) {
+template <class SM>
+__device__ uint32_t block_select(const float* __restrict__ vals, int64_t cnt, int K, SM& sm,
+                                 bool collect = true) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t prefix = 0, pmask = 0;
   int want = K;
@@ -384,7 +389,8 @@ __device__ uint32_t smem_kth_dist(SelectSmem& sm, int K, int k) {
 
 // Bitonic sort of sm.key[0..cnt) ascending (cnt padded to a power of two
 // with all-ones keys).
-__device__ void block_sort_keys(SelectSmem& sm, int cnt) {
+template <class SM>
+__device__ void block_sort_keys(SM& sm, int cnt) {
   int P2 = 1;
   while (P2 < cnt) P2 <<= 1;
   for (int i = cnt + threadIdx.x; i < P2; i += kNT) sm.key[i] = ~0ull;
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
                                                        int32_t* __restrict__ probes,
                                                        float* __restrict__ probe_d2) {
   extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
-  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
+  ProbeSmem& sm = *reinterpret_cast<ProbeSmem*>(sel_dyn4);
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* vals = D + q * L;
@@ -889,9 +895,9 @@ void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int
                           float* probe_d2, cudaStream_t s) {
   if (nq <= 0) return;
   int kprime = nprobe + margin;
-  if (kprime > kSelectCap) kprime = kSelectCap;
-  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_probes), sizeof(SelectSmem));
-  k_select_probes<<<(unsigned)nq, kNT, sizeof(SelectSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
+  if (kprime > kProbeCap) kprime = kProbeCap;
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_probes), sizeof(ProbeSmem));
+  k_select_probes<<<(unsigned)nq, kNT, sizeof(ProbeSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
                                                probe_d2);
 }
 
