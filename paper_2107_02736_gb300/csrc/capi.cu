@@ -157,8 +157,6 @@ struct StageTimer {
   }
 };
 
-int select_margin(int k, int precision) { return precision == 0 ? k / 4 + 16 : k + 32; }
-
 float scan_err_scale(int dp, int precision) {
   const float u = 1.0f / 16777216.0f;  // 2^-24
   if (precision == 0) return 2.0f * ((float)dp / 32.0f + 40.0f) * u;
@@ -328,8 +326,6 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
                       bool ids_only = false) {
   const SearchBufs& s = cb.search;
   const int L = ix->nlist;
-  const int margin = select_margin(k, precision);
-  const int kprime = std::min(kSelectCap, k + margin);
   for (int64_t q0 = 0; q0 < nq; q0 += s.qc) {
     const int64_t nc = std::min<int64_t>(s.qc, nq - q0);
     const float* Yc = cb.Yp + q0 * ix->dp;
@@ -392,7 +388,6 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.d = ix->d;
     a.dp = ix->dp;
     a.k = k;
-    a.kprime = kprime;
     a.kern = ix->kern;
     a.h = ix->h;
     a.err_scale = scan_err_scale(ix->dp, precision);

@@ -220,7 +220,7 @@ struct SelectArgs {
   const float* Yn;
   int64_t nq;
   int d, dp;
-  int k, kprime;
+  int k;
   int kern;
   float h;
   float err_scale;           // approx-distance error bound per unit of (|x| + |y|)^2

@@ -3,20 +3,26 @@
 // points).
 //
 //  * query norms |y|^2;
-//  * probe selection: the nprobe nearest centroids of each query;
+//  * probe selection: the nprobe nearest centroids of each query (radix
+//    select of a margin, FP32 rescoring, sort);
 //  * the (query, probe) work plan that groups pairs by list for the
-//    list-major scan;
-//  * neighbour selection: from the approximate distances written by the scan,
-//    a block-wide radix select keeps the k' = k + margin smallest, those are
-//    rescored in difference form with compensated FP32 arithmetic, sorted by
-//    (distance, id) and the first k are returned, together with the exact
-//    neighbour contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1, line 4).
+//    list-major scan, candidate segments aligned to 32 floats, and the order
+//    in which queries are selected (grouped by nearest list);
+//  * neighbour selection, one CTA per query, from the approximate distances
+//    the scan wrote: t_k, the k-th smallest approximate distance, is
+//    bracketed by a histogram; every candidate whose approximate distance is
+//    within 2E of t_k is collected (E bounds the scan's error for this query:
+//    the true k-th distance is at most t_k + E and every true top-k point has
+//    an approximate distance at most t_k + 2E, so the set holds the exact top
+//    k); those rows are rescored in FP32 difference form, and only the
+//    candidates inside the FP32 error band of the k-th are re-ranked with
+//    compensated arithmetic.  Returned: the k neighbours (sorted by (distance,
+//    id), or as a set for the query path) and the exact neighbour
+//    contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1, line 4).
 //
-// The margin is certified per query: every unselected candidate has an
-// approximate distance >= T (the k'-th smallest) and an error bound E, so if
-// T - E exceeds the k-th rescored distance plus its own bound, no unselected
-// candidate can belong to the top k.  Queries that fail the test are counted
-// in the device error word.
+// More than kSelectCap candidates in the band cannot all be kept: the
+// kSelectCap smallest are rescored and the query is counted as uncertified in
+// the device error word (kde_stats).
 #include "common.cuh"
 
 namespace deann {
