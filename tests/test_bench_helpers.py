@@ -1,0 +1,60 @@
+"""Host helpers of bench.py: the FP8-e4m3 and BF16 roundings of the FP8 scan
+study against PyTorch's own conversions, and the roofline arithmetic."""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _values(rng, n=20000):
+    v = np.concatenate([
+        rng.standard_normal(n) * 10.0,
+        rng.uniform(-448, 448, n),
+        rng.uniform(-2 ** -6, 2 ** -6, n),           # subnormal range of e4m3
+        np.ldexp(rng.integers(1, 16, 1000), -9) * rng.choice([-1, 1], 1000),
+    ])
+    return v.astype(np.float32).astype(np.float64)
+
+
+def test_round_bf16_matches_torch():
+    v = _values(np.random.default_rng(1))
+    want = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bench.round_bf16(v), want)
+
+
+def test_round_e4m3_matches_torch():
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn in this torch")
+    v = _values(np.random.default_rng(2))
+    v = v[np.abs(v) <= 448.0]  # the study saturates beyond; torch maps to NaN
+    want = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(bench.round_e4m3(v), want)
+
+
+def test_round_e4m3_grid_and_saturation():
+    # every e4m3 value is a fixed point; halfway points go to the even neighbour
+    grid = [0.0]
+    for e in range(-6, 9):
+        for mnt in range(8):
+            grid.append((1 + mnt / 8) * 2.0 ** e)
+    grid += [k * 2.0 ** -9 for k in range(1, 8)]
+    grid = np.array(sorted(set(g for g in grid if g <= 448)))
+    assert np.array_equal(bench.round_e4m3(grid), grid)
+    assert bench.round_e4m3(np.array([1.0625]))[0] == 1.0     # tie to even mantissa 000
+    assert bench.round_e4m3(np.array([1.1875]))[0] == 1.25    # tie to even mantissa 010
+    assert bench.round_e4m3(np.array([1e6]))[0] == 448.0      # saturates
+    assert bench.round_e4m3(np.array([-1e6]))[0] == -448.0
+
+
+def test_stage_work_and_alu_peak():
+    # the estimator's bytes are m rows of d FP32 values (+ query, ids, output)
+    b, f = bench.stage_work("estimate", 10, 1000, 128, 8, 16, 100, 5.0)
+    assert b == 10 * (100 * 128 * 4 + 128 * 4 + 16 * 4 + 4) and f == 0.0
+    b, f = bench.stage_work("scan", 10, 1000, 128, 8, 16, 100, 50.0)
+    assert f == 2.0 * 10 * 50.0 * 128 and b == 1000 * 128 * 2 + 10 * 50.0 * 4
+    assert bench.fp32_alu_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
