@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--profile-case", type=int, default=0, metavar="NQ",
                    help="run one call of each query-path kernel on NQ queries of the workload "
                         "(for a profiler) and exit")
+    p.add_argument("--profile-schedule", default="1536,4000,8", metavar="K,M,NPROBE",
+                   help="the DEANN schedule --profile-case runs (BF16 scan); the default is "
+                        "the one the tuner picks on this workload")
     return p.parse_args()
 
 
@@ -162,17 +165,17 @@ def src_digest(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(stage):
+def ncu_traffic(stage, sched):
     """DRAM bytes per launch of a stage's kernel at this workload, from the
-    committed ncu summary, if the kernel's source is unchanged since the
-    capture; else None."""
+    committed ncu summary, if the capture ran the same schedule (k, m, nprobe,
+    scan precision) and the kernel's source is unchanged since; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except OSError:
         return None
     e = t.get(stage)
-    if not e or e.get("src_sha") != src_digest(e["source"]):
+    if not e or e.get("src_sha") != src_digest(e["source"]) or e.get("schedule") != sched:
         return None
     return e.get("bytes_per_launch_full")
 
@@ -572,7 +575,7 @@ def stage_work(stage, nq, n, d, nlist, k, m, cbar):
     return 0, 0.0
 
 
-def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind):
+def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind, sched):
     """Achieved vs peak for one stage of the query path, from its algorithmic
     bytes or flops per call and its measured device time per call; the bound
     is whichever of the two takes longer at peak."""
@@ -590,7 +593,7 @@ def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind):
         r = {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
              "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"}
     r["frac"] = r["achieved"] / r["peak"]
-    r["traffic"] = ncu_traffic(stage)
+    r["traffic"] = ncu_traffic(stage, sched)
     r["stage"] = stage
     r["ms_per_call"] = ms
     r["t_min_ms"] = 1e3 * max(t_hbm, t_fl)
@@ -707,23 +710,26 @@ def fp8_study(args):
 
 
 def profile_case(args):
-    """One batch of args.profile_case queries through each path at the bench's
-    schedule (k = 1024, m = 8000, nprobe = 8, BF16 scan, h = 12.85): DEANN,
-    DEANNP (tiled windows), and the tensor-core exact KDE; one launch each of
-    k_scan_tc, k_select_neighbors, k_estimate, k_window_tile, k_exact_tc."""
+    """One batch of args.profile_case queries through each path at the DEANN
+    schedule args.profile_schedule (BF16 scan, h = 12.85): DEANN, DEANNP (tiled
+    windows), and the tensor-core exact KDE; one launch each of k_scan_tc,
+    k_select_neighbors, k_estimate, k_window_tile, k_exact_tc."""
     import torch
     import paper_2107_02736_gb300 as pkg
+    k, m, P = (int(v) for v in args.profile_schedule.split(","))
     dev = torch.device("cuda", 0)
     n = int(1_000_000 * args.scale)
     X, Y, _ = workloads.mixture_embed(n=n, nq=args.profile_case)
     index = pkg.KDEIndex(torch.from_numpy(X).to(dev), args.kernel, 12.85, nlist=1024, seed=1)
     index.prepare_permuted()
     Yd = torch.from_numpy(Y).to(dev)
-    a = index.query(Yd, 1024, 8000, nprobe=8, seed=1, precision=1)
-    b = index.query(Yd, 1024, 8000, nprobe=8, seed=1, precision=1, sample_mode=2)
+    a = index.query(Yd, k, m, nprobe=P, seed=1, precision=1)
+    b = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, sample_mode=2)
     c = index.exact(Yd[:1024], path="tensor")
     torch.cuda.synchronize()
-    print("profile case ok", float(a.mean()), float(b.mean()), float(c.mean()))
+    print("profile case ok", json.dumps({"k": k, "m": m, "nprobe": P, "precision": "bf16",
+                                         "nq": args.profile_case}),
+          float(a.mean()), float(b.mean()), float(c.mean()))
 
 
 def main():
@@ -824,9 +830,11 @@ def main():
     dom = max(stages, key=stages.get)
     C_ivf, assign_ivf = index.export_ivf()
     cbar = mean_candidates(X, Y, C_ivf.numpy(), assign_ivf.numpy(), P)
-    roof = roofline(dom, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks, peak_kind)
+    sched_key = {"k": k, "m": m, "nprobe": P, "precision": head}
+    roof = roofline(dom, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks, peak_kind,
+                    sched_key)
     others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks,
-                          peak_kind) for s in ("coarse", "scan", "select", "estimate")
+                          peak_kind, sched_key) for s in ("coarse", "scan", "select", "estimate")
               if s in stages}
     # whole query path: the sum of the stages' times at peak over the step time
     path_roof = {"t_min_ms": sum(o["t_min_ms"] for o in others.values()),

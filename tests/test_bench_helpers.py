@@ -58,3 +58,25 @@ def test_stage_work_and_alu_peak():
     b, f = bench.stage_work("scan", 10, 1000, 128, 8, 16, 100, 50.0)
     assert f == 2.0 * 10 * 50.0 * 128 and b == 1000 * 128 * 2 + 10 * 50.0 * 4
     assert bench.fp32_alu_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+
+
+def test_ncu_traffic_requires_same_schedule_and_source(tmp_path, monkeypatch):
+    """A committed DRAM-traffic figure is used only for the schedule it was
+    captured at and while the kernel's source is unchanged."""
+    import json
+    src = tmp_path / "paper_2107_02736_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "sample.cu").write_text("kernel v1")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sched = {"k": 1536, "m": 4000, "nprobe": 8, "precision": "bf16"}
+    entry = {"kernel": "k_estimate<32>", "source": "sample.cu",
+             "src_sha": bench.src_digest("sample.cu"), "schedule": sched,
+             "bytes_per_launch_full": 123}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"estimate": entry}))
+    assert bench.ncu_traffic("estimate", dict(sched)) == 123
+    assert bench.ncu_traffic("estimate", dict(sched, m=8000)) is None
+    assert bench.ncu_traffic("estimate", dict(sched, precision="fp32")) is None
+    assert bench.ncu_traffic("select", sched) is None
+    (src / "sample.cu").write_text("kernel v2")
+    assert bench.ncu_traffic("estimate", sched) is None
