@@ -90,6 +90,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Requests the 128-byte line holding p into L2 (a hint: no register waits
+// for it, and no fault is raised for it).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Nonnegative float -> order-preserving uint32 (NaN treated as +inf).
 __device__ __forceinline__ uint32_t dist_key(float v) {
   if (!(v >= 0.f)) v = (v < 0.f) ? 0.f : __int_as_float(0x7f800000);

@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
 // --------------------------------------------------------------------------
 // Neighbour selection from the scan's candidate buffer.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
+__global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
   SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
   __shared__ int64_t s_seg[kMaxProbe + 1];
@@ -646,20 +646,30 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
     const float4* X4 = reinterpret_cast<const float4*>(a.XL);
     const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
     const int myrow = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+    // the row of candidate j in the list-ordered copy, or -1
+    auto locate = [&](int j) -> int64_t {
+      if (j >= K) return -1;
+      const int s = sm.slot[j];
+      int lo = 0, hi = a.P - 1;  // last segment with start <= s
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+      }
+      // a slot past its list (the segment's padding) is never a row
+      return s - s_seg[lo] < s_llen[lo] ? s_lstart[lo] + (s - s_seg[lo]) : -1;
+    };
+    const int lines = (a.dp * 4 + 127) >> 7;  // 128-byte lines of a row
+    // lane u (u < 8) locates row j0 + u of the warp's group
+    int64_t p_own = locate(warp * 8 + (lane & 7));
     for (int j0 = warp * 8; j0 < K; j0 += kNW * 8) {
-      // lane u (u < 8) locates row j0 + u in the candidate segments
-      int64_t p_own = -1;
+      // the next group's rows are requested into L2 now, one group ahead of
+      // their loads: lane l takes lines l & 3, (l & 3) + 4, ... of row l >> 2
+      const int64_t p_next = locate(j0 + kNW * 8 + (lane & 7));
       {
-        const int j = j0 + (lane & 7);
-        if (j < K) {
-          const int s = sm.slot[j];
-          int lo = 0, hi = a.P - 1;  // last segment with start <= s
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
-          }
-          // a slot past its list (the segment's padding) is never a row
-          if (s - s_seg[lo] < s_llen[lo]) p_own = s_lstart[lo] + (s - s_seg[lo]);
+        const int64_t pf = __shfl_sync(0xffffffffu, p_next, lane >> 2);
+        if (pf >= 0) {
+          const char* row = reinterpret_cast<const char*>(a.XL + pf * a.dp);
+          for (int ln = lane & 3; ln < lines; ln += 4) prefetch_l2(row + ((size_t)ln << 7));
         }
       }
       int64_t pos[8];
@@ -704,6 +714,7 @@ __global__ void __launch_bounds__(kNT) k_select_neighbors(SelectArgs a) {
       v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
       if ((lane & 3) == 0 && j0 + myrow < K)
         sm.key[j0 + myrow] = p_mine >= 0 ? pack_key(v1, id) : ~0ull;  // ~0: +inf, id -1
+      p_own = p_next;
     }
   }
   __syncthreads();
