@@ -203,6 +203,19 @@ __device__ void window_chunk(const int32_t* __restrict__ wperm, int64_t n, int64
   __syncthreads();
 }
 
+// Requests rows ids[nb .. nb + 8) of X into L2 ahead of a warp's loads of
+// them: lane l takes lines l & 3, (l & 3) + 4, ... of row nb + (l >> 2).
+__device__ __forceinline__ void prefetch_next_rows(const float* __restrict__ X, int dp,
+                                                   const int* ids, int cnt, int nb) {
+  const int lane = threadIdx.x & 31, j = nb + (lane >> 2);
+  if (j >= cnt) return;
+  const int rid = ids[j];
+  if (rid < 0) return;
+  const char* row = reinterpret_cast<const char*>(X + (size_t)rid * dp);
+  const int lines = (dp * 4 + 127) >> 7;
+  for (int ln = lane & 3; ln < lines; ln += 4) prefetch_l2(row + ((size_t)ln << 7));
+}
+
 // Sum of kernel values over rows ids[0..cnt) of X, by groups of G lanes.
 // Returns this thread's partial (lane-in-group 0 holds the group sums).
 template <int G, bool L1>
@@ -223,6 +236,7 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
     int rid[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) rid[u] = base + u < cnt ? ids[base + u] : -1;
+    if (G == 32) prefetch_next_rows(X, dp, ids, cnt, wb + kNW * kUnroll);
     const float4* X4 = reinterpret_cast<const float4*>(X);
     float acc[kUnroll];
 #pragma unroll
@@ -578,6 +592,7 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
     const float4 yv = lane < dp4 ? y4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* X4 = reinterpret_cast<const float4*>(X);
     for (int wb = warp * 8; wb < cnt; wb += kNW * 8) {
+      prefetch_next_rows(X, dp, ids, cnt, wb + kNW * 8);
       float4 diff[8];
       float acc[8];
 #pragma unroll
