@@ -577,40 +577,40 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   const int64_t cnt_real = a.q_real[q];  // candidates
   const float* vals = a.cand + a.q_off[q];
   const float* y = a.Y + q * a.dp;
-  for (int p = tid; p < a.P; p += kNT) {
-    const int l = a.probes[q * a.P + p];
-    s_seg[p] = a.seg_off[q * a.P + p];
-    s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
-    s_llen[p] = l >= 0 ? a.list_off[l + 1] - a.list_off[l] : 0;
-  }
   // Error bound E of the scan's distances for this query: |approx - exact|
   // <= err_scale r^2 with r = |x| + |y| (|x| <= the dataset's largest norm),
   // or, for the centred scan, r = |x~| + |y~| <= list radius + |y - c_probe|.
+  // Every candidate of list l is within rad_l of c_l, so its exact distance
+  // lies in [(|y - c_l| - rad_l)^2, (|y - c_l| + rad_l)^2], and the scan's
+  // value within E of it: bounds for the histogram of t_k.  Warp 0 takes the
+  // probes a lane each (with the probe's candidate segment and list) and
+  // reduces.
   __shared__ float s_E, s_hint_lo, s_hint_hi;
-  if (tid == 0) {
-    s_seg[a.P] = cnt;
-    float r = a.xmax + sqrtf(a.Yn[q]);
-    if (a.centered) {
-      r = 0.f;
-      for (int p = 0; p < a.P; ++p) {
-        const int l = a.probes[q * a.P + p];
-        if (l >= 0) r = fmaxf(r, sqrtf(a.probe_d2[q * a.P + p]) + a.rad[l]);
-      }
-    }
-    s_E = a.err_scale * r * r;
-    // every candidate of list l is within rad_l of c_l, so its exact distance
-    // lies in [(|y - c_l| - rad_l)^2, (|y - c_l| + rad_l)^2], and the scan's
-    // value within E of it: bounds for the histogram of t_k
+  if (warp == 0) {
     float lo = __int_as_float(0x7f800000), hi = 0.f;
-    for (int p = 0; p < a.P; ++p) {
+    for (int p = lane; p < a.P; p += 32) {
       const int l = a.probes[q * a.P + p];
+      s_seg[p] = a.seg_off[q * a.P + p];
+      s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
+      s_llen[p] = l >= 0 ? a.list_off[l + 1] - a.list_off[l] : 0;
       if (l < 0) continue;
-      const float dc = sqrtf(a.probe_d2[q * a.P + p]);
-      lo = fminf(lo, fmaxf(0.f, dc - a.rad[l]));
-      hi = fmaxf(hi, dc + a.rad[l]);
+      const float dc = sqrtf(a.probe_d2[q * a.P + p]), rl = a.rad[l];
+      lo = fminf(lo, fmaxf(0.f, dc - rl));
+      hi = fmaxf(hi, dc + rl);
     }
-    s_hint_lo = hi >= lo ? fmaxf(0.f, lo * lo * (1.f - 1e-5f) - s_E) : -1.f;
-    s_hint_hi = hi >= lo ? hi * hi * (1.f + 1e-5f) + s_E : -1.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      s_seg[a.P] = cnt;
+      // r = max over the probes of |y - c_l| + rad_l (0 with no valid probe)
+      const float r = a.centered ? hi : a.xmax + sqrtf(a.Yn[q]);
+      s_E = a.err_scale * r * r;
+      s_hint_lo = hi >= lo ? fmaxf(0.f, lo * lo * (1.f - 1e-5f) - s_E) : -1.f;
+      s_hint_hi = hi >= lo ? hi * hi * (1.f + 1e-5f) + s_E : -1.f;
+    }
   }
   __syncthreads();
   // Candidates to rescore: every one whose approximate distance is within 2E
