@@ -410,18 +410,21 @@ class GraphedQuery:
     query id is written to a device scalar that the estimator reads, so every
     replay draws the sample streams the direct call with that qid_offset
     would draw (with sample_mode=2, the permuted windows of Algorithm 2 that
-    follow on from the previous batch's).
+    follow on from the previous batch's).  With neighbors=True the replay
+    also returns the neighbour ids (X_1) that a backward pass needs.
     """
 
     def __init__(self, index: KDEIndex, capacity, k, m, nprobe=1, seed=0, precision=0,
-                 sample_mode=0):
+                 sample_mode=0, neighbors=False):
         self.index, self.capacity = index, int(capacity)
+        self.neighbors = bool(neighbors) and k > 0
         dev = index.device
         self.Y = torch.zeros((self.capacity, index.d), dtype=torch.float32, device=dev)
         self.qid = torch.zeros(1, dtype=torch.int64, device=dev)
         index.reserve(self.capacity, k, m, nprobe)
         args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision,
-                    sample_mode=sample_mode, dev_qid=self.qid)
+                    sample_mode=sample_mode, dev_qid=self.qid,
+                    return_neighbors=self.neighbors)
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):  # first launches (module loading) outside the capture
@@ -429,8 +432,10 @@ class GraphedQuery:
         torch.cuda.current_stream(dev).wait_stream(side)
         torch.cuda.synchronize(dev)
         self.graph = torch.cuda.CUDAGraph()
+        self.nbr = None
         with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
-            self.out = index.query(self.Y, **args)
+            res = index.query(self.Y, **args)
+        self.out, self.nbr = res if self.neighbors else (res, None)
 
     def __call__(self, Yb, qid_offset=0):
         nb = int(Yb.shape[0])
@@ -439,20 +444,24 @@ class GraphedQuery:
         self.Y[:nb].copy_(Yb, non_blocking=True)
         self.qid.fill_(int(qid_offset))
         self.graph.replay()
-        return self.out[:nb]
+        return (self.out[:nb], self.nbr[:nb]) if self.neighbors else self.out[:nb]
 
 
 class BatchServer:
     """Serves uneven batches with CUDA graphs captured per power-of-two
-    capacity class (16 ... max_batch); the query ids run on across batches."""
+    capacity class (16 ... max_batch); the query ids run on across batches.
+    With neighbors=True each call returns (estimates, neighbour ids) and
+    backward() runs the adjoint of the last batch served (its sets fixed)."""
 
     def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192,
-                 sample_mode=0):
+                 sample_mode=0, neighbors=False):
         self.index, self.args = index, dict(k=k, m=m, nprobe=nprobe, seed=seed,
-                                            precision=precision, sample_mode=sample_mode)
+                                            precision=precision, sample_mode=sample_mode,
+                                            neighbors=neighbors)
         self.max_batch = int(max_batch)
         self.graphs = {}
         self.next_qid = 0
+        self.last_qid = 0
 
     def _graph(self, nb):
         cap = 16
@@ -467,8 +476,17 @@ class BatchServer:
         if nb > self.max_batch:
             raise ValueError(f"batch of {nb} exceeds max_batch {self.max_batch}")
         out = self._graph(nb)(Yb, self.next_qid)
+        self.last_qid = self.next_qid
         self.next_qid += nb
         return out
+
+    def backward(self, Yb, nbr, gout=None):
+        """(estimate, dY, dlogh per query) of the last batch served, from its
+        neighbour ids and its regenerated sample streams."""
+        a = self.args
+        return self.index.grad_with_neighbors(Yb, nbr, a["m"], seed=a["seed"], gout=gout,
+                                              sample_mode=a["sample_mode"],
+                                              qid_offset=self.last_qid)
 
 
 class DeannKDE(torch.autograd.Function):

@@ -2,9 +2,10 @@
 
 The low-dimensional workload runs at full size on every query.  The
 1M-point d=128 workload runs at full size in the launch configuration the
-benchmark times (BF16 tcgen05 scan, k = 1024, m = 8000, nprobe = 8, 10k
-queries) and sampled queries are checked one by one.  The others run at
-reduced n with their own dimension, kernel and parameters.
+benchmark times (BF16 tcgen05 scan, k = 1536, m = 4000, nprobe = 8, 10k
+queries; DEANNP with m = 8000) and sampled queries are checked one by one.
+The others run here at reduced n with their own dimension, kernel and
+parameters (their full sizes are in test_gpu_full_size.py).
 """
 import numpy as np
 import pytest
@@ -58,7 +59,7 @@ def embed(pkg):
 @pytest.mark.parametrize("precision", [1, 0])
 def test_embed_full_size_sampled(embed, precision):
     X, Y, index, C, assign = embed
-    k, m, P, h = 1024, 8000, 8, 12.85
+    k, m, P, h = 1536, 4000, 8, 12.85
     out, nbr = index.query(_dev(Y), k, m, nprobe=P, seed=3, precision=precision,
                            return_neighbors=True)
     out, nbr = out.cpu().numpy(), nbr.cpu().numpy()
@@ -77,7 +78,7 @@ def test_embed_full_size_deannp_sampled(embed):
     """DEANNP (Algorithm 2) at full size: the 1M-entry permutation is
     bit-exact and sampled estimates match the oracle's windows."""
     X, Y, index, _, _ = embed
-    k, m, P, h = 1024, 8000, 8, 12.85
+    k, m, P, h = 1536, 8000, 8, 12.85
     perm = index.prepare_permuted(return_perm=True).cpu().numpy()
     want_perm = oracle.feistel_perm(1, X.shape[0])
     assert np.array_equal(perm, want_perm)

@@ -99,8 +99,10 @@ def _sparse_points(rng, n, probs, chunk=1 << 16):
         e = min(n, s + chunk)
         lab = rng.integers(0, probs.shape[0], size=e - s)
         mask = rng.random((e - s, d), dtype=np.float32) < probs[lab]
-        vals = rng.beta(2.0, 5.0, size=(e - s, d)).astype(np.float32)
-        out[s:e] = np.where(mask, vals, np.float32(0.0))
+        blk = np.zeros((e - s, d), dtype=np.float32)
+        # Beta(2, 5) values are drawn for the nonzero entries only
+        blk[mask] = rng.beta(2.0, 5.0, size=int(mask.sum())).astype(np.float32)
+        out[s:e] = blk
     return out
 
 
