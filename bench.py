@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="shrink n (debug only)")
     p.add_argument("--kernel", default="gaussian")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--schedule", default="", metavar="K,M,NPROBE",
+                   help="use this DEANN schedule for both scan precisions instead of tuning")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     p.add_argument("--no-schedules", dest="schedules", action="store_false",
                    help="skip the recall / k = m / fixed-parameter runs (untimed extras)")
@@ -250,7 +252,13 @@ def choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args):
     spec = workloads.CONFIGS[2]
     sched, tuned = {}, {}
     for name, prec in PRECISIONS.items():
-        if args.no_tune:
+        if args.schedule:
+            k, m, P = (int(v) for v in args.schedule.split(","))
+            est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=prec)
+            sched[name] = dict(k=k, m=m, nprobe=P, val_ms=0.0,
+                               val_err=rel_err(est.cpu().numpy(), exact_v))
+            tuned[name] = []
+        elif args.no_tune:
             sched[name] = dict(k=spec["k"], m=spec["m"], nprobe=spec["nprobe"], val_ms=0.0,
                                val_err=None)
             tuned[name] = []
@@ -437,6 +445,115 @@ def differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev
                             "note": "leave-one-out maximum-likelihood h; the headline h is "
                                     "bisected to a mean KDE of 1e-3 instead"}
     index.set_bandwidth(h)
+    return out
+
+
+def precision_form(torch, pkg, dev):
+    """The sparse image-like workload at full size (n = 1M, d = 784, 80 % zeros,
+    10,000 test queries; Gaussian kernel, h bisected to a mean exact KDE of
+    1e-4 on 1,000 validation queries): DEANN at k = 200, m = 2,000 over 2,048
+    lists with nprobe = 32, BF16 list scan (FP32 rescoring) next to the FP32
+    scan, each against the exact KDE of every test query."""
+    sp = workloads.CONFIGS[3]
+    X, Y, Yv = workloads.sparse_image()
+    nq = Y.shape[0]
+    t0 = time.perf_counter()
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), "gaussian", 1.0, nlist=sp["nlist"],
+                         seed=1)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Yd, Yv_d = torch.from_numpy(Y).to(dev), torch.from_numpy(Yv[:1000]).to(dev)
+    h, mu = fit_bandwidth(index, Yv_d, sp["target_mu"])
+    exact_t = index.exact(Yd).cpu().numpy()
+    ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
+    k, m, P = sp["k"], sp["m"], sp["nprobe"]
+    out = {"workload": sp["name"], "n": int(X.shape[0]), "d": int(X.shape[1]), "nq": int(nq),
+           "kernel": "gaussian", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"], "k": k,
+           "m": m, "nprobe": P, "build_s": build_s, "exact_qps": nq / (ms_exact / 1e3)}
+    ids = {}
+    for name, prec in PRECISIONS.items():
+        est, nb = index.query(Yd, k, m, nprobe=P, seed=6, precision=prec, return_neighbors=True)
+        ms = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=5, precision=prec), 3,
+                        torch)
+        out[name] = {"qps": nq / (ms / 1e3), "ms_per_call": ms,
+                     "test_rel_err": rel_err(est.cpu().numpy(), exact_t)}
+        ids[name] = np.sort(nb.cpu().numpy(), 1)
+    out["same_neighbours"] = bool(np.array_equal(ids["fp32"], ids["bf16"]))
+    out["margin_failures"] = index.margin_failures()
+    index.close()
+    return out
+
+
+def batched_form(torch, pkg, dev):
+    """The unit-norm power-law workload at full size (n = 4M, d = 300,
+    exponential kernel, h bisected to a mean exact KDE of 1e-3 on 1,000
+    validation queries; BF16 scan, k = 200, m = 2,000, 4,096 lists, nprobe
+    tuned on the validation queries): 100,000 test queries in 64 batches of 16
+    to 8,192 served by CUDA-graph replays (one graph per power-of-two
+    capacity), the backward pass on every tenth batch; error against the
+    exact KDE on 4,096 of the test queries."""
+    sp = workloads.CONFIGS[5]
+    X, Y, Yv = workloads.unit_powerlaw()
+    sizes = workloads.uneven_batches()
+    nq = Y.shape[0]
+    t0 = time.perf_counter()
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), "exponential", 1.0, nlist=sp["nlist"],
+                         seed=1)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Yd, Yv_d = torch.from_numpy(Y).to(dev), torch.from_numpy(Yv[:1000]).to(dev)
+    h, mu = fit_bandwidth(index, Yv_d, sp["target_mu"])
+    exact_v = index.exact(Yv_d).cpu().numpy()
+    k, m = sp["k"], sp["m"]
+    trials = []
+    for P in (4, 8, 16, 32, 64):
+        err = rel_err(index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=1).cpu().numpy(),
+                      exact_v)
+        ms = time_calls(lambda: index.query(Yv_d, k, m, nprobe=P, seed=1, precision=1), 2,
+                        torch)
+        trials.append({"nprobe": P, "val_rel_err": err, "val_ms": ms})
+        if err <= TUNE_ERR:
+            break
+    ok = [t for t in trials if t["val_rel_err"] <= TUNE_ERR]
+    P = (min(ok, key=lambda t: t["val_ms"]) if ok
+         else min(trials, key=lambda t: t["val_rel_err"]))["nprobe"]
+    server = pkg.BatchServer(index, k, m, nprobe=P, seed=9, precision=1, max_batch=8192,
+                             neighbors=True)
+    res = torch.empty(nq, dtype=torch.float32, device=dev)
+
+    def serve():
+        server.next_qid, start = 0, 0
+        for b, nb in enumerate(sizes):
+            nb = int(nb)
+            Yb = Yd[start:start + nb]
+            est, ids = server(Yb)
+            res[start:start + nb].copy_(est)
+            if b % 10 == 0:
+                server.backward(Yb, ids)
+            start += nb
+
+    serve()  # captures the graphs
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    serve()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    sub = np.random.default_rng(7).choice(nq, 4096, replace=False)
+    exact_s = index.exact(Yd[torch.from_numpy(sub).to(dev)]).cpu().numpy()
+    err = rel_err(res.cpu().numpy()[sub], exact_s)
+    ms_one = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=9, precision=1), 2, torch)
+    out = {"workload": sp["name"], "n": int(X.shape[0]), "d": int(X.shape[1]), "nq": int(nq),
+           "kernel": "exponential", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"], "k": k,
+           "m": m, "nprobe": P, "nprobe_trials": trials, "build_s": build_s,
+           "batches": int(sizes.size), "batch_min": int(sizes.min()),
+           "batch_max": int(sizes.max()), "graphs": len(server.graphs),
+           "backward_batches": int((np.arange(sizes.size) % 10 == 0).sum()),
+           "served_ms": ms, "served_qps": nq / (ms / 1e3),
+           "one_call_qps": nq / (ms_one / 1e3), "rel_err_4096": err,
+           "margin_failures": index.margin_failures()}
+    index.close()
     return out
 
 
@@ -848,6 +965,8 @@ def main():
                                       pkg, dev)
         forms = differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev)
         extras["nn_contribution"] = nn_contribution_map(torch, pkg, dev)
+        forms["precision_form"] = precision_form(torch, pkg, dev)
+        forms["batched_form"] = batched_form(torch, pkg, dev)
 
     cpu = None
     if rank == 0 and world == 1:
