@@ -11,10 +11,13 @@
 //   warp 1 (one lane): MMA issuer, tcgen05.mma M=128 (points) x N=BN
 //                      (queries) x K=16 into a double-buffered TMEM
 //                      accumulator; warp 1 also owns the TMEM allocation;
-//   warps 2-5        : epilogue, one TMEM lane (= one list point) per thread:
+//   warps 2-9        : epilogue, one TMEM lane (= one list point) per thread:
 //                      D^2 = |x|^2 + |y|^2 - 2 acc, clamped at 0, written to
 //                      each query's candidate segment (coalesced along points;
-//                      the segment's padding to 32 floats gets +inf).
+//                      the segment's padding to 32 floats gets +inf).  Two
+//                      warps share each 32-lane TMEM quadrant and take
+//                      alternate groups of 16 query columns, so twice as many
+//                      warps keep candidate stores in flight.
 // Both operands are centred on the list's centroid c_l (x~ = x - c_l, stored
 // that way at build time; y~ = y - c_l, formed here), which leaves the
 // distances unchanged but shrinks the magnitudes that the BF16 rounding error
@@ -36,7 +39,8 @@ constexpr int kBM = 128;          // points per tile (MMA M)
 constexpr int kBK = 64;           // BF16 elements per 128-byte row chunk
 constexpr int kStages = 4;
 constexpr int kStageBytes = kBM * 128;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;     // epilogue warps, a multiple of 4 (the TMEM lane quadrants)
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct ScanShared {
   uint64_t full[kStages];
@@ -85,7 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sh.tfull[b], 1);
-      tc::mbar_init(&sh.tempty[b], 4);
+      tc::mbar_init(&sh.tempty[b], kEpiWarps);
     }
     tc::mbar_init(&sh.drain, 1);
     tc::fence_mbar_init();
@@ -209,11 +213,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_wait(&sh.drain, 0u, &no_abort);
     }
   } else {
-    // ---------------- epilogue: warps 2..5 ----------------
+    // ---------------- epilogue: warps 2..9 ----------------
     // one TMEM lane (= one list point) per thread; for each query the warp's
     // 32 points go out as one coalesced 128-byte store.  Points past the list
     // up to its 32-float padded length get +inf (the segment's padding).
+    // A warp reads only its own lane quadrant (warp id mod 4); the second
+    // warp of a quadrant starts at column 16.
     const int lg = (warp & 3) * 32;
+    const int cstart = ((warp - 2) >> 2) * 16;
+    constexpr int cstep = 16 * (kEpiWarps / 4);
     const int row = lg + lane;
     const int64_t padlen = (len + 31) & ~(int64_t)31;
     for (int tt = 0; tt < ntiles; ++tt) {
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool valid = pt < len, pad = !valid && pt < padlen;
       const float xn = valid ? XLcn[xb + pt] : 0.f;
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * BN);
-      for (int c0 = 0; c0 < npairs; c0 += 16) {
+      for (int c0 = cstart; c0 < npairs; c0 += cstep) {
         uint32_t v[16];
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
 #pragma unroll
