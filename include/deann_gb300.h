@@ -88,6 +88,15 @@ typedef struct {
                                runs: a call captured in a CUDA graph then
                                serves a new batch (new sample streams) per
                                replay by rewriting this value */
+  const void* dev_active_rows; /* kde_query only: NULL, or a DEVICE pointer
+                               to an int64 A.  Rows 0 .. A-1 are the queries;
+                               rows at or past A get no probes, no neighbours
+                               and no samples: their nbr entries are -1 and
+                               their out entries unspecified.  A call
+                               captured in a CUDA graph at a fixed capacity
+                               then serves a smaller batch per replay by
+                               rewriting A, with only the query-centroid
+                               distances computed for every row */
 } kde_opts;
 
 /* kde_build -- build an index over X (Section 4: FAISS-style inverted file).

@@ -44,7 +44,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
                 ("kmeans_iters", ctypes.c_int32), ("exact_path", ctypes.c_int32),
                 ("query_id_offset", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("dev_query_id_offset", ctypes.c_void_p)]
+                ("dev_query_id_offset", ctypes.c_void_p), ("dev_active_rows", ctypes.c_void_p)]
 
 
 STAGES = ["stage", "coarse", "plan", "scan", "select", "estimate", "exact", "grad"]
@@ -281,9 +281,12 @@ class KDEIndex:
         return nbr, d2
 
     def query(self, Y, k, m, nprobe=1, seed=0, precision=0, sample_mode=0, qid_offset=0,
-              return_neighbors=False, dev_qid=None):
+              return_neighbors=False, dev_qid=None, dev_active=None):
         """DEANN estimates (Algorithm 1).  dev_qid: optional int64 CUDA tensor
-        of one element added to qid_offset on the device (graph replays)."""
+        of one element added to qid_offset on the device (graph replays).
+        dev_active: optional int64 CUDA tensor of one element A; only rows
+        below A are served (their neighbours -1 and estimates unspecified
+        past it)."""
         Y = self._prep(Y)
         nq = Y.shape[0]
         out = torch.empty(nq, dtype=torch.float32, device=Y.device)
@@ -292,6 +295,8 @@ class KDEIndex:
         o = self._opts(precision, sample_mode, qid_offset, host=not Y.is_cuda)
         if dev_qid is not None:
             o.dev_query_id_offset = dev_qid.data_ptr()
+        if dev_active is not None:
+            o.dev_active_rows = dev_active.data_ptr()
         with torch.cuda.device(self._device):
             _check(_lib.kde_query(self._h, _ptr(Y), nq, int(k), int(m), int(nprobe),
                                   int(seed) & (2**64 - 1), _ptr(out), _ptr(nbr),
@@ -405,11 +410,11 @@ class GraphedQuery:
 
     The index's scratch is reserved before the capture, so the captured call
     allocates nothing.  Each replay serves one batch of at most `capacity`
-    queries: the batch is copied into the static input (rows past the batch
-    keep stale values; their outputs are discarded) and the batch's first
-    query id is written to a device scalar that the estimator reads, so every
-    replay draws the sample streams the direct call with that qid_offset
-    would draw (with sample_mode=2, the permuted windows of Algorithm 2 that
+    queries: the batch is copied into the static input, its size is written
+    to a device scalar that marks the rows past it inactive (they get no
+    probes, neighbours or samples), and the batch's first query id to another
+    that the estimator reads, so every replay draws the sample streams the
+    direct call with that qid_offset would draw (with sample_mode=2, the permuted windows of Algorithm 2 that
     follow on from the previous batch's).  With neighbors=True the replay
     also returns the neighbour ids (X_1) that a backward pass needs.
     """
@@ -421,9 +426,12 @@ class GraphedQuery:
         dev = index.device
         self.Y = torch.zeros((self.capacity, index.d), dtype=torch.float32, device=dev)
         self.qid = torch.zeros(1, dtype=torch.int64, device=dev)
+        # no active row until a batch arrives: the warm-up call below only loads
+        # the kernels (its rows would be zero vectors)
+        self.active = torch.zeros(1, dtype=torch.int64, device=dev)
         index.reserve(self.capacity, k, m, nprobe)
         args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision,
-                    sample_mode=sample_mode, dev_qid=self.qid,
+                    sample_mode=sample_mode, dev_qid=self.qid, dev_active=self.active,
                     return_neighbors=self.neighbors)
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
@@ -443,6 +451,7 @@ class GraphedQuery:
             raise ValueError(f"batch of {nb} exceeds the captured capacity {self.capacity}")
         self.Y[:nb].copy_(Yb, non_blocking=True)
         self.qid.fill_(int(qid_offset))
+        self.active.fill_(nb)
         self.graph.replay()
         return (self.out[:nb], self.nbr[:nb]) if self.neighbors else self.out[:nb]
 

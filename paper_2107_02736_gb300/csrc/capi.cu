@@ -72,7 +72,7 @@ cudaStream_t stream_of(const kde_opts* o) {
                                                 : cudaStream_t(0);
 }
 
-const kde_opts kDefaultOpts = {0, 0, 0, 0, 0, nullptr, nullptr};
+const kde_opts kDefaultOpts = {0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
 
 // Bump layout over the index's scratch buffer; with base == nullptr it only
 // counts bytes, so the same carve code sizes and places the buffers.
@@ -323,7 +323,7 @@ kde_status stage_queries(kde_index* ix, const float* Y, int64_t nq, bool host, C
 // the sorted list with distances; the selection then skips the full sort.
 kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int P, int precision,
                       int32_t* nbr, float* nd2, float* s1, cudaStream_t st,
-                      bool ids_only = false) {
+                      bool ids_only = false, const int64_t* active = nullptr) {
   const SearchBufs& s = cb.search;
   const int L = ix->nlist;
   for (int64_t q0 = 0; q0 < nq; q0 += s.qc) {
@@ -335,7 +335,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       StageTimer t(ix, ST_COARSE, st, 2);
       launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, st);
       launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
-                           s.probes, s.probe_d2, st);
+                           s.probes, s.probe_d2, active, q0, st);
     }
     // the BF16 tensor-core scan groups up to BN queries per list; the FP32
     // SIMT scan groups 64
@@ -368,6 +368,8 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     StageTimer tsel(ix, ST_SELECT, st, 1);
     SelectArgs a;
     a.order = s.order;
+    a.active = active;
+    a.q0 = q0;
     a.cand = s.cand;
     a.q_off = s.q_off;
     a.q_count = s.q_count;
@@ -423,6 +425,7 @@ SampleArgs sample_args(kde_index* ix, const CallBufs& cb, int64_t nq, const int3
   a.seed = seed;
   a.qid_offset = o->query_id_offset;
   a.dev_qid = reinterpret_cast<const uint64_t*>(o->dev_query_id_offset);
+  a.active = nullptr;
   a.mode = o->sample_mode;
   a.XP = ix->XP;
   a.wperm = ix->wperm;
@@ -889,8 +892,11 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   TRY(prepare_call(ix, c, cb));
   TRY(stage_queries(ix, Y, nq, host, cb, st));
   int32_t* nb = (k > 0) ? ((host || nbr == nullptr) ? cb.nbr : nbr) : nullptr;
-  if (k > 0) TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st, true));
+  const int64_t* active = reinterpret_cast<const int64_t*>(o->dev_active_rows);
+  if (k > 0)
+    TRY(run_search(ix, cb, nq, k, nprobe, o->precision, nb, nullptr, cb.s1, st, true, active));
   SampleArgs a = sample_args(ix, cb, nq, nb, k, m, seed, o);
+  a.active = active;
   a.s1_in = k > 0 ? cb.s1 : nullptr;
   a.nbr_distinct = 1;
   a.out = host ? cb.out : out;

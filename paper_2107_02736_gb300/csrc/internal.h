@@ -189,9 +189,10 @@ bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_
 
 // ---- select.cu -------------------------------------------------------------
 void launch_query_norms(const float* Y, int64_t nq, int dp, float* out, cudaStream_t s);
+// active / q0: rows q0 + q >= *active (when active is not NULL) get no probes
 void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
                           const float* C, int nprobe, int margin, int32_t* probes,
-                          float* probe_d2, cudaStream_t s);
+                          float* probe_d2, const int64_t* active, int64_t q0, cudaStream_t s);
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,
                        int64_t* q_count, int64_t* q_real, int64_t* q_off, int64_t* seg_off,
                        int64_t* list_cnt,
@@ -202,6 +203,8 @@ void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_
                          int64_t* ord_off, int64_t* ord_fill, int32_t* order, cudaStream_t s);
 struct SelectArgs {
   const int32_t* order;      // [nq] processing order (nullable: row order)
+  const int64_t* active;     // device row count A (nullable): rows q0 + q >= A are skipped
+  int64_t q0;                // row of this chunk's first query within the call
   const float* cand;
   const int64_t* q_off;
   const int64_t* q_count;    // padded candidate slots per query (+inf in the padding)
@@ -252,6 +255,7 @@ struct SampleArgs {
   uint64_t seed;
   uint64_t qid_offset;
   const uint64_t* dev_qid;   // optional device-side addition to qid_offset
+  const int64_t* active;     // device row count A (nullable): rows q >= A are skipped
   int mode;                  // 0 reject, 1 drop, 2 permuted window (Algorithm 2)
   const float* XP;           // mode 2: the dataset in pi order
   const int32_t* wperm;      // mode 2: pi

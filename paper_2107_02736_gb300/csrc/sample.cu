@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   float* ys = reinterpret_cast<float*>(ys4);
   const int64_t q = a.mode == 2 ? window_order(blockIdx.x, a.nq, a.win_period) : blockIdx.x;
   const int tid = threadIdx.x;
+  if (a.active != nullptr && q >= *a.active) return;  // inactive row: no output
   const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;

@@ -430,11 +430,20 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
                                                        int dp, const float* __restrict__ C,
                                                        int nprobe, int kprime,
                                                        int32_t* __restrict__ probes,
-                                                       float* __restrict__ probe_d2) {
+                                                       float* __restrict__ probe_d2,
+                                                       const int64_t* __restrict__ active,
+                                                       int64_t q0) {
   extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
   ProbeSmem& sm = *reinterpret_cast<ProbeSmem*>(sel_dyn4);
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (active != nullptr && q0 + q >= *active) {  // an inactive row probes no list
+    for (int j = threadIdx.x; j < nprobe; j += kNT) {
+      probes[q * nprobe + j] = -1;
+      probe_d2[q * nprobe + j] = __int_as_float(0x7f800000);
+    }
+    return;
+  }
   const float* vals = D + q * L;
   const int K = min(kprime, L);
   if (K < L) {
@@ -573,6 +582,17 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   __shared__ float s_red[kNW];
   const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
+    for (int j = tid; j < a.k; j += kNT) {
+      a.nbr[q * a.k + j] = -1;
+      if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
+    }
+    if (tid == 0) {
+      if (a.s1) a.s1[q] = 0.f;
+      if (a.kcount) a.kcount[q] = 0;
+    }
+    return;
+  }
   const int64_t cnt = a.q_count[q];      // slots, with +inf in the padding
   const int64_t cnt_real = a.q_real[q];  // candidates
   const float* vals = a.cand + a.q_off[q];
@@ -909,13 +929,14 @@ void launch_exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, c
 
 void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int d, int dp,
                           const float* C, int nprobe, int margin, int32_t* probes,
-                          float* probe_d2, cudaStream_t s) {
+                          float* probe_d2, const int64_t* active, int64_t q0, cudaStream_t s) {
   if (nq <= 0) return;
   int kprime = nprobe + margin;
   if (kprime > kProbeCap) kprime = kProbeCap;
   set_dynamic_smem(reinterpret_cast<const void*>(&k_select_probes), sizeof(ProbeSmem));
-  k_select_probes<<<(unsigned)nq, kNT, sizeof(ProbeSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe, kprime, probes,
-                                               probe_d2);
+  k_select_probes<<<(unsigned)nq, kNT, sizeof(ProbeSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe,
+                                                              kprime, probes, probe_d2, active,
+                                                              q0);
 }
 
 void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* list_off, int L,

@@ -183,6 +183,7 @@ def test_unit_powerlaw_full_size_batched_form(pkg):
         start += nb
     classes = {1 << max(4, int(nb - 1).bit_length()) for nb in sizes}
     assert len(checked) == 7 and set(server.graphs) == classes
+    assert index.margin_failures() == 0  # the capacity's padding rows are inactive
     qs = np.sort(np.concatenate([[0, Y.shape[0] - 1],
                                  np.random.default_rng(5).choice(Y.shape[0], 14,
                                                                  replace=False)]))

@@ -211,6 +211,31 @@ def test_graph_replays_serve_uneven_batches(pkg):
     assert len(server.graphs) >= 3
 
 
+def test_device_active_rows(pkg):
+    """A device-side row count A serves rows below A exactly as a call on
+    those rows alone; rows past it get no neighbours (-1) and, through a
+    served graph of a larger capacity, add no selection overflow."""
+    X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=700, n_centres=100)
+    index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=64, seed=5)
+    Yd = _dev(Y)
+    for A in (700, 413, 1, 0):
+        act = torch.tensor([A], dtype=torch.int64, device="cuda")
+        out, nbr = index.query(Yd, 100, 1000, nprobe=4, seed=11, precision=1,
+                               return_neighbors=True, dev_active=act)
+        assert torch.all(nbr[A:] == -1)
+        if A:
+            want, wnbr = index.query(Yd[:A], 100, 1000, nprobe=4, seed=11, precision=1,
+                                     return_neighbors=True)
+            assert torch.equal(out[:A], want)
+            assert torch.equal(torch.sort(nbr[:A], 1)[0], torch.sort(wnbr, 1)[0])
+    index.sync()
+    # zero rows in a 1024-row capacity: padding rows used to be zero vectors
+    server = pkg.BatchServer(index, 100, 1000, nprobe=4, seed=11, precision=1, max_batch=1024)
+    got = server(Yd[:513]).clone()
+    assert torch.equal(got, index.query(Yd[:513], 100, 1000, nprobe=4, seed=11, precision=1))
+    assert index.margin_failures() == 0
+
+
 def test_powerlaw_nn_contribution_map(pkg):
     """The Lemma's power-law construction: DEANN with the exact top k (the
     first k ids) matches the oracle draw for draw, and across 8,192 query ids
