@@ -467,6 +467,81 @@ __global__ void __launch_bounds__(kNT) k_select_probes(const float* __restrict__
   }
 }
 
+// The same selection with one warp per query, for kprime <= 32 (the usual
+// nprobe).  Pairs (approximate key, id) are totally ordered; each lane keeps
+// the four smallest of its own pairs in registers, and each of kprime rounds
+// takes the smallest lane head over the warp, so the pairs come out in order:
+// the set the block version selects.  A lane whose four are used up scans its
+// pairs again for the next four above the last it gave.  Lane j keeps the
+// j-th with its compensated FP32 distance, and a rank count orders them by
+// (distance, id).
+__global__ void __launch_bounds__(kNT) k_select_probes_warp(
+    const float* __restrict__ D, int64_t nq, int L, const float* __restrict__ Y, int d, int dp,
+    const float* __restrict__ C, int nprobe, int kprime, int32_t* __restrict__ probes,
+    float* __restrict__ probe_d2, const int64_t* __restrict__ active, int64_t q0) {
+  using u64 = unsigned long long;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * kNW + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  int K = min(kprime, L);
+  if (active != nullptr && q0 + q >= *active) K = 0;  // an inactive row probes no list
+  const float* vals = D + q * L;
+  const float* y = Y + q * dp;
+  constexpr u64 kNone = ~0ull;
+  u64 b0 = kNone, b1 = kNone, b2 = kNone, b3 = kNone;
+  // the four smallest of this lane's pairs above `floor` (pairs are stored + 1,
+  // so floor 0 is below all of them)
+  auto fill = [&](u64 floor) {
+    b0 = b1 = b2 = b3 = kNone;
+    for (int i = lane; i < L; i += 32) {
+      const u64 c = (((u64)dist_key(vals[i]) << 32) | (unsigned)i) + 1ull;
+      if (c > floor && c < b3) {
+        const u64 n3 = c < b2 ? b2 : c;
+        const u64 n2 = c < b2 ? (c < b1 ? b1 : c) : b2;
+        const u64 n1 = c < b1 ? (c < b0 ? b0 : c) : b1;
+        b0 = c < b0 ? c : b0;
+        b1 = n1;
+        b2 = n2;
+        b3 = n3;
+      }
+    }
+  };
+  if (K > 0) fill(0ull);
+  u64 mine = kNone;
+  for (int r = 0; r < K; ++r) {
+    u64 best = b0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const u64 t = __shfl_xor_sync(0xffffffffu, best, o);
+      best = t < best ? t : best;
+    }
+    if (b0 == best) {  // this lane's head (pairs are distinct): pop it
+      b0 = b1;
+      b1 = b2;
+      b2 = b3;
+      b3 = kNone;
+      if (b0 == kNone) fill(best);
+    }
+    const int c = (int)((best - 1ull) & 0xffffffffull);
+    const float d2 = precise_sq_dist<32>(C + (int64_t)c * dp, y, d, lane);
+    if (lane == r) mine = pack_key(d2, c);
+  }
+  // rank of lane j's key among the K keys (all distinct: they carry the id)
+  int rank = 0;
+  for (int j = 0; j < K; ++j) {
+    const unsigned long long t = __shfl_sync(0xffffffffu, mine, j);
+    rank += t < mine ? 1 : 0;
+  }
+  if (lane < K && rank < nprobe) {
+    probes[q * nprobe + rank] = (int32_t)(mine & 0xffffffffu);
+    probe_d2[q * nprobe + rank] = __uint_as_float((uint32_t)(mine >> 32));
+  }
+  for (int j = K + lane; j < nprobe; j += 32) {
+    probes[q * nprobe + j] = -1;
+    probe_d2[q * nprobe + j] = __int_as_float(0x7f800000);
+  }
+}
+
 // --------------------------------------------------------------------------
 // Work plan of the list-major scan.
 // --------------------------------------------------------------------------
@@ -933,6 +1008,11 @@ void launch_select_probes(const float* D, int64_t nq, int L, const float* Y, int
   if (nq <= 0) return;
   int kprime = nprobe + margin;
   if (kprime > kProbeCap) kprime = kProbeCap;
+  if (kprime <= 32) {
+    k_select_probes_warp<<<(unsigned)((nq + kNW - 1) / kNW), kNT, 0, s>>>(
+        D, nq, L, Y, d, dp, C, nprobe, kprime, probes, probe_d2, active, q0);
+    return;
+  }
   set_dynamic_smem(reinterpret_cast<const void*>(&k_select_probes), sizeof(ProbeSmem));
   k_select_probes<<<(unsigned)nq, kNT, sizeof(ProbeSmem), s>>>(D, nq, L, Y, d, dp, C, nprobe,
                                                               kprime, probes, probe_d2, active,
