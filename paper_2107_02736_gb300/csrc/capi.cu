@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "deann_gb300.h"
 #include "internal.h"
@@ -347,7 +348,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       StageTimer t(ix, ST_PLAN, st, 9);
       launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_real, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
-                        s.tile_cnt, s.tile_off, qtile, st);
+                        s.tile_cnt, s.tile_off, ix->lorder, qtile, st);
       launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
     }
     ScanPlan plan;
@@ -355,6 +356,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     plan.pair_dst = s.pair_dst;
     plan.bucket_off = s.bucket_off;
     plan.tile_off = s.tile_off;
+    plan.lorder = ix->lorder;
     plan.max_tiles = (nc * P + qtile - 1) / qtile + L;
     if (tcore) {
       StageTimer t(ix, ST_SCAN, st, 1);
@@ -697,6 +699,18 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   ix->max_list = 0;
   for (int64_t l = 0; l < L; ++l)
     ix->max_list = std::max(ix->max_list, ix->h_list_off[l + 1] - ix->h_list_off[l]);
+  {
+    // the scans take the lists longest first, so that the longest (the
+    // slowest tiles) do not start last and leave a tail
+    std::vector<int32_t> order(L);
+    for (int l = 0; l < L; ++l) order[l] = l;
+    const int64_t* lo = ix->h_list_off;
+    std::stable_sort(order.begin(), order.end(), [lo](int32_t a, int32_t b) {
+      return lo[a + 1] - lo[a] > lo[b + 1] - lo[b];
+    });
+    BTRY(dev_alloc(&ix->lorder, (size_t)L));
+    BCK(cudaMemcpy(ix->lorder, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice));
+  }
   int64_t margin = 0;
   s = collect_errors(ix, st, &margin);
   if (s == KDE_ELIMIT) s = KDE_OK;  // k-means init fell back to fixed points
@@ -718,6 +732,7 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->XLb);
   cudaFree(ix->perm);
   cudaFree(ix->assign);
+  cudaFree(ix->lorder);
   cudaFree(ix->list_off);
   cudaFree(ix->C);
   cudaFree(ix->Cn);

@@ -81,6 +81,7 @@ struct kde_index {
   float* rad = nullptr;       // [nlist] max |x - c_list| over the list
   int32_t* perm = nullptr;    // list position -> original id
   int32_t* assign = nullptr;  // original id -> list id
+  int32_t* lorder = nullptr;  // [nlist] list ids, longest list first (scan order)
   int64_t* list_off = nullptr;  // [nlist + 1] device
   int64_t* h_list_off = nullptr;  // host copy
   int64_t max_list = 0;
@@ -164,7 +165,8 @@ struct ScanPlan {
   const int32_t* pair_q;      // query of each (query, probe) pair, bucketed by list
   const int64_t* pair_dst;    // destination offset of the pair's segment in cand
   const int64_t* bucket_off;  // [L + 1] pairs of list l: [bucket_off[l], bucket_off[l+1])
-  const int64_t* tile_off;    // [L + 1] query tiles of list l
+  const int64_t* tile_off;    // [L + 1] query tiles of the i-th list of lorder
+  const int32_t* lorder;      // [L] lists in scan order, longest first
   int64_t max_tiles;          // grid bound
 };
 void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const float* XLn,
@@ -197,7 +199,8 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
                        int64_t* q_count, int64_t* q_real, int64_t* q_off, int64_t* seg_off,
                        int64_t* list_cnt,
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
-                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
+                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off,
+                       const int32_t* lorder, int qtile,
                        cudaStream_t s);
 void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_t* ord_cnt,
                          int64_t* ord_off, int64_t* ord_fill, int32_t* order, cudaStream_t s);

@@ -610,10 +610,12 @@ __global__ void k_order_fill(const int32_t* __restrict__ probes, int64_t nq, int
   order[slot] = (int32_t)q;
 }
 
+// tile_cnt in scan order: entry i counts the query tiles of list lorder[i]
 __global__ void k_plan_tiles(const int64_t* __restrict__ list_cnt, int L, int qtile,
+                             const int32_t* __restrict__ lorder,
                              int64_t* __restrict__ tile_cnt) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l < L) tile_cnt[l] = (list_cnt[l] + qtile - 1) / qtile;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) tile_cnt[i] = (list_cnt[lorder[i]] + qtile - 1) / qtile;
 }
 
 // Single-block exclusive scan; out has count + 1 entries (the last = total).
@@ -1023,8 +1025,8 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
                        int64_t* q_count, int64_t* q_real, int64_t* q_off, int64_t* seg_off,
                        int64_t* list_cnt,
                        int64_t* bucket_off, int64_t* bucket_fill, int32_t* pair_q,
-                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off, int qtile,
-                       cudaStream_t s) {
+                       int64_t* pair_dst, int64_t* tile_cnt, int64_t* tile_off,
+                       const int32_t* lorder, int qtile, cudaStream_t s) {
   cudaMemsetAsync(list_cnt, 0, sizeof(int64_t) * L, s);
   cudaMemsetAsync(bucket_fill, 0, sizeof(int64_t) * L, s);
   k_plan_segments<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(probes, nq, P, list_off, q_count,
@@ -1035,7 +1037,8 @@ void launch_plan_pairs(const int32_t* probes, int64_t nq, int P, const int64_t* 
   k_plan_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(probes, nq, P, q_off, seg_off,
                                                            bucket_off, bucket_fill, pair_q,
                                                            pair_dst);
-  k_plan_tiles<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(list_cnt, L, qtile, tile_cnt);
+  k_plan_tiles<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(list_cnt, L, qtile, lorder,
+                                                           tile_cnt);
   k_exclusive_scan<<<1, 1024, 0, s>>>(tile_cnt, L, tile_off, 1);
 }
 

@@ -51,6 +51,7 @@ struct ScanShared {
   uint32_t tmem_base;
   int abort;
   int list;
+  int pos;  // the list's place in the scan order
   int64_t dst[256];
   float yn[256];
 };
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int64_t* __restrict__ list_off, int L, int dpb, int BN,
               const int32_t* __restrict__ pair_q, const int64_t* __restrict__ pair_dst,
               const int64_t* __restrict__ bucket_off, const int64_t* __restrict__ tile_off,
-              float* __restrict__ cand, uint32_t* __restrict__ err) {
+              const int32_t* __restrict__ lorder, float* __restrict__ cand,
+              uint32_t* __restrict__ err) {
   __shared__ ScanShared sh;
   extern __shared__ uint8_t dyn_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -81,7 +83,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int mid = (lo + hi + 1) >> 1;
       if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    sh.list = lo;
+    sh.pos = lo;
+    sh.list = lorder[lo];
     sh.abort = 0;
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&sh.full[s], 1);
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   const int l = sh.list;
-  const int64_t pb = bucket_off[l] + (t - tile_off[l]) * BN;
+  const int64_t pb = bucket_off[l] + (t - tile_off[sh.pos]) * BN;
   const int64_t left_pairs = bucket_off[l + 1] - pb;
   const int npairs = left_pairs < (int64_t)BN ? (int)left_pairs : BN;
   const int64_t xb = list_off[l];
@@ -301,7 +304,7 @@ bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, c
   k_scan_tc<<<(unsigned)plan.max_tiles, kThreads, smem, s>>>(
       *reinterpret_cast<const CUtensorMap*>(tmap),
       Yp, C, dp, XLcn, list_off, L, dpb, BN, plan.pair_q,
-      plan.pair_dst, plan.bucket_off, plan.tile_off, cand, err);
+      plan.pair_dst, plan.bucket_off, plan.tile_off, plan.lorder, cand, err);
   return true;
 }
 

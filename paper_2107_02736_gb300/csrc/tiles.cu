@@ -294,24 +294,25 @@ __global__ void __launch_bounds__(256) k_scan_simt(
     const float* __restrict__ XLn, const int64_t* __restrict__ list_off, int L, int dp,
     const int32_t* __restrict__ pair_q, const int64_t* __restrict__ pair_dst,
     const int64_t* __restrict__ bucket_off, const int64_t* __restrict__ tile_off,
-    float* __restrict__ cand) {
+    const int32_t* __restrict__ lorder, float* __restrict__ cand) {
   __shared__ TileSmem sm;
-  __shared__ int s_list;
+  __shared__ int s_list, s_pos;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t t = blockIdx.x;
   if (t >= tile_off[L]) return;
   if (tid == 0) {
-    int lo = 0, hi = L - 1;  // last l with tile_off[l] <= t
+    int lo = 0, hi = L - 1;  // last place i in the scan order with tile_off[i] <= t
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    s_list = lo;
+    s_pos = lo;
+    s_list = lorder[lo];
   }
   __syncthreads();
   const int l = s_list;
-  const int64_t pb = bucket_off[l] + (t - tile_off[l]) * kTile;
+  const int64_t pb = bucket_off[l] + (t - tile_off[s_pos]) * kTile;
   const int64_t pe = min(bucket_off[l + 1], pb + kTile);
   const int64_t xb = list_off[l], xe = list_off[l + 1];
   const float* aptr[2];
@@ -402,7 +403,8 @@ void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const fl
   if (plan.max_tiles <= 0) return;
   k_scan_simt<<<(unsigned)plan.max_tiles, 256, 0, s>>>(Y, Yn, XL, XLn, list_off, L, dp,
                                                        plan.pair_q, plan.pair_dst,
-                                                       plan.bucket_off, plan.tile_off, cand);
+                                                       plan.bucket_off, plan.tile_off,
+                                                       plan.lorder, cand);
 }
 
 }  // namespace deann
