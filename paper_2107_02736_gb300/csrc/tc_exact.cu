@@ -21,7 +21,8 @@
 // Roles: warp 0 lane 0 streams (3 query parts + 3 point parts) x 64 dims per
 // stage by TMA (128-byte swizzle, 2 stages of 96 KiB); warp 1 lane 0 issues
 // tcgen05.mma (M = 128 queries, N = 128 points, K = 16) into a double-buffered
-// TMEM accumulator; warps 2-5 (one TMEM lane = one query each) form D^2,
+// TMEM accumulator; warps 2-17 (one TMEM lane = one query each; four warps
+// per 32-lane quadrant, each on a quarter of the tile's points) form D^2,
 // apply the kernel and sum.
 #include <cuda_bf16.h>
 
@@ -39,7 +40,8 @@ constexpr int kParts = 3;
 constexpr int kPartBytes = 128 * 128;         // 128 rows x 128 bytes
 constexpr int kStageBytes = 2 * kParts * kPartBytes;  // A parts then B parts
 constexpr int kStages = 2;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 16;                 // a multiple of 4 (the TMEM lane quadrants)
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct ExactShared {
   uint64_t full[kStages];
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sh.tfull[b], 1);
-      tc::mbar_init(&sh.tempty[b], 4);
+      tc::mbar_init(&sh.tempty[b], kEpiWarps);
     }
     tc::mbar_init(&sh.drain, 1);
     tc::fence_mbar_init();
@@ -161,6 +163,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     const int lg = (warp & 3) * 32;
+    // the quadrant's warps take equal runs of the tile's points
+    constexpr int kRun = kPN / (kEpiWarps / 4);
+    const int cbeg = ((warp - 2) >> 2) * kRun;
     const int64_t q = q0 + lg + lane;
     const bool qvalid = q < nq;
     const float ynq = qvalid ? yn[q] : 0.f;
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t xrow = x_begin + (int64_t)t * kPN;
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * 2 * kPN);
       float part = 0.f;
-      for (int c0 = 0; c0 < kPN; c0 += 16) {
+      for (int c0 = cbeg; c0 < cbeg + kRun; c0 += 16) {
         uint32_t v[16];
         uint32_t w[16];
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
