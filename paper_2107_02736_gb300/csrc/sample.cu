@@ -33,8 +33,10 @@ constexpr int kNW = kNT / 32;
 constexpr int kChunk = 2048;   // samples staged per gather round
 constexpr int kUnroll = 8;     // rows in flight per lane group
 
+constexpr int kFiltWords = 1024;  // membership filter: 32,768 bits
 struct EstSmem {
   int nb[kMaxK];               // sorted distinct neighbour ids
+  uint32_t filt[kFiltWords];   // bit (id mod 32768) set for every id in nb
   int S[kChunk];
   int warp_cnt[kNW];
   float red[kNW];
@@ -51,6 +53,15 @@ __device__ __forceinline__ bool is_member(const int* nb, int kk, int64_t id) {
     if (nb[mid] < id) lo = mid + 1; else hi = mid;
   }
   return lo < kk && nb[lo] == id;
+}
+
+// The same test, with the filter first: a clear bit rules the id out at the
+// cost of one shared load, a set bit (a member, or another id with the same
+// residue) falls back to the search.
+__device__ __forceinline__ bool is_member_f(const EstSmem& sm, int kk, int64_t id) {
+  const uint32_t w = sm.filt[(id >> 5) & (kFiltWords - 1)];
+  if (((w >> (id & 31)) & 1u) == 0u) return false;
+  return is_member(sm.nb, kk, id);
 }
 
 // Ascending bitonic sort of v[0..P2) (P2 a power of two) by the whole CTA;
@@ -113,6 +124,12 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
     __syncthreads();
   }
   if (tid == 0) sm.kk = base;
+  for (int i = tid; i < kFiltWords; i += kNT) sm.filt[i] = 0u;
+  __syncthreads();
+  for (int i = tid; i < base; i += kNT) {
+    const int id = sm.nb[i];
+    atomicOr(&sm.filt[(id >> 5) & (kFiltWords - 1)], 1u << (id & 31));
+  }
   __syncthreads();
 }
 
@@ -136,7 +153,7 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
     int64_t id = 0;
     if (tt < cap) {
       id = draw_index(seed, qid, (uint32_t)tt, 0u, n);
-      acc = (mode == 1) || !is_member(smc.nb, smc.kk, id);
+      acc = (mode == 1) || !is_member_f(smc, smc.kk, id);
     }
     const unsigned ma = __ballot_sync(0xffffffffu, acc);
     if (lane == 0) sm.warp_cnt[warp] = __popc(ma);
@@ -184,7 +201,7 @@ __device__ void window_chunk(const int32_t* __restrict__ wperm, int64_t n, int64
       if (jj >= n) jj -= n;
       j = (int)jj;
       const int32_t id = wperm[j];
-      keep = !is_member(sm.nb, sm.kk, id);
+      keep = !is_member_f(sm, sm.kk, id);
       if (srow) srow[t] = keep ? id : -1;
     }
     const unsigned mk = __ballot_sync(0xffffffffu, keep);
