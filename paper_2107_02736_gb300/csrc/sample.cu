@@ -136,7 +136,10 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
 // Fills sm.S[0..sm.cnt) with the next accepted sample indices (at most
 // `room`), starting at draw t0; sets sm.tnext to the first unused draw.
 // mode 0 rejects members of X_1; mode 1 accepts every draw.  Returns false
-// when the draw cap is reached.
+// when the draw cap is reached.  A round covers kNT * kDraws consecutive
+// draws, thread i taking kDraws of them in a row, so the accepted draws are
+// ranked in draw order by a block prefix sum of the per-thread counts.
+constexpr int kDraws = 4;
 __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, int64_t cap,
                            int room, int mode, const EstSmem& smc, EstSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -148,32 +151,48 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
       ok = false;
       break;
     }
-    const int64_t tt = t + tid;
-    bool acc = false;
-    int64_t id = 0;
-    if (tt < cap) {
-      id = draw_index(seed, qid, (uint32_t)tt, 0u, n);
-      acc = (mode == 1) || !is_member_f(smc, smc.kk, id);
+    const int64_t tb = t + (int64_t)tid * kDraws;
+    int ids[kDraws];
+    unsigned accm = 0u;
+#pragma unroll
+    for (int r = 0; r < kDraws; ++r) {
+      ids[r] = 0;
+      if (tb + r < cap) {
+        ids[r] = (int)draw_index(seed, qid, (uint32_t)(tb + r), 0u, n);
+        if (mode == 1 || !is_member_f(smc, smc.kk, ids[r])) accm |= 1u << r;
+      }
     }
-    const unsigned ma = __ballot_sync(0xffffffffu, acc);
-    if (lane == 0) sm.warp_cnt[warp] = __popc(ma);
+    const int mine = __popc(accm);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) sm.warp_cnt[warp] = incl;
     __syncthreads();
     int off = 0, tot = 0;
     for (int w = 0; w < kNW; ++w) {
       if (w < warp) off += sm.warp_cnt[w];
       tot += sm.warp_cnt[w];
     }
-    const int rank = off + __popc(ma & ((1u << lane) - 1u));
+    int rank = off + incl - mine;
     const int left = room - filled;
-    if (acc && rank < left) {
-      sm.S[filled + rank] = (int)id;
-      if (rank == left - 1) sm.tnext = tt + 1;
+#pragma unroll
+    for (int r = 0; r < kDraws; ++r) {
+      if ((accm >> r) & 1u) {
+        if (rank < left) {
+          sm.S[filled + rank] = ids[r];
+          if (rank == left - 1) sm.tnext = tb + r + 1;
+        }
+        ++rank;
+      }
     }
     if (tot >= left) {
       filled = room;
     } else {
       filled += tot;
-      t += kNT;
+      t += (int64_t)kNT * kDraws;
       if (t > cap) t = cap;
       if (tid == 0) sm.tnext = t;
     }
