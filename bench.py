@@ -20,6 +20,7 @@ oracle on the host cores instead (a bounded query sample per step).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import math
@@ -48,7 +49,7 @@ PRECISIONS = {"fp32": 0, "bf16": 1}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0, help="shrink n (debug only)")
@@ -105,9 +106,13 @@ def rel_err(est, exact):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons during a region.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Samples come every 20 ms with their timestamps; start() returns once the
+    first has arrived, and stop() keeps those taken between mark_begin() and
+    mark_end() (all of them when the region is shorter than one interval)."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -115,6 +120,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -122,10 +128,29 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+            return
+        deadline = time.time() + 3.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+
+    def mark_begin(self):
+        self.t_begin = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
@@ -138,18 +163,23 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [t.strip() for t in line.split(",")]
-            if len(parts) >= 8:
+            if len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sel = []
+        if self.t_begin is not None and self.t_end is not None:
+            sel = [r for r in rows if self.t_begin <= (self._stamp(r[0]) or 0.0) <= self.t_end]
+        n_all = len(rows)
+        rows = [r[1:] for r in (sel or rows)]
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "samples_in_region": len(sel), "samples_total": n_all}
 
 
 def load_peaks():
@@ -905,11 +935,13 @@ def main():
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")  # lets a profiler capture just this region
+    clocks.mark_begin()
     ev0.record()
     for s in range(args.steps):
         outs.append(index.query(Yd, k, m, nprobe=P, seed=s, precision=prec))
     ev1.record()
     torch.cuda.synchronize()
+    clocks.mark_end()
     torch.cuda.nvtx.range_pop()
     ms_total = ev0.elapsed_time(ev1)
     clk = clocks.stop()
