@@ -8,8 +8,9 @@
 // One CTA = one (list, group of up to BN probing queries).  Roles:
 //   warp 0 (one lane): TMA producer, streams 128-point x 64-dim BF16 tiles of
 //                      the list (128-byte swizzle) through a 4-stage ring;
-//   warp 1 (one lane): MMA issuer, tcgen05.mma M=128 (points) x N=BN
-//                      (queries) x K=16 into a double-buffered TMEM
+//   warp 1 (one lane): MMA issuer, tcgen05.mma M=128 (points) x N (the
+//                      CTA's queries rounded up to 16, at most BN) x K=16
+//                      into a double-buffered TMEM
 //                      accumulator; warp 1 also owns the TMEM allocation;
 //   warps 2-9        : epilogue, one TMEM lane (= one list point) per thread:
 //                      D^2 = |x|^2 + |y|^2 - 2 acc, clamped at 0, written to
@@ -102,6 +103,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t pb = bucket_off[l] + (t - tile_off[sh.pos]) * BN;
   const int64_t left_pairs = bucket_off[l + 1] - pb;
   const int npairs = left_pairs < (int64_t)BN ? (int)left_pairs : BN;
+  // the MMA's N: this CTA's queries rounded up to a multiple of 16 (rows past
+  // npairs are zero and their columns are never read)
+  const int nN = (npairs + 15) & ~15;
   const int64_t xb = list_off[l];
   const int64_t len = list_off[l + 1] - xb;
   const int ntiles = (int)((len + kBM - 1) / kBM);
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // row r of block kb at B + kb*BN*128 + r*128, 16-byte chunk c stored at
   // chunk position c ^ (r & 7) (the 128-byte swizzle)
   const float* cl = C + (int64_t)l * dp;
-  const int chunks = BN * KB * 8;
+  const int chunks = nN * KB * 8;
   for (int i = tid; i < chunks; i += kThreads) {
     const int r = i / (KB * 8);
     const int rem = i - r * (KB * 8);
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         make_uint4(w[0], w[1], w[2], w[3]);
   }
   // |y~|^2 in FP32 and the candidate destinations, one warp per query row
-  for (int r = warp; r < BN; r += kThreads / 32) {
+  for (int r = warp; r < nN; r += kThreads / 32) {
     float s = 0.f;
     if (r < npairs) {
       const float* yq = Yp + (int64_t)pair_q[pb + r] * dp;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = tc::make_idesc(kBM, BN, 1u);
+      const uint32_t idesc = tc::make_idesc(kBM, nN, 1u);
       int it = 0;
       bool ok = true;
       for (int tt = 0; tt < ntiles && ok; ++tt) {
