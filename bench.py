@@ -1008,6 +1008,14 @@ def main():
         cpu = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": f"first {done} of the {nq} test queries (IVF search from the "
                          f"exported index + DEANN, FP64), {spent:.1f} s"}
+        # one thread, for comparison with the paper's single-core timings
+        import oracle
+        oracle.set_num_threads(1)
+        qps1, _, done1, spent1 = oracle_sample_rate(X, Y, C.numpy(), assign.numpy(), args.kernel,
+                                                    h, k, m, P, min(4.0, args.cpu_budget))
+        oracle.set_num_threads(cores)
+        cpu["single_thread"] = {"value": qps1, "unit": "queries/s", "cores": 1,
+                                "sample": f"first {done1} test queries, {spent1:.1f} s"}
 
     line = {
         "metric": "kde_queries_per_s_at_1e-2_mean_rel_err", "value": value, "unit": "queries/s",
