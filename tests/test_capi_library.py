@@ -4,6 +4,8 @@ before touching the device."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -81,3 +83,29 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pkg._build_mod, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not found"):
         pkg.load_library()
+
+
+@pytest.mark.parametrize("cname,pyname", [("kde_opts", "_Opts"), ("kde_profile", "_Profile")])
+def test_structs_match_binding(tmp_path, cname, pyname):
+    """The binding's ctypes mirror of a header struct has its fields, in order,
+    at the same offsets and with the same size (compiled against the header)."""
+    import paper_2107_02736_gb300 as pkg
+    mirror = getattr(pkg, pyname)
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{(.*?)\} " + cname + ";", text, flags=re.S).group(1)
+    fields = re.findall(r"(\w+)\s*(?:\[\w+\])?\s*;", body)
+    assert [f[0] for f in mirror._fields_] == fields
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "deann_gb300.h"\n'
+                   f"int main(void) {{ printf(\"%zu\", sizeof({cname}));"
+                   + "".join(f' printf(" %zu", offsetof({cname}, {f}));' for f in fields)
+                   + " return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(mirror)] + [getattr(mirror, f).offset for f in fields]
+    assert got == want
