@@ -148,7 +148,7 @@ kde_status kde_index_info(const kde_index* index, int64_t* n, int32_t* d, int32_
  * of each point, in the original point order).  Either may be NULL. */
 kde_status kde_export_ivf(kde_index* index, float* centroids, int32_t* assign);
 
-/* kde_search -- the ANN subroutine of Algorithm 1, line 2: the k nearest
+/* kde_search -- the ANN subroutine of Algorithm 1: the k nearest
  * points (Euclidean) among the lists of the nprobe nearest centroids.
  *   Y      nq x d queries; nq >= 0.
  *   k      1 <= k <= 2048; 1 <= nprobe <= min(nlist, 256).
@@ -173,7 +173,7 @@ kde_status kde_query(kde_index* index, const float* Y, int64_t nq, int32_t k, in
                      int32_t nprobe, uint64_t seed, float* out, int32_t* nbr,
                      const kde_opts* opts);
 
-/* kde_query_with_neighbors -- Algorithm 1 lines 3-7 with a caller-supplied
+/* kde_query_with_neighbors -- the estimate of Algorithm 1 with a caller-supplied
  * neighbour set per query (nq x k ids; negative entries are padding,
  * duplicates count once; an id >= n is an error).  Same estimate as
  * kde_query. */

@@ -87,7 +87,7 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 }
 
 /* Draw number t of query qid's stream: the uniform index in [0, n) that the
- * estimator's random sample uses (Algorithm 1, line 5; Lemma RS samples with
+ * estimator's random sample uses (Algorithm 1; Lemma RS samples with
  * repetition).  key = (lo32(seed), hi32(seed)); counter = (t, lo32(qid),
  * hi32(qid), stream).  u = (r1 << 32) | r0 and index = floor(u * n / 2^64),
  * the exact high word of the 128-bit product. */
@@ -338,7 +338,7 @@ static int in_set(const int64_t* set, int kk, int64_t id) {
   return 0;
 }
 
-/* The sample S of Algorithm 1, line 5, for one query: the first m draws of
+/* The sample S of Algorithm 1 for one query: the first m draws of
  * the query's Philox stream (stream 0) that are not in X_1; draws in X_1 are
  * rejected, so S is uniform on X \ X_1 with repetition (Lemma RS).  Returns
  * the number of draws used, or -1 when the draw cap 64 m + 4096 is hit. */

@@ -1,4 +1,4 @@
-// The DEANN estimator's sampling half (Algorithm 1, lines 4-7) and random
+// The DEANN estimator's sampling half (Algorithm 1) and random
 // sampling (Lemma RS), plus the adjoint of both.
 //
 // One CTA of 256 threads serves one query:

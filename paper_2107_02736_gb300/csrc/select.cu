@@ -18,7 +18,7 @@
 //    candidates inside the FP32 error band of the k-th are re-ranked with
 //    compensated arithmetic.  Returned: the k neighbours (sorted by (distance,
 //    id), or as a set for the query path) and the exact neighbour
-//    contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1, line 4).
+//    contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1).
 //
 // More than kSelectCap candidates in the band cannot all be kept: the
 // kSelectCap smallest are rescored and the query is counted as uncertified in
