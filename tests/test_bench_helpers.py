@@ -1,5 +1,6 @@
 """Host helpers of bench.py: the FP8-e4m3 and BF16 roundings of the FP8 scan
-study against PyTorch's own conversions, and the roofline arithmetic."""
+study against PyTorch's own conversions, the roofline arithmetic and the
+clock record of the timed region."""
 import os
 import sys
 
@@ -80,3 +81,44 @@ def test_ncu_traffic_requires_same_schedule_and_source(tmp_path, monkeypatch):
     assert bench.ncu_traffic("select", sched) is None
     (src / "sample.cu").write_text("kernel v2")
     assert bench.ncu_traffic("estimate", sched) is None
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_of_the_timed_region(tmp_path):
+    """Only samples stamped inside [mark_begin, mark_end] are summarised; the
+    reasons are those seen there; with none inside, every sample is used."""
+    import datetime
+    base = datetime.datetime(2026, 12, 4, 2, 46, 43)
+    def line(dt_ms, sm, reasons=("Not Active",) * 4):
+        t = base + datetime.timedelta(milliseconds=dt_ms)
+        stamp = t.strftime("%Y/%m/%d %H:%M:%S.") + f"{t.microsecond // 1000:03d}"
+        return ", ".join([stamp, str(sm), "2070", "900.5", "0x0"] + list(reasons))
+    rows = [line(0, 1200, ("Active", "Not Active", "Not Active", "Not Active")),
+            line(20, 2070), line(40, 2055),
+            line(60, 2070, ("Not Active", "Not Active", "Not Active", "Active")),
+            line(80, 900)]
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clk.csv")
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    c.proc = _Done()
+    c.t_begin = (base + datetime.timedelta(milliseconds=15)).timestamp()
+    c.t_end = (base + datetime.timedelta(milliseconds=65)).timestamp()
+    got = c.stop()
+    assert got["samples_in_region"] == 3 and got["samples_total"] == 5
+    assert got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"]
+    # a region between two samples: every sample is summarised
+    c.path = str(tmp_path / "clk2.csv")
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    c.t_begin = (base + datetime.timedelta(milliseconds=5)).timestamp()
+    c.t_end = (base + datetime.timedelta(milliseconds=10)).timestamp()
+    got = c.stop()
+    assert got["samples_in_region"] == 0 and got["samples"] == 5
+    assert got["reasons"] == ["hw_slowdown", "sw_power_cap"]
