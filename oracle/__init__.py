@@ -73,6 +73,8 @@ def _load():
         lib.or_exact_grad.argtypes = [P, i64, i32, P, i64, i32, f64, P, P]
         lib.or_knn.argtypes = [P, i64, i32, P, i64, i32, P, P]
         lib.or_nearest_centroid.argtypes = [P, i64, i32, P, i32, P, P]
+        lib.or_kmeans.argtypes = [P, i64, i32, i32, u64, i32, P, P, P]
+        lib.or_kmeans.restype = i32
         lib.or_ivf_search.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, P, P, P]
         lib.or_deann.argtypes = [P, i64, i32, P, i64, i32, f64, P, i32, i32, u64, u64,
                                  i32, P, P]
@@ -180,6 +182,23 @@ def nearest_centroid(X, C):
     _load().or_nearest_centroid(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0],
                                 _ptr(a), _ptr(d2))
     return a, d2
+
+
+def kmeans(X, L, seed, iters=20):
+    """The inverted file's k-means (Philox-stream-1 initial points, `iters`
+    Lloyd iterations with farthest-point reseeding, final assignment).
+    Returns (centroids float32 L x d, assignment int32, mean squared distance
+    of each assignment, status: OK, or ELIMIT when the initial draws ran out)."""
+    X = _f32(X)
+    n, d = X.shape
+    C = np.zeros((L, d), dtype=np.float32)
+    a = np.zeros(n, dtype=np.int32)
+    obj = np.zeros(iters + 1, dtype=np.float64)
+    st = _load().or_kmeans(_ptr(X), n, d, int(L), int(seed) & (2**64 - 1), int(iters), _ptr(C),
+                           _ptr(a), _ptr(obj))
+    if st == EINVAL:
+        raise OracleError("kmeans: invalid arguments")
+    return C, a, obj, st
 
 
 def ivf_search(X, C, assign, Y, nprobe, k):

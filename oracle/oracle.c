@@ -16,8 +16,9 @@
  * over queries only (OpenMP when the compiler offers it); every query's
  * arithmetic is sequential, so the result does not depend on the thread count.
  *
- * Pinned by tests/test_oracle_*.py; the one part with no pin is called out in
- * its own comment ("parity unpinned").
+ * Every function is pinned by tests/test_oracle_pins.py against values and
+ * properties fixed outside this file (published known answers, closed forms,
+ * library routines, brute force, invariants).
  */
 #include <math.h>
 #include <stdint.h>
@@ -260,6 +261,83 @@ void or_nearest_centroid(const float* X, int64_t n, int d, const float* C,
     assign[i] = arg;
     if (d2) d2[i] = best;
   }
+}
+
+/* k-means for the inverted file.  Section 4 builds the IVF index with FAISS's
+ * k-means and gives no details; this is the reading taken for them:
+ *  - initial centroids: the first L distinct points drawn from Philox stream 1
+ *    of `seed` (query id 0, draws t = 0, 1, 2, ...; a point already chosen is
+ *    skipped; after 64 L + 4096 draws centroid c falls back to point c mod n,
+ *    and the function returns OR_ELIMIT);
+ *  - `iters` Lloyd iterations, each (i) assigning every point to its nearest
+ *    centroid (ties to the lower id), (ii) moving every centroid with points
+ *    to their mean (summed in increasing point index), stored as float32 as
+ *    the index stores it, and (iii) giving each empty list, in increasing
+ *    list order, the point farthest from its centroid of step (i) (ties to the
+ *    lower index; a point is given once);
+ *  - a final assignment.
+ * obj (nullable, iters + 1 entries) receives the mean squared distance of
+ * each assignment. */
+int or_kmeans(const float* X, int64_t n, int d, int L, uint64_t seed, int iters,
+              float* C, int32_t* assign, double* obj) {
+  if (n < 1 || L < 1 || L > n || d < 1 || iters < 0) return OR_EINVAL;
+  int status = OR_OK;
+  char* taken = (char*)calloc((size_t)n, 1);
+  uint32_t t = 0;
+  const uint32_t cap = 64u * (uint32_t)L + 4096u;
+  for (int c = 0; c < L; ++c) {
+    int64_t pick = -1;
+    while (pick < 0) {
+      if (t >= cap) {
+        pick = c % n;
+        status = OR_ELIMIT;
+        break;
+      }
+      const int64_t id = or_draw_index(seed, 0, t++, 1u, n);
+      if (!taken[id]) {
+        taken[id] = 1;
+        pick = id;
+      }
+    }
+    memcpy(C + (int64_t)c * d, X + pick * (int64_t)d, sizeof(float) * (size_t)d);
+  }
+  double* d2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* sum = (double*)malloc(sizeof(double) * (size_t)d);
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
+  for (int it = 0; it <= iters; ++it) {
+    or_nearest_centroid(X, n, d, C, L, assign, d2);
+    if (obj) {
+      double tot = 0.0;
+      for (int64_t i = 0; i < n; ++i) tot += d2[i];
+      obj[it] = tot / (double)n;
+    }
+    if (it == iters) break;
+    for (int c = 0; c < L; ++c) cnt[c] = 0;
+    for (int64_t i = 0; i < n; ++i) ++cnt[assign[i]];
+    for (int c = 0; c < L; ++c) {
+      if (cnt[c] == 0) continue;
+      for (int j = 0; j < d; ++j) sum[j] = 0.0;
+      for (int64_t i = 0; i < n; ++i)
+        if (assign[i] == c)
+          for (int j = 0; j < d; ++j) sum[j] += (double)X[i * (int64_t)d + j];
+      for (int j = 0; j < d; ++j) C[(int64_t)c * d + j] = (float)(sum[j] / (double)cnt[c]);
+    }
+    memset(taken, 0, (size_t)n);
+    for (int c = 0; c < L; ++c) {
+      if (cnt[c] != 0) continue;
+      int64_t far = -1;
+      for (int64_t i = 0; i < n; ++i)
+        if (!taken[i] && (far < 0 || d2[i] > d2[far])) far = i;
+      if (far < 0) continue;
+      taken[far] = 1;
+      memcpy(C + (int64_t)c * d, X + far * (int64_t)d, sizeof(float) * (size_t)d);
+    }
+  }
+  free(cnt);
+  free(sum);
+  free(d2);
+  free(taken);
+  return status;
 }
 
 /* IVF search run from an exported index (Section 4, the FAISS inverted file:

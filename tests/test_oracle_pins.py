@@ -172,6 +172,82 @@ def test_nearest_centroid_matches_library_argmin():
     assert np.array_equal(a, np.argmin(_cdist2(X, C), axis=1))
 
 
+def _first_distinct_draws(seed, n, L):
+    """Initial k-means points from the Philox block itself (the known-answer
+    pinned function): draw t of stream 1, query id 0, index floor(u n / 2^64)."""
+    ids, seen, t = [], set(), 0
+    while len(ids) < L:
+        r = oracle.philox4x32_10([t, 0, 0, 1], [seed & 0xffffffff, seed >> 32])
+        u = (int(r[1]) << 32) | int(r[0])
+        i = (u * n) >> 64
+        t += 1
+        if i not in seen:
+            seen.add(i)
+            ids.append(i)
+    return np.array(ids)
+
+
+def test_kmeans_initial_points_are_the_first_distinct_draws():
+    X = np.random.default_rng(30).standard_normal((97, 3)).astype(np.float32)
+    for seed, L in ((1, 7), (2 ** 40 + 5, 30), (9, 97)):
+        C0, _, _, st = oracle.kmeans(X, L, seed, iters=0)
+        assert st == oracle.OK
+        assert np.array_equal(C0, X[_first_distinct_draws(seed, 97, L)])
+
+
+@pytest.mark.parametrize("L", [6, 12])
+def test_kmeans_matches_sklearn_lloyd(L):
+    """From the same initial centroids, the iterations are Lloyd's algorithm:
+    scikit-learn's KMeans (algorithm="lloyd", one run, the same number of
+    iterations) ends with the same labels and centroids."""
+    sklearn_cluster = pytest.importorskip("sklearn.cluster")
+    rng = np.random.default_rng(31)
+    centres = rng.standard_normal((6, 8)) * 5.0
+    X = (centres[rng.integers(0, 6, 3000)] + rng.standard_normal((3000, 8))).astype(np.float32)
+    C0, _, _, _ = oracle.kmeans(X, L, 4, iters=0)
+    C, a, _, _ = oracle.kmeans(X, L, 4, iters=20)
+    assert np.bincount(a, minlength=L).min() > 0  # no empty list: plain Lloyd
+    km = sklearn_cluster.KMeans(n_clusters=L, init=C0.astype(np.float64), n_init=1, max_iter=20,
+                                tol=0.0, algorithm="lloyd").fit(X.astype(np.float64))
+    assert np.array_equal(km.labels_, a)
+    assert np.allclose(km.cluster_centers_, C, atol=1e-5)
+
+
+def test_kmeans_objective_never_increases():
+    rng = np.random.default_rng(32)
+    X = rng.standard_normal((4000, 10)).astype(np.float32) * rng.uniform(0.5, 3.0, 10)
+    _, _, obj, _ = oracle.kmeans(X, 40, 5, iters=25)
+    assert np.all(np.diff(obj) <= 1e-6 * obj[:-1])
+    assert obj[-1] < 0.8 * obj[0]
+
+
+def test_kmeans_one_point_per_list():
+    X = np.random.default_rng(33).standard_normal((50, 4)).astype(np.float32)
+    C, a, obj, _ = oracle.kmeans(X, 50, 6, iters=3)
+    assert obj[0] == 0.0 and obj[-1] == 0.0
+    assert np.array_equal(C[a], X) and np.unique(a).size == 50
+
+
+def test_kmeans_reseeds_an_empty_list_with_the_farthest_point():
+    """Initial points at the same place leave a list empty (its twin with the
+    lower id takes every point); the list then takes the point farthest from
+    its centroid, and no list stays empty."""
+    base = np.array([[0, 0], [10, 0], [0, 10]], dtype=np.float32)
+    X = np.repeat(base, 20, axis=0)
+    X = np.vstack([X, [[40.0, 40.0]]]).astype(np.float32)  # row 60: the outlier
+    n = X.shape[0]
+    for seed in range(200):
+        ids = _first_distinct_draws(seed, n, 4)
+        if len({tuple(X[i]) for i in ids}) == 3 and 60 not in ids:
+            break
+    else:
+        pytest.fail("no seed with a repeated initial place")
+    C, a, obj, _ = oracle.kmeans(X, 4, seed, iters=5)
+    assert np.bincount(a, minlength=4).min() > 0
+    assert np.sum(a == a[60]) == 1 and np.array_equal(C[a[60]], X[60])
+    assert obj[-1] == 0.0
+
+
 def test_ivf_full_probe_equals_brute_force():
     """nprobe = nlist scans every list: the IVF search is the exact kNN."""
     rng = np.random.default_rng(6)
