@@ -250,6 +250,28 @@ def test_ivf_build_assignment_and_search(pkg):
         assert_neighbours_match(X, Y, nbr.cpu().numpy(), want, want_d2)
 
 
+@pytest.mark.parametrize("L", [16, 64])
+def test_kmeans_build_matches_oracle(pkg, L):
+    """The IVF build's k-means against the oracle's: the same Philox initial
+    points and Lloyd iterations (GPU assignment distances in FP32, the oracle's
+    in FP64) end with the same lists and centroids, up to points whose two
+    nearest centroids are nearly equidistant."""
+    X, _, _ = workloads.mixture_iso(n=20000, d=16, nq=16)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=L, seed=3)
+    C, a = (t.numpy() for t in index.export_ivf())
+    Co, ao, _, st = oracle.kmeans(X, L, 3, iters=20)
+    assert st == oracle.OK
+    assert np.mean(a == ao) >= 0.999
+
+    def objective(C, a):
+        return np.mean(((X.astype(np.float64) - C[a].astype(np.float64)) ** 2).sum(1))
+    assert abs(objective(C, a) / objective(Co, ao) - 1.0) <= 1e-4
+    same = [l for l in range(L)
+            if np.array_equal(np.flatnonzero(a == l), np.flatnonzero(ao == l))]
+    assert len(same) >= 0.9 * L
+    assert np.allclose(C[same], Co[same], rtol=0.0, atol=1e-5)
+
+
 def test_query_end_to_end(pkg):
     X, Y, _ = workloads.mixture_iso(n=10_000, d=16, nq=200)
     index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=16, seed=1)
