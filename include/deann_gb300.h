@@ -168,7 +168,9 @@ kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, i
  *   m      >= 0 (m = 0 keeps only the neighbours' exact contribution);
  *   nprobe 1 <= nprobe <= min(nlist, 256) (ignored when k = 0).
  *   out    nq estimates (FP32).
- *   nbr    NULL, or nq x k receiving the neighbour ids that were used. */
+ *   nbr    NULL, or nq x k receiving the neighbour ids that were used.
+ * With opts.dev_active_rows only the rows below the device count are served
+ * (a CUDA graph captured at a fixed capacity serving a smaller batch). */
 kde_status kde_query(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t m,
                      int32_t nprobe, uint64_t seed, float* out, int32_t* nbr,
                      const kde_opts* opts);
