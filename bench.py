@@ -859,8 +859,9 @@ def fp8_study(args):
 def profile_case(args):
     """One batch of args.profile_case queries through each path at the DEANN
     schedule args.profile_schedule (BF16 scan, h = 12.85): DEANN, DEANNP (tiled
-    windows), and the tensor-core exact KDE; one launch each of k_scan_tc,
-    k_select_neighbors, k_estimate, k_window_tile, k_exact_tc."""
+    windows), the tensor-core exact KDE and the adjoint on the DEANN query's
+    neighbours; one launch each of k_scan_tc, k_select_neighbors, k_estimate,
+    k_window_tile, k_exact_tc, k_estimate_grad."""
     import torch
     import paper_2107_02736_gb300 as pkg
     k, m, P = (int(v) for v in args.profile_schedule.split(","))
@@ -870,13 +871,14 @@ def profile_case(args):
     index = pkg.KDEIndex(torch.from_numpy(X).to(dev), args.kernel, 12.85, nlist=1024, seed=1)
     index.prepare_permuted()
     Yd = torch.from_numpy(Y).to(dev)
-    a = index.query(Yd, k, m, nprobe=P, seed=1, precision=1)
+    a, nbr = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, return_neighbors=True)
     b = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, sample_mode=2)
     c = index.exact(Yd[:1024], path="tensor")
+    g = index.grad_with_neighbors(Yd, nbr, m, seed=1)[1]
     torch.cuda.synchronize()
     print("profile case ok", json.dumps({"k": k, "m": m, "nprobe": P, "precision": "bf16",
                                          "nq": args.profile_case}),
-          float(a.mean()), float(b.mean()), float(c.mean()))
+          float(a.mean()), float(b.mean()), float(c.mean()), float(g.abs().mean()))
 
 
 def main():
