@@ -93,6 +93,9 @@ def _load():
         lib.or_fit_bandwidth.argtypes = [P, i64, i32, P, i64, i32, f64, P, i32, i32, u64, i32,
                                          f64, P, P]
         lib.or_fit_bandwidth.restype = i32
+        lib.or_mean_shift.argtypes = [P, i64, i32, P, i32, P, P, i64, f64, i32, i32, i32, u64,
+                                      u64, i32, P]
+        lib.or_mean_shift.restype = i32
         _lib = lib
         return lib
 
@@ -261,6 +264,23 @@ def deann_grad(X, Y, kernel, h, nbr, m, seed, qid_offset=0, gout=None):
                                m, seed, qid_offset, _ptr(g), _ptr(out), _ptr(dY), _ptr(dl))
     _check(st, "deann_grad")
     return out, dY, dl
+
+
+def mean_shift(X, C, assign, Y, h, k, m, nprobe, seed, steps, qid_offset=0):
+    """Gaussian mean-shift steps y <- y + h^2 grad KDE~(y) / KDE~(y) with the
+    DEANN estimate: step s searches the exported inverted file (C, assign)
+    for X_1 (none when k = 0) and draws S with seed + s.  Returns the moved
+    queries (FP32, as the iterate is held) and the estimate at the start of
+    the last step."""
+    X, C, assign = _f32(X), _f32(C), _i32(assign)
+    Yo = np.array(_f32(Y), dtype=np.float32, copy=True, order="C")
+    nq = Yo.shape[0]
+    est = np.zeros(nq, dtype=np.float64)
+    st = _load().or_mean_shift(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0],
+                               _ptr(assign), _ptr(Yo), nq, float(h), int(k), int(m),
+                               int(nprobe), int(seed), int(qid_offset), int(steps), _ptr(est))
+    _check(st, "mean_shift")
+    return Yo, est
 
 
 def loo_exact(X, zid, kernel, h):

@@ -779,3 +779,57 @@ int or_fit_bandwidth(const float* X, int64_t n, int d, const int32_t* zid, int64
   free(dY);
   return status;
 }
+
+/* ------------------------------------------------------------------------
+ * Density-gradient flow with the DEANN estimate (Section 1 names gradient
+ * lines of densities among the uses of KDE; the paper gives no algorithm).
+ * Gaussian kernel only.  Each of `steps` steps moves every query by
+ *     y <- y + h^2 grad KDE~(y) / KDE~(y),
+ * the mean-shift step: since grad K_h(x, y) = K_h(x, y) (x - y) / h^2 for the
+ * Gaussian kernel, the new y is the estimate-weighted mean of the points of
+ * X_1 and S.  Step s takes X_1 from the IVF search of the current y (the
+ * exported centroids C and list assignment, nprobe lists, k neighbours; no
+ * search when k = 0) and draws S from the Philox stream of seed + s with query
+ * id qid_offset + q; the gradient is the pathwise derivative of
+ * or_deann_grad.  The iterate stays in FP32 between steps (a query is an FP32
+ * vector); each update is computed in FP64 and rounded once.  A query whose
+ * estimate is 0 does not move.  est (nullable) receives the estimate at the
+ * start of the last step (0 when steps = 0).
+ * ---------------------------------------------------------------------- */
+int or_mean_shift(const float* X, int64_t n, int d, const float* C, int L,
+                  const int32_t* assign, float* Y, int64_t nq, double h, int k,
+                  int m, int nprobe, uint64_t seed, uint64_t qid_offset, int steps,
+                  double* est) {
+  if (n <= 0 || d <= 0 || nq < 0 || k < 0 || m < 0 || steps < 0 || !(h > 0.0))
+    return OR_EINVAL;
+  if (k > 0 && (nprobe < 1 || nprobe > L)) return OR_EINVAL;
+  const size_t q1 = (size_t)(nq > 0 ? nq : 1);
+  int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * q1 * (size_t)(k > 0 ? k : 1));
+  int32_t* probes = (int32_t*)malloc(sizeof(int32_t) * q1 * (size_t)(nprobe > 0 ? nprobe : 1));
+  double* out = (double*)malloc(sizeof(double) * q1);
+  double* dY = (double*)malloc(sizeof(double) * q1 * (size_t)d);
+  double* dl = (double*)malloc(sizeof(double) * q1);
+  int status = OR_OK;
+  if (est)
+    for (int64_t q = 0; q < nq; ++q) est[q] = 0.0;
+  for (int s = 0; s < steps && status == OR_OK; ++s) {
+    if (k > 0)
+      or_ivf_search(X, n, d, C, L, assign, Y, nq, nprobe, k, probes, nbr, NULL);
+    status = or_deann_grad(X, n, d, Y, nq, OR_GAUSSIAN, h, k > 0 ? nbr : NULL, k, m,
+                           seed + (uint64_t)s, qid_offset, NULL, out, dY, dl);
+    if (status != OR_OK) break;
+    for (int64_t q = 0; q < nq; ++q) {
+      if (est) est[q] = out[q];
+      if (!(out[q] > 0.0)) continue;
+      float* y = Y + q * (int64_t)d;
+      for (int j = 0; j < d; ++j)
+        y[j] = (float)((double)y[j] + h * h * dY[q * (int64_t)d + j] / out[q]);
+    }
+  }
+  free(dl);
+  free(dY);
+  free(out);
+  free(probes);
+  free(nbr);
+  return status;
+}

@@ -132,12 +132,9 @@ def test_aniso_full_size_gradients(pkg):
     Yg, _ = index.mean_shift(Yd, 2, k, m, nprobe=P, seed=7)
     Yg = Yg.cpu().numpy()
     for q in qs[:16]:
-        yo = Y[q:q + 1].astype(np.float64)
-        for s in range(2):
-            y32 = yo.astype(np.float32)
-            _, nb, _ = oracle.ivf_search(X, C, assign, y32, P, k)
-            e, g, _ = oracle.deann_grad(X, y32, "gaussian", h, nb, m, 7 + s, qid_offset=int(q))
-            yo = y32.astype(np.float64) + h * h * g / e[:, None]
+        yo, _ = oracle.mean_shift(X, C, assign, Y[q:q + 1], h, k, m, P, 7, steps=2,
+                                  qid_offset=int(q))
+        yo = yo.astype(np.float64)
         moved = np.linalg.norm(yo[0] - Y[q])
         assert np.linalg.norm(Yg[q] - yo[0]) <= 1e-4 * max(moved, 1e-3), q
     index.close()

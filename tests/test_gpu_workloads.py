@@ -151,14 +151,11 @@ def test_aniso_gradient_and_mean_shift(pkg):
         fd = np.array([(f(y0 + step * e) - f(y0 - step * e)) / (2 * step)
                        for e in np.eye(X.shape[1])])
         assert np.linalg.norm(dY[q] - fd) <= 1e-3 * np.linalg.norm(fd)
-    # two mean-shift steps: the oracle repeats search + adjoint with seed + step
-    Yg, _ = index.mean_shift(_dev(Y[:16]), 2, k, m, nprobe=P, seed=7)
-    Yo = Y[:16].astype(np.float64)
-    for s in range(2):
-        Y32 = Yo.astype(np.float32)
-        _, nb, _ = oracle.ivf_search(X, C, assign, Y32, P, k)
-        e, g, _ = oracle.deann_grad(X, Y32, "gaussian", h, nb, m, 7 + s)
-        Yo = Y32.astype(np.float64) + h * h * g / e[:, None]
+    # two mean-shift steps against the oracle's driver (search + adjoint, seed + step)
+    Yg, eg = index.mean_shift(_dev(Y[:16]), 2, k, m, nprobe=P, seed=7)
+    Yo, eo = oracle.mean_shift(X, C, assign, Y[:16], h, k, m, P, 7, steps=2)
+    assert_kde_close(eg.cpu().numpy(), eo)
+    Yo = Yo.astype(np.float64)
     moved = np.linalg.norm(Yo - Y[:16], axis=1)
     err = np.linalg.norm(Yg.cpu().numpy() - Yo, axis=1)
     assert np.all(err <= 1e-4 * np.maximum(moved, 1e-3)), (err, moved)

@@ -730,3 +730,91 @@ def test_deann_variance_formula_given_the_neighbours():
     # variance for the kurtosis of these kernel values)
     assert abs(s2 / var - 1) < 0.08
     assert math.isclose(est.mean(), Kv.mean(), rel_tol=6 * math.sqrt(var / 4000) / Kv.mean())
+
+
+# ------------------------------------------------------------- mean shift ----
+def _mixture_small(n=300, d=4, nq=6, seed=31):
+    rng = np.random.default_rng(seed)
+    centres = rng.normal(0.0, 3.0, (4, d))
+    X = (centres[rng.integers(0, 4, n)] + rng.normal(0.0, 1.0, (n, d))).astype(np.float32)
+    Y = (centres[rng.integers(0, 4, nq)] + rng.normal(0.0, 1.5, (nq, d))).astype(np.float32)
+    return X, Y
+
+
+def test_mean_shift_step_is_the_weighted_mean_of_neighbours_and_samples():
+    """For the Gaussian kernel grad K = K (x - y) / h^2, so one step
+    y + h^2 grad(est)/est lands on sum_i w_i K_i x_i / sum_i w_i K_i over X_1 and
+    S, with w = 1/n on X_1 and (n - k')/(n m) per sample.  X_1 comes from the
+    IVF search (pinned by brute force) and S from the stream (pinned by the
+    published known answers); the weighted mean is formed here in numpy.  A
+    dropped h^2, a wrong sign of the gradient or weights without the (n - k')
+    factor each move the result off the weighted mean."""
+    X, Y = _mixture_small()
+    n = X.shape[0]
+    C, assign, _, _ = oracle.kmeans(X, 8, seed=2)
+    h, k, m, P, seed = 1.3, 20, 40, 3, 11
+    moved, est = oracle.mean_shift(X, C, assign, Y, h, k, m, P, seed, steps=1, qid_offset=5)
+    _, nbr, _ = oracle.ivf_search(X, C, assign, Y, P, k)
+    _, S = oracle.deann(X, Y, "gaussian", h, nbr, m, seed, qid_offset=5, return_samples=True)
+    X64 = X.astype(np.float64)
+    for q in range(Y.shape[0]):
+        ids = np.unique(nbr[q][nbr[q] >= 0])
+        y = Y[q].astype(np.float64)
+        K1 = np.exp(-((X64[ids] - y) ** 2).sum(1) / (2 * h * h))
+        K2 = np.exp(-((X64[S[q]] - y) ** 2).sum(1) / (2 * h * h))
+        w1, w2 = 1.0 / n, (n - ids.size) / (n * m)
+        num = w1 * (K1[:, None] * X64[ids]).sum(0) + w2 * (K2[:, None] * X64[S[q]]).sum(0)
+        den = w1 * K1.sum() + w2 * K2.sum()
+        assert est[q] == pytest.approx(den, rel=1e-12)
+        want = (num / den).astype(np.float32)
+        assert np.allclose(moved[q], want, rtol=0, atol=2e-6 * (1 + np.abs(want).max()))
+        assert np.abs(moved[q] - Y[q]).max() > 1e-3  # the step did move the query
+
+
+def test_mean_shift_with_every_point_as_neighbour_is_the_textbook_step():
+    """With one list and k = n the estimate is the exact KDE (no sampling),
+    and a step is the classical Gaussian mean-shift update sum K x / sum K over
+    all of X (Fukunaga-Hostetler; Comaniciu-Meer)."""
+    X, Y = _mixture_small(n=120, nq=4, seed=5)
+    n = X.shape[0]
+    C = X.astype(np.float64).mean(0, keepdims=True).astype(np.float32)
+    assign = np.zeros(n, dtype=np.int32)
+    h = 2.0
+    moved, _ = oracle.mean_shift(X, C, assign, Y, h, n, 50, 1, 3, steps=3)
+    y = Y.astype(np.float64)
+    X64 = X.astype(np.float64)
+    for _ in range(3):
+        K = np.exp(-((X64[None, :, :] - y[:, None, :]) ** 2).sum(2) / (2 * h * h))
+        y = ((K @ X64) / K.sum(1, keepdims=True)).astype(np.float32).astype(np.float64)
+    assert np.allclose(moved, y, rtol=0, atol=1e-5)
+
+
+def test_mean_shift_converges_to_the_centre_of_a_symmetric_set():
+    """Points c +- a e_j (j < d) are symmetric about c, so c is a stationary
+    point of the KDE; with h well above a it is the only mode, and the exact
+    (k = n) flow started anywhere nearby ends at c.  Started at c, it stays."""
+    d, a, h = 3, 1.0, 2.5
+    c = np.array([0.5, -1.25, 2.0])
+    X = np.concatenate([c + a * np.eye(d), c - a * np.eye(d)]).astype(np.float32)
+    n = X.shape[0]
+    C = c[None, :].astype(np.float32)
+    assign = np.zeros(n, dtype=np.int32)
+    Y = np.array([c + [0.4, -0.3, 0.2], c - [0.5, 0.1, 0.6], c], dtype=np.float32)
+    moved, _ = oracle.mean_shift(X, C, assign, Y, h, n, 10, 1, 0, steps=60)
+    assert np.abs(moved - c).max() < 1e-5
+    still, _ = oracle.mean_shift(X, C, assign, Y[2:], h, n, 10, 1, 0, steps=5)
+    assert np.abs(still[0] - c).max() < 1e-6
+
+
+def test_mean_shift_steps_redraw_with_seed_plus_step():
+    """Two steps with seed s equal one step with seed s followed by one step
+    with seed s + 1 from the moved queries (sets redrawn every step)."""
+    X, Y = _mixture_small(seed=9)
+    C, assign, _, _ = oracle.kmeans(X, 6, seed=1)
+    args = (1.1, 15, 30, 2)
+    two, _ = oracle.mean_shift(X, C, assign, Y, *args, 7, steps=2)
+    one, _ = oracle.mean_shift(X, C, assign, Y, *args, 7, steps=1)
+    again, _ = oracle.mean_shift(X, C, assign, one, *args, 8, steps=1)
+    assert np.array_equal(two, again)
+    other, _ = oracle.mean_shift(X, C, assign, one, *args, 7, steps=1)
+    assert not np.array_equal(two, other)
