@@ -227,6 +227,23 @@ kde_status kde_grad_with_neighbors(kde_index* index, const float* Y, int64_t nq,
                                    const float* gout, float* out, float* dY, float* dlogh,
                                    const kde_opts* opts);
 
+/* kde_grad -- the adjoint of kde_query: runs the same IVF search for X_1
+ * (k nearest among nprobe lists; none when k = 0) and the same sample S (seed,
+ * query ids as in kde_query), then the pathwise derivative of Algorithm 1's
+ * estimate with X_1 and S held fixed (the paper defines no gradient; X_1 is
+ * piecewise constant in y and E_S[estimate | X_1] is the exact KDE, so the
+ * derivative is unbiased for the KDE's almost everywhere):
+ *   dY[q]   gout[q] * d out[q] / d y_q (nq x d);
+ *   dlogh   NULL, or ONE float: sum_q gout[q] * d out[q] / d log h, summed on
+ *           the device in FP64 in a fixed order and rounded once.
+ * gout may be NULL (all ones).  The search is a deterministic function of
+ * (Y, index, k, nprobe, opts.precision), so after kde_query with the same
+ * arguments the sets are the ones that call used.  Limits as kde_query
+ * (sample_mode 0 or 1), d <= 1024.  Errors: EINVAL, ELIMIT, ECUDA. */
+kde_status kde_grad(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t m,
+                    int32_t nprobe, uint64_t seed, const float* gout, float* dY, float* dlogh,
+                    const kde_opts* opts);
+
 /* kde_mean_shift -- density-gradient flow with the DEANN estimate (Gaussian
  * kernel only; the paper names gradient lines of densities as a use of KDE,
  * Section 1): `steps` updates y <- y + h^2 grad(KDE~)(y) / KDE~(y), which for

@@ -85,6 +85,7 @@ def load_library():
         "kde_exact": [P, P, i64, P, O],
         "kde_sample_indices": [P, i64, P, i32, i32, u64, P, O],
         "kde_grad_with_neighbors": [P, P, i64, P, i32, i32, u64, P, P, P, P, O],
+        "kde_grad": [P, P, i64, i32, i32, i32, u64, P, P, P, O],
         "kde_mean_shift": [P, P, i64, i32, i32, i32, i32, u64, P, O],
         "kde_sync": [P, O],
         "kde_stats": [P, P, O],
@@ -384,6 +385,23 @@ class KDEIndex:
                                                                host=not Y.is_cuda))))
         return Y, est
 
+    def grad(self, Y, k, m, nprobe=1, seed=0, gout=None, precision=0, sample_mode=0,
+             qid_offset=0):
+        """(dY, dlogh) of the DEANN estimate (kde_grad: the search and the
+        sample of kde_query with the same arguments, held fixed); dlogh is the
+        device-side sum over the queries (a 0-d tensor)."""
+        Y = self._prep(Y)
+        nq = Y.shape[0]
+        g = None if gout is None else _f32(gout, device=Y.device)
+        dY = torch.empty((nq, self.d), dtype=torch.float32, device=Y.device)
+        dl = torch.empty((), dtype=torch.float32, device=Y.device)
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_grad(self._h, _ptr(Y), nq, int(k), int(m), int(nprobe),
+                                 int(seed) & (2**64 - 1), _ptr(g), _ptr(dY), _ptr(dl),
+                                 ctypes.byref(self._opts(precision, sample_mode, qid_offset,
+                                                         host=not Y.is_cuda))))
+        return dY, dl
+
     def grad_with_neighbors(self, Y, nbr, m, seed=0, gout=None, sample_mode=0, qid_offset=0):
         """(out, dY, dlogh_per_query) of the estimate with X_1 and S fixed."""
         Y = self._prep(Y)
@@ -501,27 +519,29 @@ class BatchServer:
 class DeannKDE(torch.autograd.Function):
     """out = DEANN estimate of KDE(Y) with bandwidth exp(log_h).
 
-    Forward runs the IVF search and the estimator; backward recomputes kernel
-    values from the saved neighbour ids and the regenerated sample (the same
-    Philox stream) and returns d/dY and d/dlog h of the estimate with the
-    neighbour set and the sample held fixed.
+    Forward runs kde_query (IVF search and estimator).  Backward runs
+    kde_grad with the same arguments: the library repeats the deterministic
+    search, regenerates the sample from the same Philox stream, recomputes the
+    kernel values and returns d/dY and the device-reduced d/dlog h of the
+    estimate with the neighbour set and the sample held fixed.  Nothing but
+    the queries and log h is saved.
     """
 
     @staticmethod
     def forward(ctx, Y, log_h, index: KDEIndex, k: int, m: int, nprobe: int, seed: int,
                 precision: int = 0):
-        index.set_bandwidth(float(torch.exp(log_h.detach()).item()))
-        out, nbr = index.query(Y.detach(), k, m, nprobe=nprobe, seed=seed, precision=precision,
-                               return_neighbors=True)
-        ctx.index, ctx.m, ctx.seed = index, m, seed
-        ctx.save_for_backward(Y.detach(), nbr if nbr is not None else torch.empty(0))
-        ctx.k = k
+        h = float(torch.exp(log_h.detach()).item())
+        index.set_bandwidth(h)
+        out = index.query(Y.detach(), k, m, nprobe=nprobe, seed=seed, precision=precision)
+        ctx.index, ctx.args, ctx.h = index, (k, m, nprobe, seed, precision), h
+        ctx.save_for_backward(Y.detach())
         return out
 
     @staticmethod
     def backward(ctx, gout):
-        Y, nbr = ctx.saved_tensors
-        nb = nbr if ctx.k > 0 else None
-        _, dY, dl = ctx.index.grad_with_neighbors(Y, nb, ctx.m, seed=ctx.seed,
-                                                  gout=gout.contiguous())
-        return dY, dl.sum().reshape(()), None, None, None, None, None, None
+        (Y,) = ctx.saved_tensors
+        k, m, nprobe, seed, precision = ctx.args
+        ctx.index.set_bandwidth(ctx.h)
+        dY, dl = ctx.index.grad(Y, k, m, nprobe=nprobe, seed=seed, gout=gout.contiguous(),
+                                precision=precision)
+        return dY, dl.to(gout.dtype), None, None, None, None, None, None

@@ -1114,6 +1114,80 @@ kde_status kde_grad_with_neighbors(kde_index* ix, const float* Y, int64_t nq,
   return finish_call(ix, host, st);
 }
 
+kde_status kde_grad(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32_t m,
+                    int32_t nprobe, uint64_t seed, const float* gout, float* dY, float* dlogh,
+                    const kde_opts* opts) {
+  TRY(check_index(ix));
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
+  TRY(check_est_args(ix, nq, k, m, o));
+  if (ix->d > 1024) return fail(KDE_EINVAL, "the adjoint supports d <= 1024");
+  if (o->sample_mode == 2) return fail(KDE_EINVAL, "the adjoint supports sample_mode 0 and 1");
+  if (k > 0) {
+    TRY(check_search_args(ix, nq, k, nprobe));
+  } else if (m < 1) {
+    return fail(KDE_EINVAL, "k = 0 needs m >= 1");
+  }
+  if (nq == 0) {
+    if (dlogh == nullptr) return KDE_OK;
+    // an empty batch: dlogh = 0 in the space of the pointer
+    DeviceGuard g(ix->device);
+    const Space sp = space_of(dlogh, ix->device);
+    if (sp == SPACE_FOREIGN) return fail(KDE_ESTATE, "dlogh lives on another device");
+    if (sp == SPACE_HOST) {
+      *dlogh = 0.f;
+      return KDE_OK;
+    }
+    CK(cudaMemsetAsync(dlogh, 0, sizeof(float), stream_of(o)));
+    return KDE_OK;
+  }
+  if (Y == nullptr || dY == nullptr) return fail(KDE_EINVAL, "Y and dY must not be NULL");
+  DeviceGuard g(ix->device);
+  bool host = false;
+  TRY(call_space(ix, Y, {gout, dY, dlogh}, &host));
+  cudaStream_t st = stream_of(o);
+  CallShape c;
+  c.nq = nq;
+  c.k = k;
+  c.m = m;
+  c.P = nprobe;
+  c.search = k > 0;
+  c.host = host;
+  c.need_nbr = k > 0;
+  c.need_out = true;
+  c.grad = true;
+  CallBufs cb;
+  TRY(prepare_call(ix, c, cb));
+  TRY(stage_queries(ix, Y, nq, host, cb, st));
+  // X_1: the same search kde_query runs (a deterministic function of the
+  // queries, the index, k, nprobe and the scan precision)
+  if (k > 0)
+    TRY(run_search(ix, cb, nq, k, nprobe, o->precision, cb.nbr, nullptr, nullptr, st, true));
+  const float* go = gout;
+  if (host && gout) {
+    CK(cudaMemcpyAsync(cb.gout, gout, sizeof(float) * nq, cudaMemcpyHostToDevice, st));
+    go = cb.gout;
+  }
+  SampleArgs a = sample_args(ix, cb, nq, k > 0 ? cb.nbr : nullptr, k, m, seed, o);
+  a.rs = k == 0 ? 1 : 0;
+  a.nbr_distinct = 1;
+  a.gout = go;
+  a.out = cb.out;
+  a.dY = host ? cb.dY : dY;
+  a.dlogh = cb.dlogh;
+  {
+    StageTimer t(ix, ST_GRAD, st, dlogh ? 2 : 1);
+    launch_estimate_grad(a, st);
+    // dlogh = sum over the queries of gout[q] d out[q] / d log h
+    if (dlogh) launch_sum_to_scalar(cb.dlogh, nq, host ? cb.out : dlogh, st);
+  }
+  if (host) {
+    TRY(copy_out(dY, cb.dY, sizeof(float) * nq * ix->d, true, st));
+    if (dlogh) TRY(copy_out(dlogh, cb.out, sizeof(float), true, st));
+  }
+  return finish_call(ix, host, st);
+}
+
 kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, int32_t k,
                           int32_t m, int32_t nprobe, uint64_t seed, float* est,
                           const kde_opts* opts) {

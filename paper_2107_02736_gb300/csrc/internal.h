@@ -329,5 +329,7 @@ void launch_prepend_self(const int32_t* zid, const int32_t* nbr, int64_t nz, int
                          cudaStream_t s);
 void launch_loo_reduce(const float* loo, const float* dloo, int64_t nz, double* red,
                        cudaStream_t s);
+// out[0] = sum of v[0..n) (FP64 in a fixed order, rounded once); one block
+void launch_sum_to_scalar(const float* v, int64_t n, float* out, cudaStream_t s);
 
 }  // namespace deann

@@ -962,6 +962,24 @@ __global__ void k_prepend_self(const int32_t* __restrict__ zid, const int32_t* _
 // red[2] = points used; loo[j] is the held-out estimate at z_j, dloo[j] its
 // derivative.  A point with no held-out density (loo <= 0: every other kernel
 // value underflowed) is left out.
+// out[0] = sum_i v[i], FP64 partial sums in a fixed order (thread t takes
+// i = t, t + 1024, ...; then a tree over the 1024 partials), rounded once, so
+// that the result does not depend on the launch or the device.
+__global__ void __launch_bounds__(1024) k_sum_to_scalar(const float* __restrict__ v, int64_t n,
+                                                        float* __restrict__ out) {
+  __shared__ double part[1024];
+  const int tid = threadIdx.x;
+  double a = 0.0;
+  for (int64_t i = tid; i < n; i += 1024) a += (double)v[i];
+  part[tid] = a;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (tid < o) part[tid] += part[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) out[0] = (float)part[0];
+}
+
 __global__ void __launch_bounds__(1024) k_loo_reduce(const float* __restrict__ loo,
                                                      const float* __restrict__ dloo, int64_t nz,
                                                      double* __restrict__ red) {
@@ -1005,6 +1023,10 @@ void launch_prepend_self(const int32_t* zid, const int32_t* nbr, int64_t nz, int
 void launch_loo_reduce(const float* loo, const float* dloo, int64_t nz, double* red,
                        cudaStream_t s) {
   k_loo_reduce<<<1, 1024, 0, s>>>(loo, dloo, nz, red);
+}
+
+void launch_sum_to_scalar(const float* v, int64_t n, float* out, cudaStream_t s) {
+  k_sum_to_scalar<<<1, 1024, 0, s>>>(v, n, out);
 }
 
 void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const float* est,

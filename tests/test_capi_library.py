@@ -30,7 +30,8 @@ def lib():
 def test_header_declares_the_path():
     names = _declared()
     for want in ("kde_build", "kde_query", "kde_exact", "kde_query_rs", "kde_search",
-                 "kde_grad_with_neighbors", "kde_query_with_neighbors", "kde_sample_indices",
+                 "kde_grad", "kde_grad_with_neighbors", "kde_query_with_neighbors",
+                 "kde_sample_indices", "kde_mean_shift",
                  "kde_export_ivf", "kde_free"):
         assert want in names
 

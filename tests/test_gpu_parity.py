@@ -366,6 +366,52 @@ def test_gradient_matches_oracle(pkg, kernel, d):
     assert np.all(np.abs(dl - w_dl) <= 1e-4 * np.abs(w_dl) + 1e-9)
 
 
+@pytest.mark.parametrize("kernel,precision", [("gaussian", 1), ("exponential", 0),
+                                              ("laplacian", 0)])
+def test_grad_entry_point_matches_oracle(pkg, kernel, precision):
+    """kde_grad (search + adjoint in one call, dlogh reduced on the device)
+    against the oracle: the IVF search re-run from the exported index, then
+    the pathwise gradient with those sets; dlogh is the sum over queries."""
+    X, Y, _ = workloads.mixture_iso(n=6000, d=24, nq=70)
+    h = 3.0 if kernel != "laplacian" else 12.0
+    k, m, P = 40, 300, 3
+    index = pkg.KDEIndex(_dev(X), kernel, h, nlist=16, seed=2)
+    C, assign = (a.numpy() for a in index.export_ivf())
+    rng = np.random.default_rng(8)
+    gout = rng.uniform(0.5, 2.0, size=Y.shape[0]).astype(np.float32)
+    dY, dl = index.grad(_dev(Y), k, m, nprobe=P, seed=4, gout=_dev(gout), precision=precision,
+                        qid_offset=11)
+    _, nbr, d2 = oracle.ivf_search(X, C, assign, Y, P, k)
+    got_nbr = index.query(_dev(Y), k, m, nprobe=P, seed=4, precision=precision,
+                          return_neighbors=True)[1].cpu().numpy()
+    assert_neighbours_match(X, Y, got_nbr, nbr, d2)
+    # the oracle's gradient with the GPU's sets (equal up to distance ties)
+    w_out, w_dY, w_dl = oracle.deann_grad(X, Y, kernel, h, got_nbr, m, 4, qid_offset=11,
+                                          gout=gout)
+    dY = dY.cpu().numpy().astype(np.float64)
+    for q in range(Y.shape[0]):
+        assert np.linalg.norm(dY[q] - w_dY[q]) <= 1e-4 * np.linalg.norm(w_dY[q]) + 1e-9
+    assert dl.dim() == 0
+    assert math.isclose(dl.item(), w_dl.sum(), rel_tol=1e-4, abs_tol=1e-9)
+    # host pointers give the same result
+    dYh, dlh = index.grad(torch.from_numpy(Y), k, m, nprobe=P, seed=4,
+                          gout=torch.from_numpy(gout), precision=precision, qid_offset=11)
+    assert np.array_equal(dYh.numpy(), dY.astype(np.float32))
+    assert dlh.item() == dl.item()
+    # an empty batch has dlogh = 0
+    dY0, dl0 = index.grad(_dev(Y[:0]), k, m, nprobe=P)
+    assert dY0.shape == (0, X.shape[1]) and dl0.item() == 0.0
+
+
+def test_grad_entry_point_k0_is_the_rs_gradient(pkg):
+    X, Y = _data(1500, 8, 20, seed=12)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 1.5, nlist=4)
+    dY, dl = index.grad(_dev(Y), 0, 500, seed=3)
+    _, w_dY, w_dl = oracle.deann_grad(X, Y, "gaussian", 1.5, None, 500, 3)
+    assert np.allclose(dY.cpu().numpy(), w_dY, rtol=1e-4, atol=1e-4 * np.abs(w_dY).max())
+    assert math.isclose(dl.item(), w_dl.sum(), rel_tol=1e-4)
+
+
 def test_autograd_function(pkg):
     X, Y, _ = workloads.mixture_aniso(n=4000, d=64, nq=32)
     index = pkg.KDEIndex(_dev(X), "gaussian", 1.0, nlist=8)
@@ -377,6 +423,11 @@ def test_autograd_function(pkg):
     _, w_dY, w_dl = oracle.deann_grad(X, Y, "gaussian", 1.0, nbr, 200, 5)
     assert np.allclose(Yt.grad.cpu().numpy(), w_dY, rtol=1e-4, atol=1e-4 * np.abs(w_dY).max())
     assert math.isclose(log_h.grad.item(), w_dl.sum(), rel_tol=1e-4)
+    # the backward pass used the forward's neighbour sets: the same gradient
+    # as the adjoint given the neighbour ids the forward returned
+    _, nbr_fwd = index.query(_dev(Y), 20, 200, nprobe=3, seed=5, return_neighbors=True)
+    _, dY2, _ = index.grad_with_neighbors(_dev(Y), nbr_fwd, 200, seed=5)
+    assert np.array_equal(Yt.grad.cpu().numpy(), dY2.cpu().numpy())
 
 
 # --------------------------------------------------------------- edge cases --
