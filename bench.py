@@ -14,8 +14,12 @@ validation and test queries and the seed-to-seed spread of the timed steps);
 the headline is the faster of the two, and the test-set error of every timed
 step is reported.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the host cores instead (a bounded query sample per step).
+Output (rank 0): the untimed extras (tuning grids, the other workloads, the
+paper's robustness experiments) go out first, one JSON line each with a
+"side" key; the headline goes out LAST as one compact JSON line (a few KB)
+that also carries short summaries of those extras.  ``--impl reference``
+times the FP64 CPU oracle on the host cores instead (a bounded query sample
+per step, the same schedule).
 """
 from __future__ import annotations
 
@@ -38,6 +42,11 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
+# The schedule (k, m, nprobe) of the headline workload, per scan precision:
+# the cheapest that `bench.py --tune` finds with a mean relative error <= 0.9e-2
+# on the 4,000 validation queries.  Both arms run it unless --schedule or --tune
+# says otherwise.
+DEFAULT_SCHEDULE = {"bf16": (1536, 4000, 8), "fp32": (1536, 4000, 8)}
 TARGET_ERR = 1e-2
 # the tuners aim 10 % below the target on the validation queries, so that
 # every timed step (each with its own seed) stays within it on the test queries
@@ -54,10 +63,14 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0, help="shrink n (debug only)")
     p.add_argument("--kernel", default="gaussian")
-    p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--tune", action="store_true",
+                   help="search (k, m, nprobe) per scan precision on the validation queries "
+                        "instead of using the committed schedule")
     p.add_argument("--schedule", default="", metavar="K,M,NPROBE",
-                   help="use this DEANN schedule for both scan precisions instead of tuning")
+                   help="use this DEANN schedule for both scan precisions")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    p.add_argument("--ref-budget", type=float, default=100.0,
+                   help="--impl reference: seconds of oracle work over all steps")
     p.add_argument("--no-schedules", dest="schedules", action="store_false",
                    help="skip the recall / k = m / fixed-parameter runs (untimed extras)")
     p.add_argument("--fp8-study", type=int, default=0, metavar="NQ",
@@ -96,6 +109,46 @@ def job_throughput(units_per_rank, world, ms_per_step):
     """Whole-job units/s: every rank serves its own batch (replicas), and the
     step time is the slowest rank's."""
     return units_per_rank * world / (ms_per_step / 1000.0)
+
+
+def emit(kind, obj):
+    """One untimed extra as its own JSON line, ahead of the headline."""
+    print(json.dumps({"side": kind, **obj}), flush=True)
+
+
+def sig(x, digits=4):
+    """x rounded to `digits` significant digits (recursively for containers),
+    to keep the headline line short."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, digits) for v in x]
+    return x
+
+
+# The driver reads the end of stdout (about 3 KB): the headline line has to
+# fit in it whole, with room for a prefix.
+HEADLINE_LIMIT = 2700
+
+
+def fit_headline(line, limit=HEADLINE_LIMIT,
+                 optional=("forms", "baselines", "path_roofline", "stage_ms_per_step")):
+    """The headline as JSON text of at most `limit` bytes: optional sections
+    are moved, in the given order, to a side line printed ahead of it until
+    the rest fits.  Returns (text, moved sections)."""
+    line = dict(line)
+    moved = {}
+    text = json.dumps(line)
+    for key in optional:
+        if len(text) <= limit:
+            break
+        if key in line:
+            moved[key] = line.pop(key)
+            line["moved_to_side_line"] = sorted(moved)
+            text = json.dumps(line)
+    return text, moved
 
 
 def rel_err(est, exact):
@@ -252,16 +305,16 @@ def time_calls(fn, reps, torch):
 M_GRID = [int(round(1000 * 2 ** (i / 4))) for i in range(25)]
 
 
-def tune(index, Yv_d, exact_v, torch, precision):
-    """Cheapest (k, m, nprobe) whose validation mean rel. err is <= 1e-2.  For
+def tune(index, Yv_d, exact_v, torch, precision, ks=(800, 1024, 1536, 2048), Ps=(8, 16),
+         m_grid=None):
+    """Cheapest (k, m, nprobe) whose validation mean rel. err is <= 0.9e-2.  For
     every (k, nprobe), m grows in quarter-octave steps until the target is met
-    (more samples only cost more)."""
+    (more samples only cost more); the time is that of a call on the
+    validation queries."""
     results = []
-    # smaller k (100 - 400) and nprobe = 32 never lead here: on this workload
-    # k <= 800 misses the target even at m = 64,000
-    for P in (8, 16):
-        for k in (800, 1024, 1536, 2048):
-            for m in M_GRID:
+    for P in Ps:
+        for k in ks:
+            for m in (m_grid or M_GRID):
                 est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=precision)
                 err = rel_err(est.cpu().numpy(), exact_v)
                 ms = time_calls(lambda: index.query(Yv_d, k, m, nprobe=P, seed=1,
@@ -275,25 +328,21 @@ def tune(index, Yv_d, exact_v, torch, precision):
 
 
 def choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args):
-    """The schedule of the measured configuration: per scan precision the
-    cheapest (k, m, nprobe) whose validation error meets the target, then the
-    precision whose schedule serves the test queries fastest."""
+    """The schedule of the measured configuration per scan precision: the
+    committed one (DEFAULT_SCHEDULE), the --schedule one, or with --tune the
+    cheapest meeting the validation target; then the precision whose schedule
+    serves the test queries fastest among those meeting it."""
     nq = Yd.shape[0]
-    spec = workloads.CONFIGS[2]
     sched, tuned = {}, {}
     for name, prec in PRECISIONS.items():
-        if args.schedule:
-            k, m, P = (int(v) for v in args.schedule.split(","))
-            est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=prec)
-            sched[name] = dict(k=k, m=m, nprobe=P, val_ms=0.0,
-                               val_err=rel_err(est.cpu().numpy(), exact_v))
-            tuned[name] = []
-        elif args.no_tune:
-            sched[name] = dict(k=spec["k"], m=spec["m"], nprobe=spec["nprobe"], val_ms=0.0,
-                               val_err=None)
-            tuned[name] = []
-        else:
+        if args.tune:
             sched[name], tuned[name] = tune(index, Yv_d, exact_v, torch, prec)
+            continue
+        k, m, P = ((int(v) for v in args.schedule.split(",")) if args.schedule
+                   else DEFAULT_SCHEDULE[name])
+        est = index.query(Yv_d, k, m, nprobe=P, seed=12345, precision=prec)
+        sched[name] = dict(k=k, m=m, nprobe=P, val_ms=0.0,
+                           val_err=rel_err(est.cpu().numpy(), exact_v))
     variants = {}
     for name, prec in PRECISIONS.items():
         s = sched[name]
@@ -303,8 +352,7 @@ def choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args):
                                   precision=prec).cpu().numpy(), exact_t)
         variants[name] = dict(k=s["k"], m=s["m"], nprobe=s["nprobe"], qps=nq / (ms / 1e3),
                               test_rel_err=err, val_rel_err=s["val_err"])
-    ok = [v for v in variants if variants[v]["val_rel_err"] is not None
-          and variants[v]["val_rel_err"] <= TUNE_ERR]
+    ok = [v for v in variants if variants[v]["val_rel_err"] <= TUNE_ERR]
     head = max(ok or variants, key=lambda v: variants[v]["qps"])
     return head, sched, tuned, variants
 
@@ -478,12 +526,22 @@ def differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev
     return out
 
 
+ROW_FIELDS = "k,m,nprobe,queries/s,test mean rel.err"
+
+
+def row(k, m, P, qps, err):
+    """A compact schedule row for the headline line (fields: ROW_FIELDS)."""
+    return sig([int(k), int(m), int(P), float(qps), float(err)])
+
+
 def precision_form(torch, pkg, dev):
     """The sparse image-like workload at full size (n = 1M, d = 784, 80 % zeros,
     10,000 test queries; Gaussian kernel, h bisected to a mean exact KDE of
-    1e-4 on 1,000 validation queries): DEANN at k = 200, m = 2,000 over 2,048
-    lists with nprobe = 32, BF16 list scan (FP32 rescoring) next to the FP32
-    scan, each against the exact KDE of every test query."""
+    1e-4 on 1,000 validation queries; 2,048 lists): DEANN with the BF16 list
+    scan (FP32 rescoring) next to the FP32 scan, at the configuration's
+    k = 200, m = 2,000, nprobe = 32 and at the cheapest schedule each
+    precision needs for a mean relative error <= 1e-2 (tuned on the validation
+    queries), each against the exact KDE of every test query."""
     sp = workloads.CONFIGS[3]
     X, Y, Yv = workloads.sparse_image()
     nq = Y.shape[0]
@@ -494,34 +552,77 @@ def precision_form(torch, pkg, dev):
     build_s = time.perf_counter() - t0
     Yd, Yv_d = torch.from_numpy(Y).to(dev), torch.from_numpy(Yv[:1000]).to(dev)
     h, mu = fit_bandwidth(index, Yv_d, sp["target_mu"])
+    exact_v = index.exact(Yv_d).cpu().numpy()
     exact_t = index.exact(Yd).cpu().numpy()
     ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
     k, m, P = sp["k"], sp["m"], sp["nprobe"]
     out = {"workload": sp["name"], "n": int(X.shape[0]), "d": int(X.shape[1]), "nq": int(nq),
-           "kernel": "gaussian", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"], "k": k,
-           "m": m, "nprobe": P, "build_s": build_s, "exact_qps": nq / (ms_exact / 1e3)}
+           "kernel": "gaussian", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"],
+           "build_s": build_s, "exact_qps": nq / (ms_exact / 1e3)}
+    short = {"exact_qps": sig(nq / (ms_exact / 1e3))}
     ids = {}
     for name, prec in PRECISIONS.items():
         est, nb = index.query(Yd, k, m, nprobe=P, seed=6, precision=prec, return_neighbors=True)
         ms = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=5, precision=prec), 3,
                         torch)
-        out[name] = {"qps": nq / (ms / 1e3), "ms_per_call": ms,
-                     "test_rel_err": rel_err(est.cpu().numpy(), exact_t)}
+        err = rel_err(est.cpu().numpy(), exact_t)
+        out[name] = {"fixed": {"k": k, "m": m, "nprobe": P, "qps": nq / (ms / 1e3),
+                               "ms_per_call": ms, "test_rel_err": err}}
+        short[name + "_fixed"] = row(k, m, P, nq / (ms / 1e3), err)
         ids[name] = np.sort(nb.cpu().numpy(), 1)
-    out["same_neighbours"] = bool(np.array_equal(ids["fp32"], ids["bf16"]))
+        best, grid = tune(index, Yv_d, exact_v, torch, prec, ks=(200, 400, 800, 1600),
+                          Ps=(16, 32))
+        bk, bm, bP = best["k"], best["m"], best["nprobe"]
+        ms = time_calls(lambda: index.query(Yd, bk, bm, nprobe=bP, seed=5, precision=prec), 3,
+                        torch)
+        err = rel_err(index.query(Yd, bk, bm, nprobe=bP, seed=6, precision=prec).cpu().numpy(),
+                      exact_t)
+        out[name]["tuned"] = {"k": bk, "m": bm, "nprobe": bP, "qps": nq / (ms / 1e3),
+                              "val_rel_err": best["val_err"], "test_rel_err": err}
+        out[name]["grid"] = grid
+        short[name] = row(bk, bm, bP, nq / (ms / 1e3), err)
+    out["same_neighbours_fixed"] = bool(np.array_equal(ids["fp32"], ids["bf16"]))
     out["margin_failures"] = index.margin_failures()
+    short["same_nbrs"] = out["same_neighbours_fixed"]
     index.close()
-    return out
+    return out, short
+
+
+def exponential_form(X, Yd, Yv_d, torch, pkg, dev, nlist):
+    """The headline dataset (n = 1M, d = 128, 1,024 lists) with the
+    exponential kernel, h bisected to the same mean exact KDE of 1e-3: the
+    cheapest BF16-scan DEANN schedule for a mean relative error <= 1e-2 on the
+    validation queries, timed on the 10,000 test queries."""
+    spec = workloads.CONFIGS[2]
+    index = pkg.KDEIndex(torch.from_numpy(X).to(dev), "exponential", 1.0, nlist=nlist, seed=1)
+    h, mu = fit_bandwidth(index, Yv_d, spec["target_mu"])
+    exact_v = index.exact(Yv_d).cpu().numpy()
+    exact_t = index.exact(Yd).cpu().numpy()
+    nq = Yd.shape[0]
+    ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
+    best, grid = tune(index, Yv_d, exact_v, torch, 1)
+    k, m, P = best["k"], best["m"], best["nprobe"]
+    ms = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=5, precision=1), 3, torch)
+    err = rel_err(index.query(Yd, k, m, nprobe=P, seed=6, precision=1).cpu().numpy(), exact_t)
+    out = {"workload": WORKLOAD.replace("gaussian", "exponential"), "kernel": "exponential",
+           "h": h, "val_mean_kde": mu, "k": k, "m": m, "nprobe": P, "qps": nq / (ms / 1e3),
+           "val_rel_err": best["val_err"], "test_rel_err": err,
+           "exact_qps": nq / (ms_exact / 1e3), "grid": grid}
+    index.close()
+    return out, {"row": row(k, m, P, nq / (ms / 1e3), err),
+                 "exact_qps": sig(nq / (ms_exact / 1e3))}
 
 
 def batched_form(torch, pkg, dev):
     """The unit-norm power-law workload at full size (n = 4M, d = 300,
     exponential kernel, h bisected to a mean exact KDE of 1e-3 on 1,000
-    validation queries; BF16 scan, k = 200, m = 2,000, 4,096 lists, nprobe
-    tuned on the validation queries): 100,000 test queries in 64 batches of 16
-    to 8,192 served by CUDA-graph replays (one graph per power-of-two
-    capacity), the backward pass on every tenth batch; error against the
-    exact KDE on 4,096 of the test queries."""
+    validation queries; BF16 scan, 4,096 lists): 100,000 test queries in 64
+    batches of 16 to 8,192 served by CUDA-graph replays (one graph per
+    power-of-two capacity), the backward pass on every tenth batch; error
+    against the exact KDE on 4,096 of the test queries.  Served at the
+    configuration's k = 200, m = 2,000 (nprobe tuned) and at the cheapest
+    (k, m, nprobe) meeting a mean relative error <= 1e-2 on the validation
+    queries."""
     sp = workloads.CONFIGS[5]
     X, Y, Yv = workloads.unit_powerlaw()
     sizes = workloads.uneven_batches()
@@ -534,6 +635,42 @@ def batched_form(torch, pkg, dev):
     Yd, Yv_d = torch.from_numpy(Y).to(dev), torch.from_numpy(Yv[:1000]).to(dev)
     h, mu = fit_bandwidth(index, Yv_d, sp["target_mu"])
     exact_v = index.exact(Yv_d).cpu().numpy()
+    sub = np.random.default_rng(7).choice(nq, 4096, replace=False)
+    exact_s = index.exact(Yd[torch.from_numpy(sub).to(dev)]).cpu().numpy()
+    res = torch.empty(nq, dtype=torch.float32, device=dev)
+
+    def serve_all(k, m, P):
+        server = pkg.BatchServer(index, k, m, nprobe=P, seed=9, precision=1, max_batch=8192,
+                                 neighbors=True)
+
+        def serve():
+            server.next_qid, start = 0, 0
+            for b, nb in enumerate(sizes):
+                nb = int(nb)
+                Yb = Yd[start:start + nb]
+                est, ids = server(Yb)
+                res[start:start + nb].copy_(est)
+                if b % 10 == 0:
+                    server.backward(Yb, ids)
+                start += nb
+
+        serve()  # captures the graphs
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        serve()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        err = rel_err(res.cpu().numpy()[sub], exact_s)
+        ms_one = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=9, precision=1), 2,
+                            torch)
+        r = {"k": k, "m": m, "nprobe": P, "graphs": len(server.graphs), "served_ms": ms,
+             "served_qps": nq / (ms / 1e3), "one_call_qps": nq / (ms_one / 1e3),
+             "rel_err_4096": err}
+        del server
+        return r
+
     k, m = sp["k"], sp["m"]
     trials = []
     for P in (4, 8, 16, 32, 64):
@@ -547,44 +684,24 @@ def batched_form(torch, pkg, dev):
     ok = [t for t in trials if t["val_rel_err"] <= TUNE_ERR]
     P = (min(ok, key=lambda t: t["val_ms"]) if ok
          else min(trials, key=lambda t: t["val_rel_err"]))["nprobe"]
-    server = pkg.BatchServer(index, k, m, nprobe=P, seed=9, precision=1, max_batch=8192,
-                             neighbors=True)
-    res = torch.empty(nq, dtype=torch.float32, device=dev)
-
-    def serve():
-        server.next_qid, start = 0, 0
-        for b, nb in enumerate(sizes):
-            nb = int(nb)
-            Yb = Yd[start:start + nb]
-            est, ids = server(Yb)
-            res[start:start + nb].copy_(est)
-            if b % 10 == 0:
-                server.backward(Yb, ids)
-            start += nb
-
-    serve()  # captures the graphs
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    serve()
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    sub = np.random.default_rng(7).choice(nq, 4096, replace=False)
-    exact_s = index.exact(Yd[torch.from_numpy(sub).to(dev)]).cpu().numpy()
-    err = rel_err(res.cpu().numpy()[sub], exact_s)
-    ms_one = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=9, precision=1), 2, torch)
+    fixed = serve_all(k, m, P)
+    best, grid = tune(index, Yv_d, exact_v, torch, 1, ks=(200, 400, 800, 1600),
+                      Ps=(4, 8, 16))
+    tuned = serve_all(best["k"], best["m"], best["nprobe"])
+    tuned["val_rel_err"] = best["val_err"]
     out = {"workload": sp["name"], "n": int(X.shape[0]), "d": int(X.shape[1]), "nq": int(nq),
-           "kernel": "exponential", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"], "k": k,
-           "m": m, "nprobe": P, "nprobe_trials": trials, "build_s": build_s,
-           "batches": int(sizes.size), "batch_min": int(sizes.min()),
-           "batch_max": int(sizes.max()), "graphs": len(server.graphs),
+           "kernel": "exponential", "h": h, "val_mean_kde": mu, "nlist": sp["nlist"],
+           "build_s": build_s, "batches": int(sizes.size), "batch_min": int(sizes.min()),
+           "batch_max": int(sizes.max()),
            "backward_batches": int((np.arange(sizes.size) % 10 == 0).sum()),
-           "served_ms": ms, "served_qps": nq / (ms / 1e3),
-           "one_call_qps": nq / (ms_one / 1e3), "rel_err_4096": err,
+           "nprobe_trials": trials, "fixed": fixed, "tuned": tuned, "grid": grid,
            "margin_failures": index.margin_failures()}
+    short = {"fixed": row(k, m, P, fixed["served_qps"], fixed["rel_err_4096"]),
+             "tuned": row(tuned["k"], tuned["m"], tuned["nprobe"], tuned["served_qps"],
+                          tuned["rel_err_4096"]),
+             "one_call_qps": sig([fixed["one_call_qps"], tuned["one_call_qps"]])}
     index.close()
-    return out
+    return out, short
 
 
 def nn_contribution_map(torch, pkg, dev, R=4096):
@@ -655,49 +772,66 @@ def oracle_sample_rate(X, Y, C, assign, kernel, h, k, m, nprobe, budget):
 
 # --------------------------------------------------------------------- main --
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle (IVF search from the exported index +
+    Algorithm 1) on the host cores, on the headline workload at the same
+    schedule as the GPU arm (the committed BF16 one, or --schedule).  Each step
+    runs the oracle on the same bounded sample of the test queries; the
+    sample's size is set once from a short probe so that the whole
+    --warmup + --steps run takes about --ref-budget seconds.  ms_per_step is
+    the measured wall time of a step (that sample), value the sample's queries
+    per second."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     X, Y, Yval = make_workload(args)
     spec = workloads.CONFIGS[2]
+    k, m, P = ((int(v) for v in args.schedule.split(",")) if args.schedule
+               else DEFAULT_SCHEDULE["bf16"])
     # The oracle searches an inverted file exported by the GPU library (its
-    # k-means is not part of the oracle); the bandwidth and the schedule
-    # (k, m, nprobe) are the ones the GPU arm measures with.
+    # k-means is not part of the oracle), and h is the workload's: bisected so
+    # that the mean exact KDE of the validation queries is 1e-3.  Neither is
+    # timed; no GPU tuning runs here.
     import torch
     import paper_2107_02736_gb300 as pkg
     index = pkg.KDEIndex(torch.from_numpy(X).cuda(), args.kernel, 1.0, nlist=spec["nlist"], seed=1)
-    Yv_d, Yd = torch.from_numpy(Yval).cuda(), torch.from_numpy(Y).cuda()
-    h, _ = fit_bandwidth(index, Yv_d, spec["target_mu"])
-    exact_v = index.exact(Yv_d).cpu().numpy()
-    exact_t = index.exact(Yd).cpu().numpy()
-    head, sched, _, _ = choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args)
-    k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
+    h, _ = fit_bandwidth(index, torch.from_numpy(Yval).cuda(), spec["target_mu"])
     C, assign = index.export_ivf()
     C, assign = C.numpy(), assign.numpy()
     index.close()
-    per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
-    rates, sample = [], 0
-    for step in range(args.warmup + args.steps):
-        qps, cores, done, spent = oracle_sample_rate(X, Y, C, assign, args.kernel, h, k, m, P,
-                                                     per_step)
-        if step >= args.warmup:
-            rates.append(qps)
-            sample = done
-    value = statistics.mean(rates)
+
+    def one_step(nq_s):
+        t0 = time.perf_counter()
+        Ys = Y[:nq_s]
+        _, nbr, _ = oracle.ivf_search(X, C, assign, Ys, P, k)
+        oracle.deann(X, Ys, args.kernel, h, nbr, m, 0)
+        return time.perf_counter() - t0
+
+    probe_q = 64
+    rate = probe_q / one_step(probe_q)
+    per_step = args.ref_budget / max(1, args.steps + args.warmup)
+    nq_s = int(max(16, min(Y.shape[0], round(rate * per_step))))
+    for _ in range(args.warmup):
+        one_step(nq_s)
+    times = [one_step(nq_s) for _ in range(args.steps)]
+    ms_step = 1000.0 * statistics.mean(times)
+    value = nq_s / (ms_step / 1000.0)
+    cores = oracle.num_threads()
+    sample = (f"the first {nq_s} of the {Y.shape[0]} test queries per step (IVF search from "
+              f"the exported index + DEANN, FP64)")
     line = {
-        "impl": "reference", "metric": "kde_queries_per_s_at_1e-2_mean_rel_err", "value": value,
-        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * Y.shape[0] / value, "higher_is_better": True,
+        "impl": "reference", "metric": "kde_queries_per_s_at_1e-2_mean_rel_err",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "k": k, "m": m, "nprobe": P, "h": h},
+        "config": {"workload": WORKLOAD, "k": k, "m": m, "nprobe": P, "h": h,
+                   "queries_per_step": nq_s},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} test queries per step (IVF search from the "
-                                   f"exported index + DEANN, FP64)"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(sig(line, 6)), flush=True)
 
 
 def fp32_alu_tflops(sm_mhz=2070.0):
@@ -918,10 +1052,7 @@ def main():
     head, sched, tuned, variants = choose_schedule(index, Yd, Yv_d, exact_v, exact_t, torch, args)
     prec = PRECISIONS[head]
     k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
-    permuted = deannp_variant(index, Yd, Yv_d, exact_v, exact_t, sched[head],
-                              PRECISIONS[head], torch)
-    prec = PRECISIONS[head]
-    k, m, P = sched[head]["k"], sched[head]["m"], sched[head]["nprobe"]
+    permuted = deannp_variant(index, Yd, Yv_d, exact_v, exact_t, sched[head], prec, torch)
 
     # ---- timed region: device-resident inputs -------------------------------
     for w in range(args.warmup):
@@ -964,19 +1095,29 @@ def main():
     for s in range(args.steps):
         out_h = index.query(Yh, k, m, nprobe=P, seed=s, precision=prec)
         _ = float(out_h[0])
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e = {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(nq * d * 4),
-           "d2h_bytes_per_step": int(nq * 4)}
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e = {"value": job_throughput(nq, world, 1e3 * e2e_s), "unit": "queries/s",
+           "h2d_bytes_per_step": int(nq * d * 4), "d2h_bytes_per_step": int(nq * 4)}
 
     # ---- baselines on the same GPU -----------------------------------------
+    peaks, peak_kind = load_peaks()
+    index.profile_read(reset=True)
     ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
+    # the tensor-core path launches three kernels per call (split, MMA, finish)
+    exact_tc = index.profile_read(reset=True)["exact"]["launches"] == 3 * 3
+    # the method's own work is 2 n d flops per query; the tensor-core path runs
+    # six BF16 split products for FP32-level accuracy (x 6 on the tensor pipe)
+    exact_tf = 2.0 * n * d * nq / (ms_exact / 1e3) / 1e12
+    exact = {"qps": nq / (ms_exact / 1e3), "tflops_algorithmic": exact_tf,
+             "frac_algorithmic": exact_tf / peaks["bf16_tflops"],
+             "split_products": 6 if exact_tc else 0,
+             "peak": peaks["bf16_tflops"]}
     # the paper's grid for m: 10 sqrt(2)^i
     rs_m, _ = tune_rs(index, Yv_d, exact_v, [int(round(10 * 2 ** (i / 2))) for i in range(0, 43)])
     ms_rs = time_calls(lambda: index.query_rs(Yd, rs_m, seed=3), 2, torch)
     rs_err = rel_err(index.query_rs(Yd, rs_m, seed=4).cpu().numpy(), exact_t)
 
     # ---- roofline of the dominant stage ------------------------------------
-    peaks, peak_kind = load_peaks()
     stages = {s: v["ms"] / args.steps for s, v in prof.items() if v["timed"]}
     dom = max(stages, key=stages.get)
     C_ivf, assign_ivf = index.export_ivf()
@@ -987,20 +1128,45 @@ def main():
     others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks,
                           peak_kind, sched_key) for s in ("coarse", "scan", "select", "estimate")
               if s in stages}
-    # whole query path: the sum of the stages' times at peak over the step time
+    # whole query path: the sum of the stages' times at peak over the step
+    # time; the method's own bytes only (lists read once, the k neighbours'
+    # and m samples' rows), not the candidate buffer between scan and selection
+    t_alg = (stage_work("estimate", nq, n, d, spec["nlist"], k, m, cbar)[0]
+             + nq * (k * d * 4 + k * 4) + n * d * 2) / (peaks["hbm_gbs"] * 1e9) * 1e3
     path_roof = {"t_min_ms": sum(o["t_min_ms"] for o in others.values()),
-                 "t_measured_ms": ms_step, "mean_candidates": cbar}
+                 "t_alg_ms": t_alg, "t_measured_ms": ms_step, "mean_candidates": cbar}
     path_roof["frac"] = path_roof["t_min_ms"] / ms_step
+    path_roof["frac_alg"] = t_alg / ms_step
     launches = sum(v["launches"] for v in prof.values())
+    emit("stage_rooflines", {"stages": others, "path": path_roof})
+    if tuned:
+        emit("tuning", {"workload": WORKLOAD, "grids": tuned})
+    emit("variants", {"variants": variants, "deannp": permuted})
 
-    extras = forms = None
+    forms = {}
     if args.schedules and rank == 0:
         extras = schedules_and_recall(index, X, Yd, Yv_d, exact_v, sched[head], prec, h, torch,
                                       pkg, dev)
-        forms = differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev)
         extras["nn_contribution"] = nn_contribution_map(torch, pkg, dev)
-        forms["precision_form"] = precision_form(torch, pkg, dev)
-        forms["batched_form"] = batched_form(torch, pkg, dev)
+        emit("schedules", extras)
+        fx = extras["fixed_parameters"]
+        forms["fixed_params_exp"] = sig({"deannp_qps": fx["deannp"]["qps"],
+                                         "deannp_err": fx["deannp"]["test_rel_err"],
+                                         "deann_qps": fx["deann"]["qps"],
+                                         "deann_err": fx["deann"]["test_rel_err"],
+                                         "recall": fx["recall"]})
+        forms["recall"] = sig(extras["recall"]["R"])
+        diff = differentiation_forms(index, X, Yd, k, m, P, prec, h, peaks, torch, pkg, dev)
+        emit("differentiation", diff)
+        forms["adjoint"] = sig({"qps": diff["adjoint"]["qps"], "frac": diff["adjoint"]["frac"]})
+        forms["mean_shift_qsteps"] = sig(diff["mean_shift"]["query_steps_per_s"])
+        full, forms["exponential"] = exponential_form(X, Yd, Yv_d, torch, pkg, dev,
+                                                      spec["nlist"])
+        emit("exponential_form", full)
+        full, forms["d784"] = precision_form(torch, pkg, dev)
+        emit("precision_form", full)
+        full, forms["n4M_batched"] = batched_form(torch, pkg, dev)
+        emit("batched_form", full)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -1008,43 +1174,53 @@ def main():
         qps, cores, done, spent = oracle_sample_rate(X, Y, C.numpy(), assign.numpy(),
                                                      args.kernel, h, k, m, P, args.cpu_budget)
         cpu = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {done} of the {nq} test queries (IVF search from the "
-                         f"exported index + DEANN, FP64), {spent:.1f} s"}
+               "sample": f"first {done} of {nq} test queries, IVF search + DEANN in FP64, "
+                         f"{spent:.1f} s"}
         # one thread, for comparison with the paper's single-core timings
         import oracle
         oracle.set_num_threads(1)
         qps1, _, done1, spent1 = oracle_sample_rate(X, Y, C.numpy(), assign.numpy(), args.kernel,
                                                     h, k, m, P, min(4.0, args.cpu_budget))
         oracle.set_num_threads(cores)
-        cpu["single_thread"] = {"value": qps1, "unit": "queries/s", "cores": 1,
-                                "sample": f"first {done1} test queries, {spent1:.1f} s"}
+        cpu["single_thread_qps"] = qps1
 
+    roof_short = {key: roof[key] for key in ("bound", "achieved", "peak", "unit", "frac",
+                                             "traffic", "stage", "ms_per_call", "t_min_ms")}
+    roof_short["peak_source"] = roof["peak_source"]
     line = {
         "metric": "kde_queries_per_s_at_1e-2_mean_rel_err", "value": value, "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": d, "nq": nq, "kernel": args.kernel,
-                   "h": h, "val_mean_kde": mu_val, "nlist": spec["nlist"], "k": k, "m": m,
+        "config": {"workload": WORKLOAD, "kernel": args.kernel, "h": h, "k": k, "m": m,
                    "nprobe": P, "scan_precision": head, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (X is 512 MB)"},
+                   "l2": "inputs > L2 (X 512 MB)"},
         "mean_rel_err": statistics.mean(errs), "max_step_rel_err": max(errs),
-        "meets_target": max(errs) <= TARGET_ERR,
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
-        "stage_ms_per_step": stages, "stage_rooflines": others, "path_roofline": path_roof,
+        "meets_target": max(errs) <= TARGET_ERR, "val_rel_err": sched[head]["val_err"],
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof_short,
+        "stage_ms_per_step": stages,
+        "path_roofline": {key: path_roof[key] for key in ("frac", "frac_alg", "t_min_ms",
+                                                          "t_alg_ms")},
         "cpu_baseline": cpu,
-        "build_s": build_s, "variants": variants, "deannp": permuted, "schedules": extras,
-        "forms": forms,
-        "baselines": {"exact_qps": nq / (ms_exact / 1e3), "rs_qps": nq / (ms_rs / 1e3),
-                      "rs_m": rs_m, "rs_rel_err": rs_err},
-        "margin_failures": index.margin_failures(),
-        "tuning": tuned,
+        "baselines": {"exact": exact, "rs_qps": nq / (ms_rs / 1e3), "rs_m": rs_m,
+                      "rs_rel_err": rs_err, "fp32_scan": row(variants["fp32"]["k"],
+                                                             variants["fp32"]["m"],
+                                                             variants["fp32"]["nprobe"],
+                                                             variants["fp32"]["qps"],
+                                                             variants["fp32"]["test_rel_err"]),
+                      "deannp": row(permuted["k"], permuted["m"], permuted["nprobe"],
+                                    permuted["qps"], permuted["test_rel_err"])},
+        "forms": forms, "row_fields": ROW_FIELDS, "margin_failures": index.margin_failures(),
+        "build_s": build_s,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     index.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    if rank == 0:
+        text, moved = fit_headline(sig(line, 4))
+        if moved:
+            emit("headline_overflow", moved)
+        print(text, flush=True)
 
 
 if __name__ == "__main__":

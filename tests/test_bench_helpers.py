@@ -122,3 +122,66 @@ def test_clock_samples_of_the_timed_region(tmp_path):
     got = c.stop()
     assert got["samples_in_region"] == 0 and got["samples"] == 5
     assert got["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def _representative_headline():
+    """A headline line with every section bench.py fills, at realistic sizes."""
+    r = bench.row(1536, 4000, 8, 1.9e6, 9.0e-3)
+    return bench.sig({
+        "metric": "kde_queries_per_s_at_1e-2_mean_rel_err", "value": 1.94e6,
+        "unit": "queries/s", "n_gpus": 1, "steps": 20, "warmup": 5, "ms_per_step": 5.15,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": bench.WORKLOAD, "kernel": "gaussian", "h": 12.806247, "k": 1536,
+                   "m": 4000, "nprobe": 8, "scan_precision": "bf16",
+                   "parallelism": "replicas x1", "l2": "inputs > L2 (X 512 MB)"},
+        "mean_rel_err": 0.0090123, "max_step_rel_err": 0.0091234, "meets_target": True,
+        "val_rel_err": 0.0087654,
+        "e2e": {"value": 1.91e6, "unit": "queries/s", "h2d_bytes_per_step": 5120000,
+                "d2h_bytes_per_step": 40000},
+        "gpu_launches": 480,
+        "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 7, "samples_in_region": 7, "samples_total": 500},
+        "roofline": {"bound": "hbm", "achieved": 7412.3456, "peak": 6781.4, "unit": "GB/s",
+                     "frac": 1.0930123, "traffic": 17212345678, "stage": "estimate",
+                     "ms_per_call": 2.7712345, "t_min_ms": 3.0212345,
+                     "peak_source": "measured hbm_gbs"},
+        "stage_ms_per_step": {s: 1.2345678 for s in ("stage", "coarse", "plan", "scan",
+                                                     "select", "estimate")},
+        "path_roofline": {"frac": 0.8912345, "frac_alg": 0.7812345, "t_min_ms": 4.5712345,
+                          "t_alg_ms": 4.0012345},
+        "cpu_baseline": {"value": 1321.12345, "unit": "queries/s", "cores": 16, "kind": "oracle",
+                         "sample": "first 16384 of 10000 test queries, IVF search + DEANN in "
+                                   "FP64, 12.3 s", "single_thread_qps": 72.512345},
+        "baselines": {"exact": {"qps": 551234.5, "tflops_algorithmic": 141.23456,
+                                "frac_algorithmic": 0.0741234, "split_products": 6,
+                                "peak": 1901.8},
+                      "rs_qps": 12612.345, "rs_m": 1310720, "rs_rel_err": 0.0089123,
+                      "fp32_scan": r, "deannp": r},
+        "forms": {"fixed_params_exp": {"deannp_qps": 2.5e6, "deannp_err": 0.036,
+                                       "deann_qps": 2.1e6, "deann_err": 0.04, "recall": 0.83},
+                  "recall": 0.9912345, "adjoint": {"qps": 2.02e6, "frac": 0.84123},
+                  "mean_shift_qsteps": 6.8e6, "exponential": {"row": r, "exact_qps": 91234.5},
+                  "d784": {"exact_qps": 121234.0, "fp32_fixed": r, "fp32": r, "bf16_fixed": r,
+                           "bf16": r, "same_nbrs": True},
+                  "n4M_batched": {"fixed": r, "tuned": r,
+                                  "one_call_qps": [1.45123e6, 1.41234e6]}},
+        "row_fields": bench.ROW_FIELDS, "margin_failures": 0, "build_s": 3.2123456,
+    }, 4)
+
+
+def test_headline_line_fits_the_driver_tail():
+    """The full headline, with every summary, fits in the 2,700 bytes kept for
+    it; when it would not, optional sections move to a side line and the
+    required keys stay."""
+    line = _representative_headline()
+    text, moved = bench.fit_headline(line)
+    assert moved == {} and len(text) <= bench.HEADLINE_LIMIT, len(text)
+    text, moved = bench.fit_headline(line, limit=1500)
+    assert len(text) <= 1500 and "forms" in moved
+    import json
+    got = json.loads(text)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "dtype", "config", "e2e", "clocks", "roofline",
+                "cpu_baseline", "gpu_launches"):
+        assert key in got
