@@ -168,7 +168,8 @@ kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, i
  *   m      >= 0 (m = 0 keeps only the neighbours' exact contribution);
  *   nprobe 1 <= nprobe <= min(nlist, 256) (ignored when k = 0).
  *   out    nq estimates (FP32).
- *   nbr    NULL, or nq x k receiving the neighbour ids that were used.
+ *   nbr    NULL, or nq x k receiving the neighbour ids that were used (the
+ *          set X_1, in no particular order; -1 pads).
  * With opts.dev_active_rows only the rows below the device count are served
  * (a CUDA graph captured at a fixed capacity serving a smaller batch). */
 kde_status kde_query(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t m,
@@ -300,8 +301,10 @@ kde_status kde_sync(kde_index* index, const kde_opts* opts);
 kde_status kde_stats(kde_index* index, int64_t* margin_failures, const kde_opts* opts);
 
 /* kde_reserve -- pre-allocate scratch for calls with up to nq queries and the
- * given k, m, nprobe, so that later calls allocate nothing (required before
- * capturing calls into a CUDA graph). */
+ * given k, m, nprobe at opts->precision, so that later calls allocate nothing
+ * (required before capturing calls into a CUDA graph).  A later call that
+ * needs more scratch allocates a larger buffer; the outgrown one is kept
+ * until kde_free, so graphs captured before stay valid. */
 kde_status kde_reserve(kde_index* index, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
                        const kde_opts* opts);
 

@@ -264,10 +264,10 @@ class KDEIndex:
         return {name: dict(ms=p.ms[i], timed=p.timed[i], calls=p.calls[i],
                            launches=p.launches[i]) for i, name in enumerate(STAGES)}
 
-    def reserve(self, nq, k=0, m=0, nprobe=1):
+    def reserve(self, nq, k=0, m=0, nprobe=1, precision=0):
         with torch.cuda.device(self._device):
             _check(_lib.kde_reserve(self._h, int(nq), int(k), int(m), int(nprobe),
-                                    ctypes.byref(self._opts())))
+                                    ctypes.byref(self._opts(precision))))
 
     # -- the path ------------------------------------------------------------
     def search(self, Y, k, nprobe=1, precision=0):
@@ -447,7 +447,7 @@ class GraphedQuery:
         # no active row until a batch arrives: the warm-up call below only loads
         # the kernels (its rows would be zero vectors)
         self.active = torch.zeros(1, dtype=torch.int64, device=dev)
-        index.reserve(self.capacity, k, m, nprobe)
+        index.reserve(self.capacity, k, m, nprobe, precision)
         args = dict(k=k, m=m, nprobe=nprobe, seed=seed, precision=precision,
                     sample_mode=sample_mode, dev_qid=self.qid, dev_active=self.active,
                     return_neighbors=self.neighbors)
@@ -486,6 +486,12 @@ class BatchServer:
                                             precision=precision, sample_mode=sample_mode,
                                             neighbors=neighbors)
         self.max_batch = int(max_batch)
+        # the scratch for the largest capacity class up front, so that every
+        # graph is captured on the same buffer
+        cap = 16
+        while cap < self.max_batch:
+            cap *= 2
+        index.reserve(cap, k, m, nprobe, precision)
         self.graphs = {}
         self.next_qid = 0
         self.last_qid = 0

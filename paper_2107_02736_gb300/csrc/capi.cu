@@ -94,15 +94,16 @@ kde_status ensure_scratch(kde_index* ix, size_t bytes) {
   if (bytes > ix->scratch_limit)
     return fail(KDE_ENOMEM, "call needs %zu bytes of scratch, above the limit %zu", bytes,
                 ix->scratch_limit);
-  CK(cudaDeviceSynchronize());
-  if (ix->scratch.base) cudaFree(ix->scratch.base);
-  ix->scratch.base = nullptr;
-  ix->scratch.cap = 0;
+  // The outgrown buffer is retired, not freed: CUDA graphs captured from
+  // earlier calls hold its addresses and stay valid until kde_free.
   const size_t cap = std::max(bytes, size_t(64) << 20);
-  if (cudaMalloc(&ix->scratch.base, cap) != cudaSuccess) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, cap) != cudaSuccess) {
     cudaGetLastError();
     return fail(KDE_ENOMEM, "cudaMalloc of %zu scratch bytes failed", cap);
   }
+  if (ix->scratch.base) ix->retired.push_back(ix->scratch.base);
+  ix->scratch.base = static_cast<char*>(p);
   ix->scratch.cap = cap;
   return KDE_OK;
 }
@@ -180,15 +181,22 @@ struct SearchBufs {
   int64_t* pair_dst = nullptr;
   int64_t *ord_cnt = nullptr, *ord_off = nullptr, *ord_fill = nullptr;
   int32_t* order = nullptr;
-  float* cand = nullptr;
+  float* cand = nullptr;   // FP32 scan: every candidate's distance
+  TwoPass tp;              // BF16 scan: the two-pass selection's state
 };
 
-constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of queries
+constexpr size_t kCandCap = size_t(8) << 30;  // search scratch per chunk of queries
 
-void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
+void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, int precision,
+                  SearchBufs& s) {
   const int L = ix->nlist;
-  // each (query, probe) candidate segment is padded to a multiple of 32 floats
-  const size_t per_q = ((size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32)) * sizeof(float);
+  const bool two_pass = precision == KDE_PREC_BF16;
+  // FP32 scan: each (query, probe) candidate segment is padded to a multiple
+  // of 32 floats; BF16 scan: a histogram and kSelectCap keys per query
+  const size_t per_q =
+      (two_pass ? 2 * sizeof(uint32_t) * kHistBins + sizeof(unsigned long long) * kSelectCap + 64
+                : (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32) * sizeof(float)) +
+      sizeof(float) * (size_t)L;
   int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
   qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
   s.qc = qc;
@@ -210,7 +218,26 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.ord_off = b.take<int64_t>(L + 1);
   s.ord_fill = b.take<int64_t>(L);
   s.order = b.take<int32_t>(qc);
-  s.cand = b.take<float>((size_t)qc * (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
+  if (two_pass) {
+    s.tp.hlo = b.take<float>(qc);
+    s.tp.hscale = b.take<float>(qc);
+    s.tp.E = b.take<float>(qc);
+    s.tp.thr = b.take<float>(qc);
+    s.tp.bstar = b.take<int32_t>(qc);
+    s.tp.cntA = b.take<int32_t>(qc);
+    s.tp.cntB = b.take<int32_t>(qc);
+    s.tp.rbin = b.take<int32_t>(qc);
+    s.tp.flo = b.take<float>(qc);
+    s.tp.fscale = b.take<float>(qc);
+    s.tp.k2 = b.take<int32_t>(qc);
+    s.tp.fstar = b.take<int32_t>(qc);
+    s.tp.hist = b.take<uint32_t>((size_t)qc * kHistBins);
+    s.tp.hist2 = b.take<uint32_t>((size_t)qc * kHistBins);
+    s.tp.keys = b.take<unsigned long long>((size_t)qc * kSelectCap);
+  } else {
+    s.cand = b.take<float>((size_t)qc * (size_t)P *
+                           ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
+  }
 }
 
 struct CallBufs {
@@ -256,6 +283,7 @@ struct CallShape {
   bool exact_tc = false;   // tensor-core exact: BF16 parts of the queries
   bool window = false;     // permuted-window estimator (sample_mode 2)
   int fit_k = -1;          // >= 0: bandwidth fitting with fit_k search neighbours
+  int precision = 0;       // scan precision of the search (its scratch differs)
 };
 
 void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -292,7 +320,7 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
     cb.fit_nbr = b.take<int32_t>((size_t)nq * std::max(c.fit_k, 1));
     cb.fit_red = b.take<double>(4);
   }
-  if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
+  if (c.search) carve_search(b, ix, c.nq, c.P, c.precision, cb.search);
 }
 
 kde_status prepare_call(kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -345,11 +373,14 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       return fail(KDE_ECUDA, "the BF16 tensor map could not be encoded on this driver");
     const int qtile = tcore ? scan_tc_bn(ix->dpb) : kTile;
     {
-      StageTimer t(ix, ST_PLAN, st, 9);
+      StageTimer t(ix, ST_PLAN, st, tcore ? 6 : 9);
       launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_real, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
                         s.tile_cnt, s.tile_off, ix->lorder, qtile, st);
-      launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
+      // the FP32 path's selection rescoring reads rows per query: run queries
+      // grouped by their nearest list (the BF16 path rescored inside the scan)
+      if (!tcore)
+        launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
     }
     ScanPlan plan;
     plan.pair_q = s.pair_q;
@@ -358,11 +389,22 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     plan.tile_off = s.tile_off;
     plan.lorder = ix->lorder;
     plan.max_tiles = (nc * P + qtile - 1) / qtile + L;
+    const float err_scale = scan_err_scale(ix->dp, precision);
     if (tcore) {
-      StageTimer t(ix, ST_SCAN, st, 1);
-      if (!launch_scan_tc(ix->tmap_xlb, Yc, ix->C, ix->dp, ix->XLcn, ix->list_off, L, ix->dpb,
-                          qtile, plan, s.cand, ix->err, st))
-        return fail(KDE_ECUDA, "could not configure the tensor-core scan kernel");
+      // passes of the tensor-core scan: histograms, threshold, sub-bins of
+      // crowded k-th bins, threshold, then the in-band candidates rescored in
+      // FP32 and emitted as keys
+      StageTimer t(ix, ST_SCAN, st, 6);
+      TwoPass tp = s.tp;
+      tp.kA = k;
+      launch_search_bounds(s.probes, s.probe_d2, ix->rad, nc, P, err_scale, active, q0, tp, st);
+      for (int mode : {(int)kScanHist, (int)kScanRefine, (int)kScanEmit}) {
+        if (mode == kScanRefine) launch_search_threshold(s.q_real, nc, k, 0, tp, st);
+        if (mode == kScanEmit) launch_search_threshold(s.q_real, nc, k, 1, tp, st);
+        if (!launch_scan_tc(mode, ix->tmap_xlb, Yc, ix->C, ix->dp, ix->XLcn, ix->list_off, L,
+                            ix->dpb, qtile, plan, nullptr, tp, ix->XL, ix->perm, ix->err, st))
+          return fail(KDE_ECUDA, "could not configure the tensor-core scan kernel");
+      }
     } else {
       StageTimer t(ix, ST_SCAN, st, 1);
       launch_scan_simt(Yc, Ync, ix->XL, ix->XLn, ix->list_off, L, ix->dp, plan, s.cand, st);
@@ -394,7 +436,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.k = k;
     a.kern = ix->kern;
     a.h = ix->h;
-    a.err_scale = scan_err_scale(ix->dp, precision);
+    a.err_scale = err_scale;
     a.nbr = nbr + q0 * k;
     a.nd2 = nd2 ? nd2 + q0 * k : nullptr;
     a.s1 = s1 ? s1 + q0 : nullptr;
@@ -404,7 +446,13 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.centered = tcore ? 1 : 0;
     a.ids_only = ids_only && nd2 == nullptr ? 1 : 0;
     a.err = ix->err;
-    launch_select_neighbors(a, st);
+    if (tcore) {
+      TwoPass tp = s.tp;
+      tp.kA = k;
+      launch_select_compact(a, tp, st);
+    } else {
+      launch_select_neighbors(a, st);
+    }
   }
   CK(cudaGetLastError());
   return KDE_OK;
@@ -747,6 +795,7 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->wpinv);
   cudaFree(ix->XP);
   if (ix->scratch.base) cudaFree(ix->scratch.base);
+  for (char* p : ix->retired) cudaFree(p);
   for (const auto& e : ix->events) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -844,6 +893,7 @@ kde_status kde_search(kde_index* ix, const float* Y, int64_t nq, int32_t k, int3
   c.k = k;
   c.P = nprobe;
   c.search = true;
+  c.precision = o->precision;
   c.host = host;
   c.need_nbr = host;
   c.need_nd2 = host && d2 != nullptr;
@@ -898,6 +948,7 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
+  c.precision = o->precision;
   c.host = host;
   c.need_out = host;
   c.need_nbr = k > 0 && (host || nbr == nullptr);
@@ -1152,6 +1203,7 @@ kde_status kde_grad(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32_
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
+  c.precision = o->precision;
   c.host = host;
   c.need_nbr = k > 0;
   c.need_out = true;
@@ -1217,6 +1269,7 @@ kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, in
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
+  c.precision = o->precision;
   c.host = host;
   c.need_out = true;
   c.need_nbr = k > 0;
@@ -1289,6 +1342,7 @@ kde_status kde_fit_bandwidth(kde_index* ix, const int32_t* zid, int64_t nz, int3
   c.m = m;
   c.P = std::max(1, nprobe);
   c.search = k > 0;
+  c.precision = o->precision;
   c.host = true;
   c.need_out = true;
   c.need_nbr = true;
@@ -1401,11 +1455,13 @@ kde_status kde_profile_read(kde_index* ix, kde_profile* out, int32_t reset,
 kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
                        const kde_opts* opts) {
   TRY(check_index(ix));
-  (void)opts;
+  const kde_opts* o = opts ? opts : &kDefaultOpts;
+  TRY(check_opts(o));
   DeviceGuard g(ix->device);
   size_t need = 0;
   for (int variant = 0; variant < 4; ++variant) {
     CallShape c;
+    c.precision = o->precision;  // the search's scratch depends on the scan precision
     c.nq = nq;
     c.k = k;
     c.m = m;

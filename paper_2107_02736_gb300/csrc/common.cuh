@@ -102,6 +102,12 @@ __device__ __forceinline__ uint32_t dist_key(float v) {
   return __float_as_uint(v);
 }
 
+// (distance, id) as one 64-bit key whose unsigned order is the (distance,
+// id) lexicographic order.
+__device__ __forceinline__ unsigned long long pack_key(float d2, int id) {
+  return ((unsigned long long)dist_key(d2) << 32) | (unsigned)id;
+}
+
 // Distance of one row pair computed by G lanes cooperatively, in difference
 // form with compensated summation: each lane splits x - y into an FP32 value
 // and its exact rounding error (TwoSum), accumulates the squares with their

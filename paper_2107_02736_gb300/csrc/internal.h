@@ -110,6 +110,7 @@ struct kde_index {
   float xmax = 0.f;           // max |x| over the dataset
   int64_t margin_failures = 0;
   deann::Arena scratch;
+  std::vector<char*> retired;  // outgrown scratch buffers, freed by kde_free
   size_t scratch_limit = size_t(16) << 30;
   // per-stage profiling (CUDA events on the call's stream) and launch counts
   static constexpr int kStages = 8;
@@ -173,12 +174,57 @@ void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const fl
                       const int64_t* list_off, int L, int dp, const ScanPlan& plan, float* cand,
                       cudaStream_t s);
 
+// ---- two-pass selection of the BF16 scan (tc_scan.cu, select.cu) ----------
+// Pass 1 bins every candidate's approximate distance into a per-query
+// histogram over bounds from the probed lists' radii; the threshold kernel
+// finds the bin b* of the k-th smallest and the band edge thr = (upper edge of
+// b*) + 2E; pass 2 recomputes the distances and rescores in FP32 difference
+// form only the candidates in bins below b* (region A, certainly in the top
+// k) or at most thr (region B), writing (distance, id) keys; the compact
+// selection ranks those keys.
+// A query whose k-th bin holds more than kRefineMin candidates gets a second
+// histogram pass over that bin alone (kHistBins sub-bins), so that the band
+// past the k-th sub-bin stays narrow where many candidates lie at nearly the
+// same distance.
+constexpr int kHistBins = 128;
+constexpr int kRefineMin = 64;
+struct TwoPass {
+  float* hlo = nullptr;           // [nq] histogram lower bound
+  float* hscale = nullptr;        // [nq] bins per unit of squared distance (0: one bin)
+  float* E = nullptr;             // [nq] error bound of the scan's distances
+  uint32_t* hist = nullptr;       // [nq x kHistBins]
+  uint32_t* hist2 = nullptr;      // [nq x kHistBins] sub-bins of the refined bin
+  float* thr = nullptr;           // [nq] band edge
+  int32_t* bstar = nullptr;       // [nq] bin of the k-th smallest (kHistBins: take all)
+  int32_t* rbin = nullptr;        // [nq] the refined bin (b*), or -1
+  float* flo = nullptr;           // [nq] sub-bin lower bound
+  float* fscale = nullptr;        // [nq] sub-bins per unit
+  int32_t* k2 = nullptr;          // [nq] rank of the k-th within bin b*
+  int32_t* fstar = nullptr;       // [nq] sub-bin of the k-th (refined queries)
+  int32_t* cntA = nullptr;        // [nq] keys emitted to region A
+  int32_t* cntB = nullptr;        // [nq] keys emitted to region B
+  unsigned long long* keys = nullptr;  // [nq x kSelectCap]: A at [0, kA), B at [kA, cap)
+  int kA = 0;                     // capacity of region A (= k)
+};
+// hist_bin of an approximate squared distance: the same arithmetic in both
+// passes, so a candidate lands in the same bin each time.
+__host__ __device__ inline int hist_bin(float a, float lo, float scale) {
+  if (!(scale > 0.f)) return 0;
+  const float t = (a - lo) * scale;
+  if (!(t >= 0.f)) return 0;
+  return t >= (float)kHistBins ? kHistBins - 1 : (int)t;
+}
+
 // ---- tc_scan.cu (tcgen05 BF16 scan) ----------------------------------------
+enum ScanMode { kScanCand = 0, kScanHist = 1, kScanEmit = 2, kScanRefine = 3 };
 int scan_tc_bn(int dpb);                    // queries per CTA for a given row width
 bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb);
-bool launch_scan_tc(const void* tmap, const float* Yp, const float* C, int dp, const float* XLcn,
-                    const int64_t* list_off, int L, int dpb, int BN, const ScanPlan& plan,
-                    float* cand, uint32_t* err, cudaStream_t s);
+// kScanCand: every candidate's approximate distance into cand (segments);
+// kScanHist / kScanRefine / kScanEmit: the passes above (tp, XL, perm used).
+bool launch_scan_tc(int mode, const void* tmap, const float* Yp, const float* C, int dp,
+                    const float* XLcn, const int64_t* list_off, int L, int dpb, int BN,
+                    const ScanPlan& plan, float* cand, const TwoPass& tp, const float* XL,
+                    const int32_t* perm, uint32_t* err, cudaStream_t s);
 
 // ---- tc_exact.cu (tcgen05 exact KDE, three-way BF16 split) -----------------
 void launch_col_mean(const float* X, int64_t n, int dp, float* mean, cudaStream_t s);
@@ -242,6 +288,17 @@ struct SelectArgs {
   uint32_t* err;
 };
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s);
+// Two-pass selection: per-query histogram bounds and E (zeroes the histogram
+// and counters), the threshold after pass 1, and the ranking of the keys
+// pass 2 wrote (a.cand and the segment fields unused).
+void launch_search_bounds(const int32_t* probes, const float* probe_d2, const float* rad,
+                          int64_t nq, int P, float err_scale, const int64_t* active, int64_t q0,
+                          const TwoPass& tp, cudaStream_t s);
+// stage 0 after the histogram pass (b*, the band edge, which queries to
+// refine); stage 1 after the refinement pass (the k-th sub-bin, the edge)
+void launch_search_threshold(const int64_t* q_real, int64_t nq, int k, int stage,
+                             const TwoPass& tp, cudaStream_t s);
+void launch_select_compact(const SelectArgs& a, const TwoPass& tp, cudaStream_t s);
 
 // ---- sample.cu --------------------------------------------------------------
 struct SampleArgs {

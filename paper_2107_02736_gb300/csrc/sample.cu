@@ -628,25 +628,29 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
     const int myrow = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
     const float4 yv = lane < dp4 ? y4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* X4 = reinterpret_cast<const float4*>(X);
+    // the rows' differences are formed twice (for the distances, then for
+    // the gradient after the reduction) from loads of the same addresses, the
+    // second served by L1, so only the row ids stay live across the shuffles
+    auto row_diff = [&](int rid) {
+      const float4 xv = rid >= 0 && lane < dp4 ? __ldg(X4 + (size_t)rid * dp4 + lane) : yv;
+      return make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
+    };
     for (int wb = warp * 8; wb < cnt; wb += kNW * 8) {
       prefetch_next_rows(X, dp, ids, cnt, wb + kNW * 8);
-      float4 diff[8];
+      int rid[8];
       float acc[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int rid = wb + u < cnt ? ids[wb + u] : -1;
-        const float4 xv = rid >= 0 && lane < dp4 ? __ldg(X4 + (size_t)rid * dp4 + lane) : yv;
-        diff[u] = make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
-      }
+      for (int u = 0; u < 8; ++u) rid[u] = wb + u < cnt ? ids[wb + u] : -1;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
+        const float4 df = row_diff(rid[u]);
         if (kern == KDE_KERN_LAPLACIAN) {
-          acc[u] = (fabsf(diff[u].x) + fabsf(diff[u].y)) + (fabsf(diff[u].z) + fabsf(diff[u].w));
+          acc[u] = (fabsf(df.x) + fabsf(df.y)) + (fabsf(df.z) + fabsf(df.w));
         } else {
-          float t = diff[u].x * diff[u].x;
-          t = fmaf(diff[u].y, diff[u].y, t);
-          t = fmaf(diff[u].z, diff[u].z, t);
-          acc[u] = fmaf(diff[u].w, diff[u].w, t);
+          float t = df.x * df.x;
+          t = fmaf(df.y, df.y, t);
+          t = fmaf(df.z, df.z, t);
+          acc[u] = fmaf(df.w, df.w, t);
         }
       }
       float v4[4], v2[2], dist;
@@ -688,16 +692,17 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const float c = __shfl_sync(0xffffffffu, coef, ((u >> 2) << 4) | (((u >> 1) & 1) << 3) | ((u & 1) << 2));
+        const float4 df = row_diff(rid[u]);
         if (kern == KDE_KERN_LAPLACIAN) {
-          gacc[0].x += c * (diff[u].x > 0.f ? 1.f : (diff[u].x < 0.f ? -1.f : 0.f));
-          gacc[0].y += c * (diff[u].y > 0.f ? 1.f : (diff[u].y < 0.f ? -1.f : 0.f));
-          gacc[0].z += c * (diff[u].z > 0.f ? 1.f : (diff[u].z < 0.f ? -1.f : 0.f));
-          gacc[0].w += c * (diff[u].w > 0.f ? 1.f : (diff[u].w < 0.f ? -1.f : 0.f));
+          gacc[0].x += c * (df.x > 0.f ? 1.f : (df.x < 0.f ? -1.f : 0.f));
+          gacc[0].y += c * (df.y > 0.f ? 1.f : (df.y < 0.f ? -1.f : 0.f));
+          gacc[0].z += c * (df.z > 0.f ? 1.f : (df.z < 0.f ? -1.f : 0.f));
+          gacc[0].w += c * (df.w > 0.f ? 1.f : (df.w < 0.f ? -1.f : 0.f));
         } else {
-          gacc[0].x = fmaf(c, diff[u].x, gacc[0].x);
-          gacc[0].y = fmaf(c, diff[u].y, gacc[0].y);
-          gacc[0].z = fmaf(c, diff[u].z, gacc[0].z);
-          gacc[0].w = fmaf(c, diff[u].w, gacc[0].w);
+          gacc[0].x = fmaf(c, df.x, gacc[0].x);
+          gacc[0].y = fmaf(c, df.y, gacc[0].y);
+          gacc[0].z = fmaf(c, df.z, gacc[0].z);
+          gacc[0].w = fmaf(c, df.w, gacc[0].w);
         }
       }
     }
@@ -765,20 +770,19 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
   }
 }
 
+// Narrow rows (NV <= 2: d <= 256) run four CTAs per SM within 64 registers a
+// thread; wider ones keep their NV float4 accumulators at two CTAs per SM.
 template <int G, int NV>
-__global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
+__global__ void __launch_bounds__(kNT, NV <= 2 ? 4 : 2) k_estimate_grad(SampleArgs a) {
   __shared__ EstSmem sm;
   __shared__ int tmp[kMaxK];
   extern __shared__ float4 dyn4[];
   float* ys = reinterpret_cast<float*>(dyn4);
-  float* gsum = ys + a.dp;
+  float* gpart = ys + a.dp;  // [kNT / G][dp]: each lane group's partial gradient
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x;
   const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
-  for (int j = tid; j < a.dp; j += kNT) {
-    ys[j] = a.Y[q * a.dp + j];
-    gsum[j] = 0.f;
-  }
+  for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;
   if (k > 0) {
     load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
@@ -855,18 +859,15 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
       __syncthreads();
     }
   }
-  // combine the groups' d-vectors
+  // combine the groups' d-vectors in a fixed order (group 0 first), so that
+  // the gradient is the same bits on every run
   const int lig = tid & (G - 1);
   const int dp4 = a.dp >> 2;
+  float4* mine = reinterpret_cast<float4*>(gpart + (size_t)(tid / G) * a.dp);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int j4 = lig + v * G;
-    if (j4 < dp4) {
-      atomicAdd(gsum + 4 * j4 + 0, gacc[v].x);
-      atomicAdd(gsum + 4 * j4 + 1, gacc[v].y);
-      atomicAdd(gsum + 4 * j4 + 2, gacc[v].z);
-      atomicAdd(gsum + 4 * j4 + 3, gacc[v].w);
-    }
+    if (j4 < dp4) mine[j4] = gacc[v];
   }
   const float est_t = block_sum(est, sm);
   const float sl_t = block_sum(sl, sm);
@@ -881,7 +882,11 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
     for (int j = tid; j < a.d; j += kNT) a.dY[q * a.d + j] = __int_as_float(0x7fc00000);
     return;
   }
-  for (int j = tid; j < a.d; j += kNT) a.dY[q * a.d + j] = go * gsum[j];
+  for (int j = tid; j < a.d; j += kNT) {
+    float g = 0.f;
+    for (int grp = 0; grp < kNT / G; ++grp) g += gpart[(size_t)grp * a.dp + j];
+    a.dY[q * a.d + j] = go * g;
+  }
   if (tid == 0) {
     if (a.out) a.out[q] = est_t;
     if (a.dlogh) a.dlogh[q] = go * sl_t;
@@ -1037,25 +1042,34 @@ void launch_mean_shift_update(float* Yp, int dp, int d, const float* dY, const f
                                                                       h * h);
 }
 
+// static shared memory plus the partial gradients can pass the 48 KB default
+// (d = 1024: 65 KB), so the limit is raised per launch
+template <int G, int NV>
+void launch_grad_inst(const SampleArgs& a, unsigned grid, size_t dyn, cudaStream_t s) {
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_estimate_grad<G, NV>), dyn);
+  k_estimate_grad<G, NV><<<grid, kNT, dyn, s>>>(a);
+}
+
 void launch_estimate_grad(const SampleArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
-  const size_t dyn = sizeof(float) * 2 * a.dp;
   const unsigned grid = (unsigned)a.nq;
   const int G = group_lanes(a.dp);
+  // the staged query and one partial gradient per lane group (<= 36 KB at d = 1024)
+  const size_t dyn = sizeof(float) * (size_t)a.dp * (1 + kNT / G);
   const int dp4 = a.dp / 4;
   if (G < 32) {  // d <= 64: shorter lane groups (measured faster than the warp-wide path)
     switch (G) {
-      case 4: k_estimate_grad<4, 1><<<grid, kNT, dyn, s>>>(a); break;
-      case 8: k_estimate_grad<8, 1><<<grid, kNT, dyn, s>>>(a); break;
-      default: k_estimate_grad<16, 1><<<grid, kNT, dyn, s>>>(a); break;
+      case 4: launch_grad_inst<4, 1>(a, grid, dyn, s); break;
+      case 8: launch_grad_inst<8, 1>(a, grid, dyn, s); break;
+      default: launch_grad_inst<16, 1>(a, grid, dyn, s); break;
     }
     return;
   }
   const int nv = (dp4 + 31) / 32;
-  if (nv <= 1) k_estimate_grad<32, 1><<<grid, kNT, dyn, s>>>(a);
-  else if (nv <= 2) k_estimate_grad<32, 2><<<grid, kNT, dyn, s>>>(a);
-  else if (nv <= 4) k_estimate_grad<32, 4><<<grid, kNT, dyn, s>>>(a);
-  else k_estimate_grad<32, 8><<<grid, kNT, dyn, s>>>(a);
+  if (nv <= 1) launch_grad_inst<32, 1>(a, grid, dyn, s);
+  else if (nv <= 2) launch_grad_inst<32, 2>(a, grid, dyn, s);
+  else if (nv <= 4) launch_grad_inst<32, 4>(a, grid, dyn, s);
+  else launch_grad_inst<32, 8>(a, grid, dyn, s);
 }
 
 }  // namespace deann

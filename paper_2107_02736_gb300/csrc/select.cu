@@ -418,9 +418,6 @@ __device__ void block_sort_keys(SM& sm, int cnt) {
   }
 }
 
-__device__ __forceinline__ unsigned long long pack_key(float d2, int id) {
-  return ((unsigned long long)dist_key(d2) << 32) | (unsigned)id;
-}
 
 // --------------------------------------------------------------------------
 // Probe selection: nprobe nearest centroids (ties to the lower id).
@@ -647,6 +644,215 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
   if (tid == 1023) out[count] = part[1023];
 }
 
+// Ranks the K FP32-rescored keys in sm.key (distance key << 32 | id; ~0 for
+// an empty slot) of query q and writes its outputs: the k nearest (as a set
+// with s1 on the query path, else sorted with their distances), k' and s1.
+// Only candidates inside the FP32 error band of the k-th distance are
+// re-ranked with compensated distances.  Called by the whole block after a
+// barrier.
+__device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
+                          const float* __restrict__ y) {
+  __shared__ float s_red[kNW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.ids_only && K > a.k && a.kern != KDE_KERN_LAPLACIAN) {
+    // The query path needs the set and s1, not the order: find the k-th
+    // smallest rescored distance T, take every candidate clearly below it,
+    // and rank only those within the FP32 error band of T by compensated
+    // distance.
+    const int k = a.k;
+    const float T = __uint_as_float(smem_kth_dist(sm, K, k));
+    const float bw = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T;
+    const uint32_t lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
+    const uint32_t hi_key = dist_key(T + bw);
+    unsigned long long* amb = reinterpret_cast<unsigned long long*>(sm.slot);  // 1024 keys
+    const float inv = kernel_inv(a.kern, a.h);
+    // s1 is summed in 64-bit fixed point with its unit 2^-52 of the largest
+    // term (the nearest candidate's kernel value), so that the sum does not
+    // depend on the order in which the keys arrived: integer addition is
+    // associative.  Each term is truncated by less than 2^-51 of the largest.
+    __shared__ unsigned long long s_mn[kNW], s_fx[kNW];
+    unsigned long long mn = ~0ull;
+    for (int j = tid; j < K; j += kNT) mn = min(mn, sm.key[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (lane == 0) s_mn[warp] = mn;
+    __syncthreads();
+    mn = s_mn[0];
+    for (int w = 1; w < kNW; ++w) mn = min(mn, s_mn[w]);
+    int ex = 0;
+    frexpf(kernel_from_dist(a.kern, __uint_as_float((uint32_t)(mn >> 32)), inv), &ex);
+    const int fx_shift = 52 - ex;  // every term is below 2^ex: its fixed value below 2^52
+    unsigned long long part = 0ull;
+    auto add_term = [&](uint32_t dk) {
+      part += (unsigned long long)ldexpf(kernel_from_dist(a.kern, __uint_as_float(dk), inv),
+                                         fx_shift);
+    };
+    int c_in = 0, n_amb = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int j0 = 0; j0 < K; j0 += kNT) {
+      const int j = j0 + tid;
+      const unsigned long long key = j < K ? sm.key[j] : ~0ull;
+      const uint32_t dk = (uint32_t)(key >> 32);
+      const bool cert = j < K && dk < lo_key;
+      const bool ambi = j < K && dk >= lo_key && dk <= hi_key;
+      const unsigned mc = __ballot_sync(0xffffffffu, cert), ma = __ballot_sync(0xffffffffu, ambi);
+      if (lane == 0) {
+        sm.warp_a[warp] = __popc(mc);
+        sm.warp_b[warp] = __popc(ma);
+      }
+      __syncthreads();
+      int oc = c_in, oa = n_amb, tc = 0, ta = 0;
+      for (int w = 0; w < kNW; ++w) {
+        if (w < warp) {
+          oc += sm.warp_a[w];
+          oa += sm.warp_b[w];
+        }
+        tc += sm.warp_a[w];
+        ta += sm.warp_b[w];
+      }
+      if (cert) {
+        a.nbr[q * k + oc + __popc(mc & below)] = (int32_t)(key & 0xffffffffu);
+        add_term(dk);
+      }
+      if (ambi) {
+        const int r = oa + __popc(ma & below);
+        if (r < 1024) amb[r] = key;
+      }
+      c_in += tc;
+      n_amb += ta;
+      __syncthreads();
+    }
+    const int need = k - c_in;  // 1 <= need <= n_amb
+    if (n_amb <= 1024) {
+      // compensated distances for the ambiguous candidates, then their order
+      const int grp = lane >> 3, lig = lane & 7;
+      for (int j0 = warp * 4; j0 < n_amb; j0 += kNW * 4) {
+        const int j = j0 + grp;
+        const bool valid = j < n_amb;
+        const int64_t id = valid ? (int64_t)(amb[j] & 0xffffffffu) : 0;
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
+        if (!row) d2 = __int_as_float(0x7f800000);
+        if (valid && lig == 0) amb[j] = pack_key(d2, (int)id);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int i = 1; i < n_amb; ++i) {  // short in practice: insertion sort
+          const unsigned long long v = amb[i];
+          int j = i - 1;
+          while (j >= 0 && amb[j] > v) {
+            amb[j + 1] = amb[j];
+            --j;
+          }
+          amb[j + 1] = v;
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < need; j += kNT) {
+        a.nbr[q * k + c_in + j] = (int32_t)(amb[j] & 0xffffffffu);
+        add_term((uint32_t)(amb[j] >> 32));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) s_fx[warp] = part;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long t = 0ull;
+        for (int w = 0; w < kNW; ++w) t += s_fx[w];
+        if (a.s1) a.s1[q] = (float)ldexp((double)t, -fx_shift);
+      }
+      return;
+    }
+    // a very wide ambiguous band (many equal distances): fall through to the
+    // full sort below, which rewrites the whole output
+  }
+  block_sort_keys(sm, K);
+  const int kk = min(a.k, K);
+  // Only candidates whose plain distance lies within the FP32 error band of
+  // the k-th can be misordered across the k-th place: recompute those with the
+  // compensated distance (relative error a few 2^-24) and re-sort that range.
+  if (kk > 0 && kk < K) {
+    __shared__ int s_lo, s_hi;
+    // four times the plain distance's error bound (ceil(d/8) + 3 + 2 units)
+    const float band_rel = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
+    if (tid == 0) {
+      const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
+      const float band = band_rel * dk;
+      int lo = kk - 1, hi = kk;
+      while (lo > 0 && __uint_as_float((uint32_t)(sm.key[lo - 1] >> 32)) >= dk - band) --lo;
+      while (hi < K && __uint_as_float((uint32_t)(sm.key[hi] >> 32)) <= dk + band) ++hi;
+      s_lo = lo;
+      s_hi = hi;
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    if (hi - lo > 1) {
+      const int grp = lane >> 3, lig = lane & 7;
+      for (int j0 = lo + warp * 4; j0 < hi; j0 += kNW * 4) {
+        const int j = j0 + grp;
+        const bool valid = j < hi;
+        const int64_t id = valid ? (int64_t)(sm.key[j] & 0xffffffffu) : 0;
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
+        if (!row) d2 = __int_as_float(0x7f800000);
+        if (valid && lig == 0) sm.key[j] = pack_key(d2, (int)id);
+      }
+      __syncthreads();
+      if (hi - lo <= 64) {
+        if (tid == 0) {  // a short band (the usual case): insertion sort
+          for (int i = lo + 1; i < hi; ++i) {
+            const unsigned long long v = sm.key[i];
+            int j = i - 1;
+            while (j >= lo && sm.key[j] > v) {
+              sm.key[j + 1] = sm.key[j];
+              --j;
+            }
+            sm.key[j + 1] = v;
+          }
+        }
+        __syncthreads();
+      } else {
+        block_sort_keys(sm, K);  // many near-equal distances: sort everything again
+      }
+    }
+  }
+  for (int j = tid; j < a.k; j += kNT) {
+    if (j < kk) {
+      a.nbr[q * a.k + j] = (int32_t)(sm.key[j] & 0xffffffffu);
+      if (a.nd2) a.nd2[q * a.k + j] = __uint_as_float((uint32_t)(sm.key[j] >> 32));
+    } else {
+      a.nbr[q * a.k + j] = -1;
+      if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
+    }
+  }
+  // exact neighbour contribution s1 and k'
+  if (a.s1 != nullptr || a.kcount != nullptr) {
+    const float inv = kernel_inv(a.kern, a.h);
+    float part = 0.f;
+    if (a.kern == KDE_KERN_LAPLACIAN) {
+      // the IVF ranks by Euclidean distance; the Laplacian kernel needs L1
+      for (int j = warp; j < kk; j += kNW) {
+        const int64_t id = (int64_t)(sm.key[j] & 0xffffffffu);
+        const bool row = id < a.n;  // an empty slot's key carries id -1
+        const float l1 = precise_l1_dist<32>(a.X + (row ? id : 0) * a.dp, y, a.d, lane);
+        if (lane == 0 && row) part += kernel_from_dist(a.kern, l1, inv);
+      }
+    } else {
+      for (int j = tid; j < kk; j += kNT)
+        part += kernel_from_dist(a.kern, __uint_as_float((uint32_t)(sm.key[j] >> 32)), inv);
+    }
+    part = warp_sum(part);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < kNW; ++w) t += s_red[w];
+      if (a.s1) a.s1[q] = t;
+      if (a.kcount) a.kcount[q] = kk;
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // Neighbour selection from the scan's candidate buffer.
 // --------------------------------------------------------------------------
@@ -656,7 +862,6 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   __shared__ int64_t s_seg[kMaxProbe + 1];
   __shared__ int64_t s_lstart[kMaxProbe];
   __shared__ int64_t s_llen[kMaxProbe];
-  __shared__ float s_red[kNW];
   const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
@@ -815,182 +1020,191 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
     }
   }
   __syncthreads();
-  if (a.ids_only && K > a.k && a.kern != KDE_KERN_LAPLACIAN) {
-    // The query path needs the set and s1, not the order: find the k-th
-    // smallest rescored distance T, take every candidate clearly below it,
-    // and rank only those within the FP32 error band of T by compensated
-    // distance.
-    const int k = a.k;
-    const float T = __uint_as_float(smem_kth_dist(sm, K, k));
-    const float bw = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T;
-    const uint32_t lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
-    const uint32_t hi_key = dist_key(T + bw);
-    unsigned long long* amb = reinterpret_cast<unsigned long long*>(sm.slot);  // 1024 keys
-    const float inv = kernel_inv(a.kern, a.h);
-    int c_in = 0, n_amb = 0;
-    float part = 0.f;
-    const unsigned below = (1u << lane) - 1u;
-    for (int j0 = 0; j0 < K; j0 += kNT) {
-      const int j = j0 + tid;
-      const unsigned long long key = j < K ? sm.key[j] : ~0ull;
-      const uint32_t dk = (uint32_t)(key >> 32);
-      const bool cert = j < K && dk < lo_key;
-      const bool ambi = j < K && dk >= lo_key && dk <= hi_key;
-      const unsigned mc = __ballot_sync(0xffffffffu, cert), ma = __ballot_sync(0xffffffffu, ambi);
-      if (lane == 0) {
-        sm.warp_a[warp] = __popc(mc);
-        sm.warp_b[warp] = __popc(ma);
-      }
-      __syncthreads();
-      int oc = c_in, oa = n_amb, tc = 0, ta = 0;
-      for (int w = 0; w < kNW; ++w) {
-        if (w < warp) {
-          oc += sm.warp_a[w];
-          oa += sm.warp_b[w];
-        }
-        tc += sm.warp_a[w];
-        ta += sm.warp_b[w];
-      }
-      if (cert) {
-        a.nbr[q * k + oc + __popc(mc & below)] = (int32_t)(key & 0xffffffffu);
-        part += kernel_from_dist(a.kern, __uint_as_float(dk), inv);
-      }
-      if (ambi) {
-        const int r = oa + __popc(ma & below);
-        if (r < 1024) amb[r] = key;
-      }
-      c_in += tc;
-      n_amb += ta;
-      __syncthreads();
+  rank_keys(a, sm, K, q, y);
+}
+
+// --------------------------------------------------------------------------
+// Two-pass selection of the BF16 scan.
+// --------------------------------------------------------------------------
+// Per query: the histogram bounds [lo^2 - E, hi^2 + E] with lo, hi the
+// nearest and farthest any probed list's point can be (|y - c_l| -+ rad_l),
+// E = err_scale r^2 the scan's error bound (r = max over the probes of
+// |y - c_l| + rad_l, the centred operands' magnitude bound); clears the
+// histogram and the emission counters.  One warp per query.
+__global__ void k_search_bounds(const int32_t* __restrict__ probes,
+                                const float* __restrict__ probe_d2, const float* __restrict__ rad,
+                                int64_t nq, int P, float err_scale, TwoPass tp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * kNW + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  float lo = __int_as_float(0x7f800000), hi = 0.f;
+  for (int p = lane; p < P; p += 32) {
+    const int l = probes[q * P + p];
+    if (l < 0) continue;
+    const float dc = sqrtf(probe_d2[q * P + p]), rl = rad[l];
+    lo = fminf(lo, fmaxf(0.f, dc - rl));
+    hi = fmaxf(hi, dc + rl);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  for (int b = lane; b < kHistBins; b += 32) tp.hist[q * kHistBins + b] = 0u;
+  if (lane == 0) {
+    const float E = err_scale * hi * hi;
+    float hlo = 0.f, hscale = 0.f;
+    if (hi >= lo) {
+      const float lo2 = fmaxf(0.f, lo * lo * (1.f - 1e-5f) - E);
+      const float hi2 = hi * hi * (1.f + 1e-5f) + E;
+      hlo = lo2;
+      hscale = hi2 > lo2 ? (float)kHistBins / (hi2 - lo2) : 0.f;
     }
-    const int need = k - c_in;  // 1 <= need <= n_amb
-    if (n_amb <= 1024) {
-      // compensated distances for the ambiguous candidates, then their order
-      const int grp = lane >> 3, lig = lane & 7;
-      for (int j0 = warp * 4; j0 < n_amb; j0 += kNW * 4) {
-        const int j = j0 + grp;
-        const bool valid = j < n_amb;
-        const int64_t id = valid ? (int64_t)(amb[j] & 0xffffffffu) : 0;
-        const bool row = id < a.n;  // an empty slot's key carries id -1
-        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
-        if (!row) d2 = __int_as_float(0x7f800000);
-        if (valid && lig == 0) amb[j] = pack_key(d2, (int)id);
+    tp.hlo[q] = hlo;
+    tp.hscale[q] = hscale;
+    tp.E[q] = E;
+    tp.cntA[q] = 0;
+    tp.cntB[q] = 0;
+  }
+}
+
+// The bin of a histogram holding the want-th smallest value (1 <= want <=
+// total) and the count below it, by a warp: four bins a lane, a warp scan of
+// the lanes' totals.  Every lane returns the same pair.
+__device__ __forceinline__ void warp_hist_rank(const uint32_t* __restrict__ h, uint32_t want,
+                                               int& bin_out, uint32_t& below_out) {
+  constexpr int kPer = kHistBins / 32;
+  const int lane = threadIdx.x & 31;
+  uint32_t c[kPer], s = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    c[i] = h[lane * kPer + i];
+    s += c[i];
+  }
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t excl = incl - s;
+  int bin = -1;
+  uint32_t below = 0;
+  if (excl < want && want <= incl) {
+    uint32_t run = excl;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {  // the running count crosses `want` in one bin
+      if (run < want && want <= run + c[i]) {
+        bin = lane * kPer + i;
+        below = run;
       }
-      __syncthreads();
-      if (tid == 0) {
-        for (int i = 1; i < n_amb; ++i) {  // short in practice: insertion sort
-          const unsigned long long v = amb[i];
-          int j = i - 1;
-          while (j >= 0 && amb[j] > v) {
-            amb[j + 1] = amb[j];
-            --j;
-          }
-          amb[j + 1] = v;
-        }
-      }
-      __syncthreads();
-      for (int j = tid; j < need; j += kNT) {
-        a.nbr[q * k + c_in + j] = (int32_t)(amb[j] & 0xffffffffu);
-        part += kernel_from_dist(a.kern, __uint_as_float((uint32_t)(amb[j] >> 32)), inv);
-      }
-      part = warp_sum(part);
-      if (lane == 0) s_red[warp] = part;
-      __syncthreads();
-      if (tid == 0) {
-        float t = 0.f;
-        for (int w = 0; w < kNW; ++w) t += s_red[w];
-        if (a.s1) a.s1[q] = t;
+      run += c[i];
+    }
+  }
+  const unsigned owner = __ballot_sync(0xffffffffu, bin >= 0);
+  const int src = owner ? __ffs(owner) - 1 : 0;
+  bin_out = __shfl_sync(0xffffffffu, bin, src);
+  below_out = __shfl_sync(0xffffffffu, below, src);
+}
+
+// Upper edge of bin b of a histogram from lo with `scale` bins per unit,
+// widened by a few units of rounding; +inf for the last bin (it also holds
+// every value beyond the range) or a degenerate range.
+__device__ __forceinline__ float bin_upper_edge(int b, float lo, float scale) {
+  if (!(scale > 0.f) || b >= kHistBins - 1) return __int_as_float(0x7f800000);
+  const float e = lo + (float)(b + 1) / scale;
+  return e + fabsf(e) * 1e-6f + 1e-30f;
+}
+
+// Stage 0, after the histogram pass: b* = the bin holding the k-th smallest
+// approximate distance t_k, and the band edge thr = (upper edge of b*) + 2E.
+// Every point of the exact top k has an approximate distance <= t_k + 2E (the
+// true k-th distance is at most t_k + E), so the candidates below bin b* and
+// those up to thr hold the exact top k.  A query with at most k candidates
+// takes them all (b* = kHistBins).  A bin b* with more than kRefineMin
+// candidates is marked for the refinement pass: its interval split into
+// kHistBins sub-bins, and k2 the k-th's rank among the bin's candidates.
+// Stage 1, after that pass: f* = the sub-bin holding rank k2, and the band
+// edge moves down to (upper edge of f*) + 2E.  One warp per query.
+__global__ void k_search_threshold(const int64_t* __restrict__ q_real, int64_t nq, int k,
+                                   int stage, TwoPass tp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * kNW + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  if (stage == 0) {
+    if (q_real[q] <= (int64_t)k) {
+      if (lane == 0) {
+        tp.bstar[q] = kHistBins;
+        tp.rbin[q] = -1;
+        tp.thr[q] = __int_as_float(0x7f800000);
       }
       return;
     }
-    // a very wide ambiguous band (many equal distances): fall through to the
-    // full sort below, which rewrites the whole output
-  }
-  block_sort_keys(sm, K);
-  const int kk = min(a.k, K);
-  // Only candidates whose plain distance lies within the FP32 error band of
-  // the k-th can be misordered across the k-th place: recompute those with the
-  // compensated distance (relative error a few 2^-24) and re-sort that range.
-  if (kk > 0 && kk < K) {
-    __shared__ int s_lo, s_hi;
-    // four times the plain distance's error bound (ceil(d/8) + 3 + 2 units)
-    const float band_rel = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
-    if (tid == 0) {
-      const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
-      const float band = band_rel * dk;
-      int lo = kk - 1, hi = kk;
-      while (lo > 0 && __uint_as_float((uint32_t)(sm.key[lo - 1] >> 32)) >= dk - band) --lo;
-      while (hi < K && __uint_as_float((uint32_t)(sm.key[hi] >> 32)) <= dk + band) ++hi;
-      s_lo = lo;
-      s_hi = hi;
-    }
-    __syncthreads();
-    const int lo = s_lo, hi = s_hi;
-    if (hi - lo > 1) {
-      const int grp = lane >> 3, lig = lane & 7;
-      for (int j0 = lo + warp * 4; j0 < hi; j0 += kNW * 4) {
-        const int j = j0 + grp;
-        const bool valid = j < hi;
-        const int64_t id = valid ? (int64_t)(sm.key[j] & 0xffffffffu) : 0;
-        const bool row = id < a.n;  // an empty slot's key carries id -1
-        float d2 = precise_sq_dist<8>(a.X + (row ? id : 0) * a.dp, y, a.d, lig);
-        if (!row) d2 = __int_as_float(0x7f800000);
-        if (valid && lig == 0) sm.key[j] = pack_key(d2, (int)id);
+    int b;
+    uint32_t below;
+    warp_hist_rank(tp.hist + q * kHistBins, (uint32_t)k, b, below);
+    const float lo = tp.hlo[q], scale = tp.hscale[q];
+    const uint32_t in_bin = tp.hist[q * kHistBins + b];
+    const bool refine = scale > 0.f && in_bin > (uint32_t)kRefineMin;
+    if (refine)
+      for (int i = lane; i < kHistBins; i += 32) tp.hist2[q * kHistBins + i] = 0u;
+    if (lane == 0) {
+      tp.bstar[q] = b;
+      tp.thr[q] = bin_upper_edge(b, lo, scale) + 2.f * tp.E[q];
+      tp.rbin[q] = refine ? b : -1;
+      if (refine) {
+        tp.flo[q] = lo + (float)b / scale;
+        tp.fscale[q] = scale * (float)kHistBins;
+        tp.k2[q] = k - (int)below;
       }
-      __syncthreads();
-      if (hi - lo <= 64) {
-        if (tid == 0) {  // a short band (the usual case): insertion sort
-          for (int i = lo + 1; i < hi; ++i) {
-            const unsigned long long v = sm.key[i];
-            int j = i - 1;
-            while (j >= lo && sm.key[j] > v) {
-              sm.key[j + 1] = sm.key[j];
-              --j;
-            }
-            sm.key[j + 1] = v;
-          }
-        }
-        __syncthreads();
-      } else {
-        block_sort_keys(sm, K);  // many near-equal distances: sort everything again
-      }
+      tp.fstar[q] = 0;
     }
+    return;
   }
-  for (int j = tid; j < a.k; j += kNT) {
-    if (j < kk) {
-      a.nbr[q * a.k + j] = (int32_t)(sm.key[j] & 0xffffffffu);
-      if (a.nd2) a.nd2[q * a.k + j] = __uint_as_float((uint32_t)(sm.key[j] >> 32));
-    } else {
+  if (tp.rbin[q] < 0) return;
+  int f;
+  uint32_t below;
+  warp_hist_rank(tp.hist2 + q * kHistBins, (uint32_t)tp.k2[q], f, below);
+  if (lane == 0) {
+    tp.fstar[q] = f;
+    // the last sub-bin ends where the bin b* ends
+    const float edge = f < kHistBins - 1 ? bin_upper_edge(f, tp.flo[q], tp.fscale[q])
+                                         : bin_upper_edge(tp.rbin[q], tp.hlo[q], tp.hscale[q]);
+    tp.thr[q] = edge + 2.f * tp.E[q];
+  }
+}
+
+// Ranking of the keys the emission pass wrote: region A (the candidates
+// below the k-th bin) and region B (the band), both FP32-rescored.  More
+// than fits in either region marks the query uncertified (kde_stats).
+__global__ void __launch_bounds__(kNT, 4) k_select_compact(SelectArgs a, TwoPass tp) {
+  extern __shared__ uint4 sel_dyn4[];
+  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
+    for (int j = tid; j < a.k; j += kNT) {
       a.nbr[q * a.k + j] = -1;
       if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
     }
-  }
-  // exact neighbour contribution s1 and k'
-  if (a.s1 != nullptr || a.kcount != nullptr) {
-    const float inv = kernel_inv(a.kern, a.h);
-    float part = 0.f;
-    if (a.kern == KDE_KERN_LAPLACIAN) {
-      // the IVF ranks by Euclidean distance; the Laplacian kernel needs L1
-      for (int j = warp; j < kk; j += kNW) {
-        const int64_t id = (int64_t)(sm.key[j] & 0xffffffffu);
-        const bool row = id < a.n;  // an empty slot's key carries id -1
-        const float l1 = precise_l1_dist<32>(a.X + (row ? id : 0) * a.dp, y, a.d, lane);
-        if (lane == 0 && row) part += kernel_from_dist(a.kern, l1, inv);
-      }
-    } else {
-      for (int j = tid; j < kk; j += kNT)
-        part += kernel_from_dist(a.kern, __uint_as_float((uint32_t)(sm.key[j] >> 32)), inv);
-    }
-    part = warp_sum(part);
-    if (lane == 0) s_red[warp] = part;
-    __syncthreads();
     if (tid == 0) {
-      float t = 0.f;
-      for (int w = 0; w < kNW; ++w) t += s_red[w];
-      if (a.s1) a.s1[q] = t;
-      if (a.kcount) a.kcount[q] = kk;
+      if (a.s1) a.s1[q] = 0.f;
+      if (a.kcount) a.kcount[q] = 0;
     }
+    return;
   }
+  const int capB = kSelectCap - tp.kA;
+  const int cA = tp.cntA[q], cB = tp.cntB[q];
+  const int nA = min(cA, tp.kA), nB = min(cB, capB);
+  if (tid == 0 && (cA > tp.kA || cB > capB)) {
+    atomicOr(a.err, KDE_ERRBIT_MARGIN);
+    atomicAdd(a.err + 1, 1u);
+  }
+  const unsigned long long* kq = tp.keys + q * kSelectCap;
+  for (int j = tid; j < nA; j += kNT) sm.key[j] = kq[j];
+  for (int j = tid; j < nB; j += kNT) sm.key[nA + j] = kq[tp.kA + j];
+  __syncthreads();
+  rank_keys(a, sm, nA + nB, q, a.Y + q * a.dp);
 }
 
 }  // namespace
@@ -1057,6 +1271,29 @@ void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
   set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), sizeof(SelectSmem));
   k_select_neighbors<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a);
+}
+
+void launch_search_bounds(const int32_t* probes, const float* probe_d2, const float* rad,
+                          int64_t nq, int P, float err_scale, const int64_t* active, int64_t q0,
+                          const TwoPass& tp, cudaStream_t s) {
+  (void)active;  // an inactive row has no probes: its bounds select nothing
+  (void)q0;
+  if (nq <= 0) return;
+  k_search_bounds<<<(unsigned)((nq + kNW - 1) / kNW), kNT, 0, s>>>(probes, probe_d2, rad, nq, P,
+                                                                 err_scale, tp);
+}
+
+void launch_search_threshold(const int64_t* q_real, int64_t nq, int k, int stage,
+                             const TwoPass& tp, cudaStream_t s) {
+  if (nq <= 0) return;
+  k_search_threshold<<<(unsigned)((nq + kNW - 1) / kNW), kNT, 0, s>>>(q_real, nq, k, stage,
+                                                                    tp);
+}
+
+void launch_select_compact(const SelectArgs& a, const TwoPass& tp, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_compact), sizeof(SelectSmem));
+  k_select_compact<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a, tp);
 }
 
 }  // namespace deann

@@ -208,6 +208,24 @@ def test_graph_replays_serve_uneven_batches(pkg):
     assert len(server.graphs) >= 3
 
 
+def test_graphs_stay_valid_when_the_scratch_grows(pkg):
+    """A graph captured while the index's scratch was small is replayed after
+    larger calls (other shapes, the FP32 scan) made the library allocate a
+    bigger buffer: the outgrown buffer is kept, so the replay still gives the
+    direct call's result."""
+    X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=3_000, n_centres=100)
+    index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=64, seed=5)
+    Yd = _dev(Y)
+    small = pkg.GraphedQuery(index, 64, 50, 500, nprobe=4, seed=2, precision=1)
+    got = small(Yd[:40], qid_offset=7).clone()
+    # calls that need much more scratch than the graph's capacity
+    index.query(Yd, 400, 4000, nprobe=16, seed=1, precision=0)
+    index.query(Yd, 400, 4000, nprobe=16, seed=1, precision=1)
+    again = small(Yd[:40], qid_offset=7).clone()
+    want = index.query(Yd[:40], 50, 500, nprobe=4, seed=2, precision=1, qid_offset=7)
+    assert torch.equal(got, want) and torch.equal(again, want)
+
+
 def test_device_active_rows(pkg):
     """A device-side row count A serves rows below A exactly as a call on
     those rows alone; rows past it get no neighbours (-1) and, through a
