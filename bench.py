@@ -840,17 +840,29 @@ def fp32_alu_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def stage_work(stage, nq, n, d, nlist, k, m, cbar):
+def stage_work(stage, nq, n, d, nlist, k, m, cbar, precision="bf16"):
     """Algorithmic (bytes, flops) of one call of a query-path stage: what the
-    method must move or compute, not padded tile work.  cbar = mean candidates
-    per query (the probed lists' sizes)."""
+    method must move or compute, not padded tile work or repeated passes.
+    cbar = mean candidates per query (the probed lists' sizes).  BF16 scan:
+    the list-major search reads the probed lists once in BF16 (distances) and
+    once in FP32 (rescoring the in-band candidates, rows shared by the queries
+    of a list), and writes about k (distance, id) keys per query, which the
+    selection reads back.  FP32 scan: every candidate's value goes to HBM and
+    back, and the selection reads the k neighbours' FP32 rows per query."""
     dpb = (d + 63) // 64 * 64
+    dp4 = (d + 3) // 4 * 4
     if stage == "estimate":   # m sampled FP32 rows (+ query, neighbour ids, output)
         return nq * (m * d * 4 + d * 4 + k * 4 + 4), 0.0
-    if stage == "select":     # candidate values, and the k neighbours' FP32 rows
-        return nq * (cbar * 4 + k * d * 4 + k * 4), 0.0
-    if stage == "scan":       # BF16 lists read once, candidate values written
-        return n * dpb * 2 + nq * cbar * 4, 2.0 * nq * cbar * d
+    if precision == "bf16":
+        if stage == "scan":
+            return n * dpb * 2 + n * dp4 * 4 + nq * k * 8, 2.0 * nq * cbar * d
+        if stage == "select":
+            return nq * (k * 8 + k * 4 + 4), 0.0
+    else:
+        if stage == "select":
+            return nq * (cbar * 4 + k * d * 4 + k * 4), 0.0
+        if stage == "scan":
+            return n * dp4 * 4 + nq * cbar * 4, 2.0 * nq * cbar * d
     if stage == "coarse":     # query x centroid contraction (FP32 CUDA cores)
         return nq * d * 4, 2.0 * nq * nlist * d
     return 0, 0.0
@@ -861,7 +873,7 @@ def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind, 
     bytes or flops per call and its measured device time per call; the bound
     is whichever of the two takes longer at peak."""
     ms = prof[stage]["ms"] / calls
-    nbytes, flops = stage_work(stage, nq, n, d, nlist, k, m, cbar)
+    nbytes, flops = stage_work(stage, nq, n, d, nlist, k, m, cbar, sched["precision"])
     fpeak = fp32_alu_tflops() if stage == "coarse" else peaks["bf16_tflops"]
     t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
     t_fl = flops / (fpeak * 1e12)
@@ -1128,15 +1140,11 @@ def main():
     others = {s: roofline(s, prof, args.steps, nq, n, d, spec["nlist"], k, m, cbar, peaks,
                           peak_kind, sched_key) for s in ("coarse", "scan", "select", "estimate")
               if s in stages}
-    # whole query path: the sum of the stages' times at peak over the step
-    # time; the method's own bytes only (lists read once, the k neighbours'
-    # and m samples' rows), not the candidate buffer between scan and selection
-    t_alg = (stage_work("estimate", nq, n, d, spec["nlist"], k, m, cbar)[0]
-             + nq * (k * d * 4 + k * 4) + n * d * 2) / (peaks["hbm_gbs"] * 1e9) * 1e3
+    # whole query path: the sum of the stages' times at peak (their
+    # algorithmic work, stage_work) over the step time
     path_roof = {"t_min_ms": sum(o["t_min_ms"] for o in others.values()),
-                 "t_alg_ms": t_alg, "t_measured_ms": ms_step, "mean_candidates": cbar}
+                 "t_measured_ms": ms_step, "mean_candidates": cbar}
     path_roof["frac"] = path_roof["t_min_ms"] / ms_step
-    path_roof["frac_alg"] = t_alg / ms_step
     launches = sum(v["launches"] for v in prof.values())
     emit("stage_rooflines", {"stages": others, "path": path_roof})
     if tuned:
@@ -1199,8 +1207,7 @@ def main():
         "meets_target": max(errs) <= TARGET_ERR, "val_rel_err": sched[head]["val_err"],
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof_short,
         "stage_ms_per_step": stages,
-        "path_roofline": {key: path_roof[key] for key in ("frac", "frac_alg", "t_min_ms",
-                                                          "t_alg_ms")},
+        "path_roofline": {key: path_roof[key] for key in ("frac", "t_min_ms")},
         "cpu_baseline": cpu,
         "baselines": {"exact": exact, "rs_qps": nq / (ms_rs / 1e3), "rs_m": rs_m,
                       "rs_rel_err": rs_err, "fp32_scan": row(variants["fp32"]["k"],

@@ -56,8 +56,17 @@ def test_stage_work_and_alu_peak():
     # the estimator's bytes are m rows of d FP32 values (+ query, ids, output)
     b, f = bench.stage_work("estimate", 10, 1000, 128, 8, 16, 100, 5.0)
     assert b == 10 * (100 * 128 * 4 + 128 * 4 + 16 * 4 + 4) and f == 0.0
+    # BF16 list-major search: the lists once in BF16 and once in FP32, ~k keys
     b, f = bench.stage_work("scan", 10, 1000, 128, 8, 16, 100, 50.0)
-    assert f == 2.0 * 10 * 50.0 * 128 and b == 1000 * 128 * 2 + 10 * 50.0 * 4
+    assert f == 2.0 * 10 * 50.0 * 128
+    assert b == 1000 * 128 * 2 + 1000 * 128 * 4 + 10 * 16 * 8
+    b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0)
+    assert b == 10 * (16 * 8 + 16 * 4 + 4)
+    # FP32 scan: every candidate's value to HBM and back, rows per query
+    b, _ = bench.stage_work("scan", 10, 1000, 130, 8, 16, 100, 50.0, "fp32")
+    assert b == 1000 * 132 * 4 + 10 * 50.0 * 4
+    b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0, "fp32")
+    assert b == 10 * (50.0 * 4 + 16 * 128 * 4 + 16 * 4)
     assert bench.fp32_alu_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
@@ -148,8 +157,7 @@ def _representative_headline():
                      "peak_source": "measured hbm_gbs"},
         "stage_ms_per_step": {s: 1.2345678 for s in ("stage", "coarse", "plan", "scan",
                                                      "select", "estimate")},
-        "path_roofline": {"frac": 0.8912345, "frac_alg": 0.7812345, "t_min_ms": 4.5712345,
-                          "t_alg_ms": 4.0012345},
+        "path_roofline": {"frac": 0.8912345, "t_min_ms": 4.5712345},
         "cpu_baseline": {"value": 1321.12345, "unit": "queries/s", "cores": 16, "kind": "oracle",
                          "sample": "first 16384 of 10000 test queries, IVF search + DEANN in "
                                    "FP64, 12.3 s", "single_thread_qps": 72.512345},
