@@ -46,13 +46,16 @@ import workloads  # noqa: E402
 # the cheapest that `bench.py --tune` finds with a mean relative error <= 0.9e-2
 # on the 4,000 validation queries.  Both arms run it unless --schedule or --tune
 # says otherwise.
-DEFAULT_SCHEDULE = {"bf16": (1536, 4000, 8), "fp32": (1536, 4000, 8)}
+DEFAULT_SCHEDULE = {"bf16": (1536, 4000, 8), "fp32": (1536, 4000, 8),
+                    "bf16x3": (1536, 4000, 8)}
 TARGET_ERR = 1e-2
 # the tuners aim 10 % below the target on the validation queries, so that
 # every timed step (each with its own seed) stays within it on the test queries
 TUNE_ERR = 0.9 * TARGET_ERR
 WORKLOAD = "mixture_embed n=1M d=128 nq=10k gaussian mean-KDE=1e-3 IVF nlist=1024"
-PRECISIONS = {"fp32": 0, "bf16": 1}
+# scan precisions: FP32 SIMT, BF16 tensor cores with FP32 rescoring, and the
+# three-way BF16 split on tensor cores (FP32-level distances)
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
 
 def parse():
@@ -128,13 +131,15 @@ def sig(x, digits=4):
     return x
 
 
-# The driver reads the end of stdout (about 3 KB): the headline line has to
-# fit in it whole, with room for a prefix.
-HEADLINE_LIMIT = 2700
+# The driver reads the end of stdout (about 3 KB): the headline line and the
+# short summary of the other workloads printed just before it have to fit in
+# it whole, with room for a prefix.
+HEADLINE_LIMIT = 1900
+FORMS_LIMIT = 950
 
 
 def fit_headline(line, limit=HEADLINE_LIMIT,
-                 optional=("forms", "baselines", "path_roofline", "stage_ms_per_step")):
+                 optional=("baselines", "path_roofline", "stage_ms_per_step")):
     """The headline as JSON text of at most `limit` bytes: optional sections
     are moved, in the given order, to a side line printed ahead of it until
     the rest fits.  Returns (text, moved sections)."""
@@ -842,27 +847,22 @@ def fp32_alu_tflops(sm_mhz=2070.0):
 
 def stage_work(stage, nq, n, d, nlist, k, m, cbar, precision="bf16"):
     """Algorithmic (bytes, flops) of one call of a query-path stage: what the
-    method must move or compute, not padded tile work or repeated passes.
-    cbar = mean candidates per query (the probed lists' sizes).  BF16 scan:
-    the list-major search reads the probed lists once in BF16 (distances) and
-    once in FP32 (rescoring the in-band candidates, rows shared by the queries
-    of a list), and writes about k (distance, id) keys per query, which the
-    selection reads back.  FP32 scan: every candidate's value goes to HBM and
-    back, and the selection reads the k neighbours' FP32 rows per query."""
+    method must move or compute, not padded tile work.  cbar = mean
+    candidates per query (the probed lists' sizes).  The list scan reads the
+    probed lists once (BF16, or three BF16 parts for the split scan, FP32 for
+    the SIMT scan) and writes every candidate's distance; the selection reads
+    them back, and with the FP32 and BF16 scans rescores the k neighbours'
+    FP32 rows per query (the split scan's distances need no rescoring)."""
     dpb = (d + 63) // 64 * 64
     dp4 = (d + 3) // 4 * 4
     if stage == "estimate":   # m sampled FP32 rows (+ query, neighbour ids, output)
         return nq * (m * d * 4 + d * 4 + k * 4 + 4), 0.0
-    if precision == "bf16":
-        if stage == "scan":
-            return n * dpb * 2 + n * dp4 * 4 + nq * k * 8, 2.0 * nq * cbar * d
-        if stage == "select":
-            return nq * (k * 8 + k * 4 + 4), 0.0
-    else:
-        if stage == "select":
-            return nq * (cbar * 4 + k * d * 4 + k * 4), 0.0
-        if stage == "scan":
-            return n * dp4 * 4 + nq * cbar * 4, 2.0 * nq * cbar * d
+    if stage == "scan":
+        lists = {"fp32": n * dp4 * 4, "bf16": n * dpb * 2, "bf16x3": 3 * n * dpb * 2}[precision]
+        return lists + nq * cbar * 4, 2.0 * nq * cbar * d
+    if stage == "select":
+        rows = 0 if precision == "bf16x3" else k * d * 4
+        return nq * (cbar * 4 + rows + k * 4), 0.0
     if stage == "coarse":     # query x centroid contraction (FP32 CUDA cores)
         return nq * d * 4, 2.0 * nq * nlist * d
     return 0, 0.0
@@ -1004,10 +1004,11 @@ def fp8_study(args):
 
 def profile_case(args):
     """One batch of args.profile_case queries through each path at the DEANN
-    schedule args.profile_schedule (BF16 scan, h = 12.85): DEANN, DEANNP (tiled
-    windows), the tensor-core exact KDE and the adjoint on the DEANN query's
-    neighbours; one launch each of k_scan_tc, k_select_neighbors, k_estimate,
-    k_window_tile, k_exact_tc, k_estimate_grad."""
+    schedule args.profile_schedule (h = 12.85): DEANN with the BF16 scan and
+    with the split BF16 scan, DEANNP (tiled windows), the tensor-core exact
+    KDE and the adjoint on the DEANN query's neighbours; one launch each of
+    k_scan_tc<false>, k_scan_tc<true>, k_window_tile, k_exact_tc,
+    k_estimate_grad, two of k_select_neighbors and k_estimate."""
     import torch
     import paper_2107_02736_gb300 as pkg
     k, m, P = (int(v) for v in args.profile_schedule.split(","))
@@ -1018,13 +1019,15 @@ def profile_case(args):
     index.prepare_permuted()
     Yd = torch.from_numpy(Y).to(dev)
     a, nbr = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, return_neighbors=True)
+    a2 = index.query(Yd, k, m, nprobe=P, seed=1, precision=2)
     b = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, sample_mode=2)
     c = index.exact(Yd[:1024], path="tensor")
     g = index.grad_with_neighbors(Yd, nbr, m, seed=1)[1]
     torch.cuda.synchronize()
     print("profile case ok", json.dumps({"k": k, "m": m, "nprobe": P, "precision": "bf16",
                                          "nq": args.profile_case}),
-          float(a.mean()), float(b.mean()), float(c.mean()), float(g.abs().mean()))
+          float(a.mean()), float(a2.mean()), float(b.mean()), float(c.mean()),
+          float(g.abs().mean()))
 
 
 def main():
@@ -1182,8 +1185,7 @@ def main():
         qps, cores, done, spent = oracle_sample_rate(X, Y, C.numpy(), assign.numpy(),
                                                      args.kernel, h, k, m, P, args.cpu_budget)
         cpu = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {done} of {nq} test queries, IVF search + DEANN in FP64, "
-                         f"{spent:.1f} s"}
+               "sample": f"{done} test queries, IVF search + DEANN, FP64, {spent:.1f} s"}
         # one thread, for comparison with the paper's single-core timings
         import oracle
         oracle.set_num_threads(1)
@@ -1205,20 +1207,19 @@ def main():
                    "l2": "inputs > L2 (X 512 MB)"},
         "mean_rel_err": statistics.mean(errs), "max_step_rel_err": max(errs),
         "meets_target": max(errs) <= TARGET_ERR, "val_rel_err": sched[head]["val_err"],
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof_short,
+        "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": {key: clk.get(key) for key in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+        "roofline": roof_short,
         "stage_ms_per_step": stages,
         "path_roofline": {key: path_roof[key] for key in ("frac", "t_min_ms")},
         "cpu_baseline": cpu,
         "baselines": {"exact": exact, "rs_qps": nq / (ms_rs / 1e3), "rs_m": rs_m,
-                      "rs_rel_err": rs_err, "fp32_scan": row(variants["fp32"]["k"],
-                                                             variants["fp32"]["m"],
-                                                             variants["fp32"]["nprobe"],
-                                                             variants["fp32"]["qps"],
-                                                             variants["fp32"]["test_rel_err"]),
+                      "rs_rel_err": rs_err,
+                      "scans": {name: row(v["k"], v["m"], v["nprobe"], v["qps"],
+                                          v["test_rel_err"]) for name, v in variants.items()},
                       "deannp": row(permuted["k"], permuted["m"], permuted["nprobe"],
                                     permuted["qps"], permuted["test_rel_err"])},
-        "forms": forms, "row_fields": ROW_FIELDS, "margin_failures": index.margin_failures(),
-        "build_s": build_s,
+        "margin_failures": index.margin_failures(), "build_s": build_s,
     }
     index.close()
     if world > 1:
@@ -1227,6 +1228,12 @@ def main():
         text, moved = fit_headline(sig(line, 4))
         if moved:
             emit("headline_overflow", moved)
+        if forms:
+            # the other workloads' rows, last before the headline
+            forms["row_fields"] = ROW_FIELDS
+            ftext = json.dumps({"side": "forms", **sig(forms, 4)})
+            print(ftext if len(ftext) <= FORMS_LIMIT else
+                  json.dumps({"side": "forms", "too_long": len(ftext)}), flush=True)
         print(text, flush=True)
 
 

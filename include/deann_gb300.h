@@ -62,12 +62,18 @@ typedef enum {
   KDE_ESTATE = 5  /* wrong device, or an earlier asynchronous error pending */
 } kde_status;
 
-/* Precision of the IVF scan's distance tiles.  Selected neighbours are always
- * rescored with FP32 difference-form distances, so the returned neighbour
- * distances and estimates are FP32 whatever the scan used. */
+/* Precision of the IVF scan's distance tiles.  The returned neighbour
+ * distances and estimates are FP32-level whatever the scan used: the FP32 and
+ * BF16 scans only rank candidates, and the best (every one within the scan's
+ * rigorous error band of the k-th) are rescored with FP32 difference-form
+ * distances; the split scan's distances are FP32-level themselves (operands
+ * split into three BF16 parts, six partial products), so only the candidates
+ * within its error band of the k-th distance are rescored, with compensated
+ * FP32 difference-form distances, to settle the order there. */
 typedef enum {
-  KDE_PREC_FP32 = 0, /* FP32 operands */
-  KDE_PREC_BF16 = 1  /* BF16 operands, FP32 accumulation, FP32 rescoring */
+  KDE_PREC_FP32 = 0,  /* FP32 operands */
+  KDE_PREC_BF16 = 1,  /* BF16 operands, FP32 accumulation, FP32 rescoring */
+  KDE_PREC_BF16X3 = 2 /* three-part BF16 split operands, FP32 accumulation; d <= 1152 */
 } kde_precision;
 
 typedef struct {
@@ -155,6 +161,8 @@ kde_status kde_export_ivf(kde_index* index, float* centroids, int32_t* assign);
  *   nbr    nq x k original point ids sorted by (distance, id); -1 pads rows
  *          with fewer than k candidates.
  *   d2     nq x k squared distances (FP32, difference form) or NULL; +inf pads.
+ *          (With the split scan, passing d2 makes the call rescore the
+ *          candidates' rows as the BF16 scan does.)
  * Candidates are ranked first by approximate distances from the scan (see
  * opts.precision) and the best k + margin are rescored exactly. */
 kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t nprobe,

@@ -272,6 +272,37 @@ __global__ void k_center_bf16(const float* __restrict__ XL, int dp,
   }
 }
 
+// The centred rows x~ = x - c_l of each list split into three BF16 parts,
+// x~ = p0 + p1 + p2 up to 2^-27 |x~| (p0 = bf16(x~), p1 = bf16(x~ - p0),
+// p2 = bf16(x~ - p0 - p1); each difference is exact in FP32): part p of the
+// list-order row r at dst[(p n + r) dpb + j].  |x~|^2 is summed in FP64 and
+// rounded once.  One block per list, one warp per row.
+__global__ void k_center_split3(const float* __restrict__ XL, int dp, int64_t n,
+                                const int64_t* __restrict__ list_off, const float* __restrict__ C,
+                                __nv_bfloat16* __restrict__ dst, int dpb,
+                                float* __restrict__ xsn) {
+  const int l = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t b = list_off[l], e = list_off[l + 1];
+  const float* c = C + (int64_t)l * dp;
+  for (int64_t r = b + warp; r < e; r += nw) {
+    double s = 0.0;
+    for (int j = lane; j < dpb; j += 32) {
+      const float v = j < dp ? XL[r * dp + j] - c[j] : 0.f;
+      const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(p0);
+      const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+      dst[(0 * n + r) * dpb + j] = p0;
+      dst[(1 * n + r) * dpb + j] = p1;
+      dst[(2 * n + r) * dpb + j] = p2;
+      s += (double)v * (double)v;
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) xsn[r] = (float)s;
+  }
+}
+
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t count, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -348,6 +379,12 @@ void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L,
                         void* dst, int dpb, float* xcn, float* rad, cudaStream_t s) {
   k_center_bf16<<<(unsigned)L, 256, 0, s>>>(XL, dp, list_off, C,
                                             reinterpret_cast<__nv_bfloat16*>(dst), dpb, xcn, rad);
+}
+
+void launch_center_split3(const float* XL, int dp, int64_t n, const int64_t* list_off, int L,
+                          const float* C, void* dst, int dpb, float* xsn, cudaStream_t s) {
+  k_center_split3<<<(unsigned)L, 256, 0, s>>>(XL, dp, n, list_off, C,
+                                              reinterpret_cast<__nv_bfloat16*>(dst), dpb, xsn);
 }
 
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s) {

@@ -159,9 +159,18 @@ struct StageTimer {
   }
 };
 
-float scan_err_scale(int dp, int precision) {
+float scan_err_scale(int dp, int dpb, int precision) {
   const float u = 1.0f / 16777216.0f;  // 2^-24
   if (precision == 0) return 2.0f * ((float)dp / 32.0f + 40.0f) * u;
+  if (precision == 2) {
+    // three-way split, per unit of r^2 (r = |x~| + |y~|): the main
+    // accumulator's FP32 additions, assuming only that each MMA accumulates at
+    // FP32 precision (dpb / 16 MMAs of 16 products plus the accumulator,
+    // each addition off by 2^-23 at most, on sums bounded by |x~||y~| <=
+    // r^2 / 4), twice that in D^2, plus the dropped split terms, the norms'
+    // rounding, the centring subtractions and the epilogue's FP32 sums
+    return (1.1f * (float)dpb + 8.0f) * u;
+  }
   // BF16 operands, each rounded to nearest with 8 significant bits: the dot
   // product is off by at most 2^-8 |x||y| <= 2^-10 (|x| + |y|)^2, twice that
   // in D^2, plus the FP32 accumulation and norm terms
@@ -181,22 +190,15 @@ struct SearchBufs {
   int64_t* pair_dst = nullptr;
   int64_t *ord_cnt = nullptr, *ord_off = nullptr, *ord_fill = nullptr;
   int32_t* order = nullptr;
-  float* cand = nullptr;   // FP32 scan: every candidate's distance
-  TwoPass tp;              // BF16 scan: the two-pass selection's state
+  float* cand = nullptr;
 };
 
-constexpr size_t kCandCap = size_t(8) << 30;  // search scratch per chunk of queries
+constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of queries
 
-void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, int precision,
-                  SearchBufs& s) {
+void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s) {
   const int L = ix->nlist;
-  const bool two_pass = precision == KDE_PREC_BF16;
-  // FP32 scan: each (query, probe) candidate segment is padded to a multiple
-  // of 32 floats; BF16 scan: a histogram and kSelectCap keys per query
-  const size_t per_q =
-      (two_pass ? 2 * sizeof(uint32_t) * kHistBins + sizeof(unsigned long long) * kSelectCap + 64
-                : (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32) * sizeof(float)) +
-      sizeof(float) * (size_t)L;
+  // each (query, probe) candidate segment is padded to a multiple of 32 floats
+  const size_t per_q = ((size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32)) * sizeof(float);
   int64_t qc = (int64_t)std::max<size_t>(1, kCandCap / per_q);
   qc = std::min<int64_t>(qc, std::max<int64_t>(nq, 1));
   s.qc = qc;
@@ -218,26 +220,7 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, int precision
   s.ord_off = b.take<int64_t>(L + 1);
   s.ord_fill = b.take<int64_t>(L);
   s.order = b.take<int32_t>(qc);
-  if (two_pass) {
-    s.tp.hlo = b.take<float>(qc);
-    s.tp.hscale = b.take<float>(qc);
-    s.tp.E = b.take<float>(qc);
-    s.tp.thr = b.take<float>(qc);
-    s.tp.bstar = b.take<int32_t>(qc);
-    s.tp.cntA = b.take<int32_t>(qc);
-    s.tp.cntB = b.take<int32_t>(qc);
-    s.tp.rbin = b.take<int32_t>(qc);
-    s.tp.flo = b.take<float>(qc);
-    s.tp.fscale = b.take<float>(qc);
-    s.tp.k2 = b.take<int32_t>(qc);
-    s.tp.fstar = b.take<int32_t>(qc);
-    s.tp.hist = b.take<uint32_t>((size_t)qc * kHistBins);
-    s.tp.hist2 = b.take<uint32_t>((size_t)qc * kHistBins);
-    s.tp.keys = b.take<unsigned long long>((size_t)qc * kSelectCap);
-  } else {
-    s.cand = b.take<float>((size_t)qc * (size_t)P *
-                           ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
-  }
+  s.cand = b.take<float>((size_t)qc * (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
 }
 
 struct CallBufs {
@@ -283,7 +266,6 @@ struct CallShape {
   bool exact_tc = false;   // tensor-core exact: BF16 parts of the queries
   bool window = false;     // permuted-window estimator (sample_mode 2)
   int fit_k = -1;          // >= 0: bandwidth fitting with fit_k search neighbours
-  int precision = 0;       // scan precision of the search (its scratch differs)
 };
 
 void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -320,7 +302,7 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
     cb.fit_nbr = b.take<int32_t>((size_t)nq * std::max(c.fit_k, 1));
     cb.fit_red = b.take<double>(4);
   }
-  if (c.search) carve_search(b, ix, c.nq, c.P, c.precision, cb.search);
+  if (c.search) carve_search(b, ix, c.nq, c.P, cb.search);
 }
 
 kde_status prepare_call(kde_index* ix, const CallShape& c, CallBufs& cb) {
@@ -366,21 +348,23 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
                            s.probes, s.probe_d2, active, q0, st);
     }
-    // the BF16 tensor-core scan groups up to BN queries per list; the FP32
-    // SIMT scan groups 64
-    const bool tcore = precision == KDE_PREC_BF16;
-    if (tcore && !ix->tmap_ok)
+    // the tensor-core scans group up to BN queries per list; the FP32 SIMT
+    // scan groups 64
+    const bool tcore = precision == KDE_PREC_BF16 || precision == KDE_PREC_BF16X3;
+    const bool split = precision == KDE_PREC_BF16X3;
+    if (split && ix->dpb > kMaxSplitDim)
+      return fail(KDE_EINVAL, "the split BF16 scan needs d <= %d", kMaxSplitDim);
+    if (tcore && !(split ? ix->xls_ok : ix->tmap_ok))
       return fail(KDE_ECUDA, "the BF16 tensor map could not be encoded on this driver");
-    const int qtile = tcore ? scan_tc_bn(ix->dpb) : kTile;
+    const int qtile = tcore ? scan_tc_bn(ix->dpb, split) : kTile;
+    if (qtile <= 0)
+      return fail(KDE_EINVAL, "the split BF16 scan needs d <= %d", kMaxSplitDim);
     {
-      StageTimer t(ix, ST_PLAN, st, tcore ? 6 : 9);
+      StageTimer t(ix, ST_PLAN, st, 9);
       launch_plan_pairs(s.probes, nc, P, ix->list_off, L, s.q_count, s.q_real, s.q_off, s.seg_off,
                         s.list_cnt, s.bucket_off, s.bucket_fill, s.pair_q, s.pair_dst,
                         s.tile_cnt, s.tile_off, ix->lorder, qtile, st);
-      // the FP32 path's selection rescoring reads rows per query: run queries
-      // grouped by their nearest list (the BF16 path rescored inside the scan)
-      if (!tcore)
-        launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
+      launch_select_order(s.probes, nc, P, L, s.ord_cnt, s.ord_off, s.ord_fill, s.order, st);
     }
     ScanPlan plan;
     plan.pair_q = s.pair_q;
@@ -389,22 +373,12 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     plan.tile_off = s.tile_off;
     plan.lorder = ix->lorder;
     plan.max_tiles = (nc * P + qtile - 1) / qtile + L;
-    const float err_scale = scan_err_scale(ix->dp, precision);
     if (tcore) {
-      // passes of the tensor-core scan: histograms, threshold, sub-bins of
-      // crowded k-th bins, threshold, then the in-band candidates rescored in
-      // FP32 and emitted as keys
-      StageTimer t(ix, ST_SCAN, st, 6);
-      TwoPass tp = s.tp;
-      tp.kA = k;
-      launch_search_bounds(s.probes, s.probe_d2, ix->rad, nc, P, err_scale, active, q0, tp, st);
-      for (int mode : {(int)kScanHist, (int)kScanRefine, (int)kScanEmit}) {
-        if (mode == kScanRefine) launch_search_threshold(s.q_real, nc, k, 0, tp, st);
-        if (mode == kScanEmit) launch_search_threshold(s.q_real, nc, k, 1, tp, st);
-        if (!launch_scan_tc(mode, ix->tmap_xlb, Yc, ix->C, ix->dp, ix->XLcn, ix->list_off, L,
-                            ix->dpb, qtile, plan, nullptr, tp, ix->XL, ix->perm, ix->err, st))
-          return fail(KDE_ECUDA, "could not configure the tensor-core scan kernel");
-      }
+      StageTimer t(ix, ST_SCAN, st, 1);
+      if (!launch_scan_tc(split, split ? ix->tmap_xls : ix->tmap_xlb, Yc, ix->C, ix->dp,
+                          split ? ix->XLsn : ix->XLcn, ix->n, ix->list_off, L, ix->dpb, qtile,
+                          plan, s.cand, ix->err, st))
+        return fail(KDE_ECUDA, "could not configure the tensor-core scan kernel");
     } else {
       StageTimer t(ix, ST_SCAN, st, 1);
       launch_scan_simt(Yc, Ync, ix->XL, ix->XLn, ix->list_off, L, ix->dp, plan, s.cand, st);
@@ -436,7 +410,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.k = k;
     a.kern = ix->kern;
     a.h = ix->h;
-    a.err_scale = err_scale;
+    a.err_scale = scan_err_scale(ix->dp, ix->dpb, precision);
     a.nbr = nbr + q0 * k;
     a.nd2 = nd2 ? nd2 + q0 * k : nullptr;
     a.s1 = s1 ? s1 + q0 : nullptr;
@@ -444,15 +418,16 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.probe_d2 = s.probe_d2;
     a.rad = ix->rad;
     a.centered = tcore ? 1 : 0;
+    a.rescore = split ? 0 : 1;
+    // 2.5 times the largest D^2 error per unit of (|x~| + |y~|)^2 measured for
+    // the split scan on GB300 (dpb / 16 units of 2^-24: one per MMA along a
+    // row), and s1 kept unrescored up to a relative error of 8e-6
+    a.XLsn = ix->XLsn;
+    a.acc_scale = (float)ix->dpb / 16.0f / 16777216.0f;
+    a.acc_tol = 8e-6f;
     a.ids_only = ids_only && nd2 == nullptr ? 1 : 0;
     a.err = ix->err;
-    if (tcore) {
-      TwoPass tp = s.tp;
-      tp.kA = k;
-      launch_select_compact(a, tp, st);
-    } else {
-      launch_select_neighbors(a, st);
-    }
+    launch_select_neighbors(a, st);
   }
   CK(cudaGetLastError());
   return KDE_OK;
@@ -501,8 +476,8 @@ kde_status check_index(const kde_index* ix) {
 }
 
 kde_status check_opts(const kde_opts* o) {
-  if (o->precision != KDE_PREC_FP32 && o->precision != KDE_PREC_BF16)
-    return fail(KDE_EINVAL, "precision must be 0 (FP32) or 1 (BF16)");
+  if (o->precision < KDE_PREC_FP32 || o->precision > KDE_PREC_BF16X3)
+    return fail(KDE_EINVAL, "precision must be 0 (FP32), 1 (BF16) or 2 (BF16 x3 split)");
   if (o->sample_mode < 0 || o->sample_mode > 2)
     return fail(KDE_EINVAL, "sample_mode must be 0 (reject), 1 (drop) or 2 (permuted window)");
   if (o->exact_path < 0 || o->exact_path > 2)
@@ -721,6 +696,16 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   launch_center_bf16(ix->XL, ix->dp, ix->list_off, (int)L, ix->C, ix->XLb, ix->dpb, ix->XLcn,
                      ix->rad, st);
   ix->tmap_ok = make_bf16_row_map(ix->tmap_xlb, ix->XLb, n, ix->dpb);
+  if (ix->dpb <= kMaxSplitDim) {
+    // the split copy of the centred rows for the FP32-accurate scan
+    uint16_t* xls = nullptr;
+    BTRY(dev_alloc(&xls, (size_t)3 * n * ix->dpb));
+    ix->XLs = xls;
+    BTRY(dev_alloc(&ix->XLsn, (size_t)n));
+    launch_center_split3(ix->XL, ix->dp, n, ix->list_off, (int)L, ix->C, ix->XLs, ix->dpb,
+                         ix->XLsn, st);
+    ix->xls_ok = make_parts_map(ix->tmap_xls, ix->XLs, 3 * n, ix->dpb);
+  }
   if (kernel != KDE_LAPLACIAN) {
     // exact KDE on tensor cores: centred rows split into three BF16 parts
     BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
@@ -778,6 +763,8 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->XL);
   cudaFree(ix->XLn);
   cudaFree(ix->XLb);
+  cudaFree(ix->XLs);
+  cudaFree(ix->XLsn);
   cudaFree(ix->perm);
   cudaFree(ix->assign);
   cudaFree(ix->lorder);
@@ -893,7 +880,6 @@ kde_status kde_search(kde_index* ix, const float* Y, int64_t nq, int32_t k, int3
   c.k = k;
   c.P = nprobe;
   c.search = true;
-  c.precision = o->precision;
   c.host = host;
   c.need_nbr = host;
   c.need_nd2 = host && d2 != nullptr;
@@ -948,7 +934,6 @@ kde_status kde_query(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
-  c.precision = o->precision;
   c.host = host;
   c.need_out = host;
   c.need_nbr = k > 0 && (host || nbr == nullptr);
@@ -1203,7 +1188,6 @@ kde_status kde_grad(kde_index* ix, const float* Y, int64_t nq, int32_t k, int32_
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
-  c.precision = o->precision;
   c.host = host;
   c.need_nbr = k > 0;
   c.need_out = true;
@@ -1269,7 +1253,6 @@ kde_status kde_mean_shift(kde_index* ix, float* Y, int64_t nq, int32_t steps, in
   c.m = m;
   c.P = nprobe;
   c.search = k > 0;
-  c.precision = o->precision;
   c.host = host;
   c.need_out = true;
   c.need_nbr = k > 0;
@@ -1342,7 +1325,6 @@ kde_status kde_fit_bandwidth(kde_index* ix, const int32_t* zid, int64_t nz, int3
   c.m = m;
   c.P = std::max(1, nprobe);
   c.search = k > 0;
-  c.precision = o->precision;
   c.host = true;
   c.need_out = true;
   c.need_nbr = true;
@@ -1455,13 +1437,11 @@ kde_status kde_profile_read(kde_index* ix, kde_profile* out, int32_t reset,
 kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t nprobe,
                        const kde_opts* opts) {
   TRY(check_index(ix));
-  const kde_opts* o = opts ? opts : &kDefaultOpts;
-  TRY(check_opts(o));
+  (void)opts;
   DeviceGuard g(ix->device);
   size_t need = 0;
   for (int variant = 0; variant < 4; ++variant) {
     CallShape c;
-    c.precision = o->precision;  // the search's scratch depends on the scan precision
     c.nq = nq;
     c.k = k;
     c.m = m;

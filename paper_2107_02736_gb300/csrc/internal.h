@@ -26,6 +26,7 @@ constexpr int kMaxK = 2048;          // largest neighbour count k
 constexpr int kMaxProbe = 256;       // largest nprobe
 constexpr int kSelectCap = 4096;     // largest candidate count kept for rescoring
 constexpr int kTile = 64;            // SIMT distance tile edge
+constexpr int kMaxSplitDim = 1152;   // widest padded row of the split BF16 scan
 
 // Row stride (in floats) of every FP32 row-major matrix: d rounded up to a
 // multiple of 4 so rows start on 16-byte boundaries; padding is zero.
@@ -91,6 +92,13 @@ struct kde_index {
   // 128-byte swizzle
   alignas(64) unsigned char tmap_xlb[128] = {0};
   bool tmap_ok = false;
+  // the same centred rows split into three BF16 parts [3][n][dpb] (the
+  // FP32-accurate tensor-core scan), their FP64-accurate squared norms, and
+  // the TMA descriptor of the parts
+  void* XLs = nullptr;
+  float* XLsn = nullptr;
+  alignas(64) unsigned char tmap_xls[128] = {0};
+  bool xls_ok = false;
   // exact KDE on tensor cores (Euclidean kernels): dataset mean, the rows
   // minus the mean split into three BF16 parts [3][n][dpb], their squared
   // norms, and the TMA descriptor of the parts
@@ -151,6 +159,9 @@ void launch_to_bf16(const float* X, int64_t n, int dp, void* dst, int dpb, cudaS
 void launch_center_bf16(const float* XL, int dp, const int64_t* list_off, int L, const float* C,
                         void* dst, int dpb, float* xcn, float* rad, cudaStream_t s);
 void launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s);
+// three-way BF16 split of the list-centred rows, [3][n][dpb], and FP64 norms
+void launch_center_split3(const float* XL, int dp, int64_t n, const int64_t* list_off, int L,
+                          const float* C, void* dst, int dpb, float* xsn, cudaStream_t s);
 void launch_feistel_perm(uint64_t seed, int64_t n, int32_t* out, cudaStream_t s);
 void launch_invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
 
@@ -174,57 +185,15 @@ void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const fl
                       const int64_t* list_off, int L, int dp, const ScanPlan& plan, float* cand,
                       cudaStream_t s);
 
-// ---- two-pass selection of the BF16 scan (tc_scan.cu, select.cu) ----------
-// Pass 1 bins every candidate's approximate distance into a per-query
-// histogram over bounds from the probed lists' radii; the threshold kernel
-// finds the bin b* of the k-th smallest and the band edge thr = (upper edge of
-// b*) + 2E; pass 2 recomputes the distances and rescores in FP32 difference
-// form only the candidates in bins below b* (region A, certainly in the top
-// k) or at most thr (region B), writing (distance, id) keys; the compact
-// selection ranks those keys.
-// A query whose k-th bin holds more than kRefineMin candidates gets a second
-// histogram pass over that bin alone (kHistBins sub-bins), so that the band
-// past the k-th sub-bin stays narrow where many candidates lie at nearly the
-// same distance.
-constexpr int kHistBins = 128;
-constexpr int kRefineMin = 64;
-struct TwoPass {
-  float* hlo = nullptr;           // [nq] histogram lower bound
-  float* hscale = nullptr;        // [nq] bins per unit of squared distance (0: one bin)
-  float* E = nullptr;             // [nq] error bound of the scan's distances
-  uint32_t* hist = nullptr;       // [nq x kHistBins]
-  uint32_t* hist2 = nullptr;      // [nq x kHistBins] sub-bins of the refined bin
-  float* thr = nullptr;           // [nq] band edge
-  int32_t* bstar = nullptr;       // [nq] bin of the k-th smallest (kHistBins: take all)
-  int32_t* rbin = nullptr;        // [nq] the refined bin (b*), or -1
-  float* flo = nullptr;           // [nq] sub-bin lower bound
-  float* fscale = nullptr;        // [nq] sub-bins per unit
-  int32_t* k2 = nullptr;          // [nq] rank of the k-th within bin b*
-  int32_t* fstar = nullptr;       // [nq] sub-bin of the k-th (refined queries)
-  int32_t* cntA = nullptr;        // [nq] keys emitted to region A
-  int32_t* cntB = nullptr;        // [nq] keys emitted to region B
-  unsigned long long* keys = nullptr;  // [nq x kSelectCap]: A at [0, kA), B at [kA, cap)
-  int kA = 0;                     // capacity of region A (= k)
-};
-// hist_bin of an approximate squared distance: the same arithmetic in both
-// passes, so a candidate lands in the same bin each time.
-__host__ __device__ inline int hist_bin(float a, float lo, float scale) {
-  if (!(scale > 0.f)) return 0;
-  const float t = (a - lo) * scale;
-  if (!(t >= 0.f)) return 0;
-  return t >= (float)kHistBins ? kHistBins - 1 : (int)t;
-}
-
 // ---- tc_scan.cu (tcgen05 BF16 scan) ----------------------------------------
-enum ScanMode { kScanCand = 0, kScanHist = 1, kScanEmit = 2, kScanRefine = 3 };
-int scan_tc_bn(int dpb);                    // queries per CTA for a given row width
+// Queries per CTA for a row width (0: the operands do not fit); split = the
+// three-way BF16 split of both operands (tmap over [3][n][dpb], xn the FP64-
+// accurate norms), else plain BF16 (tmap over [n][dpb]).
+int scan_tc_bn(int dpb, bool split);
 bool make_bf16_row_map(void* map_out, const void* base, int64_t rows, int dpb);
-// kScanCand: every candidate's approximate distance into cand (segments);
-// kScanHist / kScanRefine / kScanEmit: the passes above (tp, XL, perm used).
-bool launch_scan_tc(int mode, const void* tmap, const float* Yp, const float* C, int dp,
-                    const float* XLcn, const int64_t* list_off, int L, int dpb, int BN,
-                    const ScanPlan& plan, float* cand, const TwoPass& tp, const float* XL,
-                    const int32_t* perm, uint32_t* err, cudaStream_t s);
+bool launch_scan_tc(bool split, const void* tmap, const float* Yp, const float* C, int dp,
+                    const float* xn, int64_t n, const int64_t* list_off, int L, int dpb, int BN,
+                    const ScanPlan& plan, float* cand, uint32_t* err, cudaStream_t s);
 
 // ---- tc_exact.cu (tcgen05 exact KDE, three-way BF16 split) -----------------
 void launch_col_mean(const float* X, int64_t n, int dp, float* mean, cudaStream_t s);
@@ -285,20 +254,14 @@ struct SelectArgs {
   const float* rad;          // [nlist]
   int centered;
   int ids_only;              // 1: the neighbour set in any order (+ s1); no nd2
+  int rescore;               // 1: rescore the band's rows in FP32 (plain BF16 / FP32 scans);
+                             // 0: the scan's values are FP32-level (split scan)
+  const float* XLsn;         // split scan: |x - c_list|^2 of each list-ordered row
+  float acc_scale;           // split scan: D^2 error per unit of r^2 assumed for kernel values
+  float acc_tol;             // split scan: largest relative error of s1 used unrescored
   uint32_t* err;
 };
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s);
-// Two-pass selection: per-query histogram bounds and E (zeroes the histogram
-// and counters), the threshold after pass 1, and the ranking of the keys
-// pass 2 wrote (a.cand and the segment fields unused).
-void launch_search_bounds(const int32_t* probes, const float* probe_d2, const float* rad,
-                          int64_t nq, int P, float err_scale, const int64_t* active, int64_t q0,
-                          const TwoPass& tp, cudaStream_t s);
-// stage 0 after the histogram pass (b*, the band edge, which queries to
-// refine); stage 1 after the refinement pass (the k-th sub-bin, the edge)
-void launch_search_threshold(const int64_t* q_real, int64_t nq, int k, int stage,
-                             const TwoPass& tp, cudaStream_t s);
-void launch_select_compact(const SelectArgs& a, const TwoPass& tp, cudaStream_t s);
 
 // ---- sample.cu --------------------------------------------------------------
 struct SampleArgs {

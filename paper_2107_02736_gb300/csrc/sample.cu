@@ -628,29 +628,25 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
     const int myrow = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
     const float4 yv = lane < dp4 ? y4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* X4 = reinterpret_cast<const float4*>(X);
-    // the rows' differences are formed twice (for the distances, then for
-    // the gradient after the reduction) from loads of the same addresses, the
-    // second served by L1, so only the row ids stay live across the shuffles
-    auto row_diff = [&](int rid) {
-      const float4 xv = rid >= 0 && lane < dp4 ? __ldg(X4 + (size_t)rid * dp4 + lane) : yv;
-      return make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
-    };
     for (int wb = warp * 8; wb < cnt; wb += kNW * 8) {
       prefetch_next_rows(X, dp, ids, cnt, wb + kNW * 8);
-      int rid[8];
+      float4 diff[8];
       float acc[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) rid[u] = wb + u < cnt ? ids[wb + u] : -1;
+      for (int u = 0; u < 8; ++u) {
+        const int rid = wb + u < cnt ? ids[wb + u] : -1;
+        const float4 xv = rid >= 0 && lane < dp4 ? __ldg(X4 + (size_t)rid * dp4 + lane) : yv;
+        diff[u] = make_float4(xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w);
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const float4 df = row_diff(rid[u]);
         if (kern == KDE_KERN_LAPLACIAN) {
-          acc[u] = (fabsf(df.x) + fabsf(df.y)) + (fabsf(df.z) + fabsf(df.w));
+          acc[u] = (fabsf(diff[u].x) + fabsf(diff[u].y)) + (fabsf(diff[u].z) + fabsf(diff[u].w));
         } else {
-          float t = df.x * df.x;
-          t = fmaf(df.y, df.y, t);
-          t = fmaf(df.z, df.z, t);
-          acc[u] = fmaf(df.w, df.w, t);
+          float t = diff[u].x * diff[u].x;
+          t = fmaf(diff[u].y, diff[u].y, t);
+          t = fmaf(diff[u].z, diff[u].z, t);
+          acc[u] = fmaf(diff[u].w, diff[u].w, t);
         }
       }
       float v4[4], v2[2], dist;
@@ -692,7 +688,7 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const float c = __shfl_sync(0xffffffffu, coef, ((u >> 2) << 4) | (((u >> 1) & 1) << 3) | ((u & 1) << 2));
-        const float4 df = row_diff(rid[u]);
+        const float4 df = diff[u];
         if (kern == KDE_KERN_LAPLACIAN) {
           gacc[0].x += c * (df.x > 0.f ? 1.f : (df.x < 0.f ? -1.f : 0.f));
           gacc[0].y += c * (df.y > 0.f ? 1.f : (df.y < 0.f ? -1.f : 0.f));
@@ -770,10 +766,8 @@ __device__ void grad_rows(const float* __restrict__ X, int dp, const float* __re
   }
 }
 
-// Narrow rows (NV <= 2: d <= 256) run four CTAs per SM within 64 registers a
-// thread; wider ones keep their NV float4 accumulators at two CTAs per SM.
 template <int G, int NV>
-__global__ void __launch_bounds__(kNT, NV <= 2 ? 4 : 2) k_estimate_grad(SampleArgs a) {
+__global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
   __shared__ EstSmem sm;
   __shared__ int tmp[kMaxK];
   extern __shared__ float4 dyn4[];

@@ -650,8 +650,10 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
 // Only candidates inside the FP32 error band of the k-th distance are
 // re-ranked with compensated distances.  Called by the whole block after a
 // barrier.
+// band_abs widens the re-ranked band to the keys' own error bound when they
+// come unrescored from the split scan (0 for FP32-rescored keys).
 __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
-                          const float* __restrict__ y) {
+                          const float* __restrict__ y, float band_abs) {
   __shared__ float s_red[kNW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (a.ids_only && K > a.k && a.kern != KDE_KERN_LAPLACIAN) {
@@ -661,7 +663,8 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
     // distance.
     const int k = a.k;
     const float T = __uint_as_float(smem_kth_dist(sm, K, k));
-    const float bw = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T;
+    const float bw =
+        fmaxf(4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T, band_abs);
     const uint32_t lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
     const uint32_t hi_key = dist_key(T + bw);
     unsigned long long* amb = reinterpret_cast<unsigned long long*>(sm.slot);  // 1024 keys
@@ -777,7 +780,7 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
     const float band_rel = 4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
     if (tid == 0) {
       const float dk = __uint_as_float((uint32_t)(sm.key[kk - 1] >> 32));
-      const float band = band_rel * dk;
+      const float band = fmaxf(band_rel * dk, band_abs);
       int lo = kk - 1, hi = kk;
       while (lo > 0 && __uint_as_float((uint32_t)(sm.key[lo - 1] >> 32)) >= dk - band) --lo;
       while (hi < K && __uint_as_float((uint32_t)(sm.key[hi] >> 32)) <= dk + band) ++hi;
@@ -862,6 +865,7 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   __shared__ int64_t s_seg[kMaxProbe + 1];
   __shared__ int64_t s_lstart[kMaxProbe];
   __shared__ int64_t s_llen[kMaxProbe];
+  __shared__ float s_dc[kMaxProbe];  // |y - c_l| of each probe
   const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
@@ -895,8 +899,10 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
       s_seg[p] = a.seg_off[q * a.P + p];
       s_lstart[p] = l >= 0 ? a.list_off[l] : 0;
       s_llen[p] = l >= 0 ? a.list_off[l + 1] - a.list_off[l] : 0;
+      s_dc[p] = 0.f;
       if (l < 0) continue;
       const float dc = sqrtf(a.probe_d2[q * a.P + p]), rl = a.rad[l];
+      s_dc[p] = dc;
       lo = fminf(lo, fmaxf(0.f, dc - rl));
       hi = fmaxf(hi, dc + rl);
     }
@@ -941,8 +947,67 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   // rescore in plain FP32 difference form: a warp takes 8 rows at once, each
   // lane one 16-byte piece of every row, all 8 loads issued together; a
   // reduce-scatter over the warp leaves row 4 b4 + 2 b3 + b2 (b_i the lane's
-  // bits) on the lanes with b1 = b0 = 0, which write its key
-  {
+  // bits) on the lanes with b1 = b0 = 0, which write its key.  The split
+  // scan's values are FP32-level already: their keys are formed directly.
+  //
+  // The split scan's keys are used unrescored when the kernel values they
+  // give are accurate enough for this query: the D^2 error of a candidate is
+  // taken as a.acc_scale r^2 with r = |x~| + |y~| its centred operands'
+  // magnitude (the scale the split's FP32 accumulation error follows; the
+  // constant is 2.5 times the largest measured), so the relative error of the
+  // neighbour sum is at most sum K e / sum K over the collected candidates;
+  // above a.acc_tol the query's rows are rescored like the BF16 scan's.  A caller that asks for
+  // the neighbours' distances (kde_search) gets FP32 difference-form ones, so
+  // those calls rescore too.
+  __shared__ int s_rescore;
+  bool rescore = a.rescore != 0 || a.nd2 != nullptr;
+  if (!rescore) {
+    const float inv = kernel_inv(a.kern, a.h);
+    float ksum = 0.f, esum = 0.f;
+    for (int j = tid; j < K; j += kNT) {
+      const int s = sm.slot[j];
+      int lo = 0, hi = a.P - 1;  // last segment with start <= s
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+      }
+      const int64_t off = s - s_seg[lo];
+      const bool row = off < s_llen[lo];
+      const float d2 = vals[s];
+      const int64_t pos = s_lstart[lo] + off;  // list-order row of the candidate
+      sm.key[j] = row ? pack_key(d2, a.perm[pos]) : ~0ull;
+      if (row && a.kern != KDE_KERN_LAPLACIAN) {
+        const float kv = kernel_from_dist(a.kern, d2, inv);
+        const float r = sqrtf(a.XLsn[pos]) + s_dc[lo];
+        const float ed = a.acc_scale * r * r;  // the D^2 error taken
+        // d log K / d D^2: 1 / (2 h^2) (Gaussian), 1 / (2 h r) (exponential)
+        const float rel = a.kern == KDE_KERN_GAUSSIAN
+                              ? ed * inv
+                              : ed * inv / (2.f * sqrtf(fmaxf(d2, ed)));
+        ksum += kv;
+        esum += kv * fminf(rel, 1.f);
+      }
+    }
+    ksum = warp_sum(ksum);
+    esum = warp_sum(esum);
+    __shared__ float s_ks[kNW], s_es[kNW];
+    if (lane == 0) {
+      s_ks[warp] = ksum;
+      s_es[warp] = esum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float kt = 0.f, et = 0.f;
+      for (int w = 0; w < kNW; ++w) {
+        kt += s_ks[w];
+        et += s_es[w];
+      }
+      s_rescore = et > a.acc_tol * kt ? 1 : 0;
+    }
+    __syncthreads();
+    rescore = s_rescore != 0;
+  }
+  if (rescore) {
     const int dp4 = a.dp >> 2;
     const float4* y4 = reinterpret_cast<const float4*>(y);
     const float4* X4 = reinterpret_cast<const float4*>(a.XL);
@@ -1020,191 +1085,7 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
     }
   }
   __syncthreads();
-  rank_keys(a, sm, K, q, y);
-}
-
-// --------------------------------------------------------------------------
-// Two-pass selection of the BF16 scan.
-// --------------------------------------------------------------------------
-// Per query: the histogram bounds [lo^2 - E, hi^2 + E] with lo, hi the
-// nearest and farthest any probed list's point can be (|y - c_l| -+ rad_l),
-// E = err_scale r^2 the scan's error bound (r = max over the probes of
-// |y - c_l| + rad_l, the centred operands' magnitude bound); clears the
-// histogram and the emission counters.  One warp per query.
-__global__ void k_search_bounds(const int32_t* __restrict__ probes,
-                                const float* __restrict__ probe_d2, const float* __restrict__ rad,
-                                int64_t nq, int P, float err_scale, TwoPass tp) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * kNW + (threadIdx.x >> 5);
-  if (q >= nq) return;
-  float lo = __int_as_float(0x7f800000), hi = 0.f;
-  for (int p = lane; p < P; p += 32) {
-    const int l = probes[q * P + p];
-    if (l < 0) continue;
-    const float dc = sqrtf(probe_d2[q * P + p]), rl = rad[l];
-    lo = fminf(lo, fmaxf(0.f, dc - rl));
-    hi = fmaxf(hi, dc + rl);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
-  for (int b = lane; b < kHistBins; b += 32) tp.hist[q * kHistBins + b] = 0u;
-  if (lane == 0) {
-    const float E = err_scale * hi * hi;
-    float hlo = 0.f, hscale = 0.f;
-    if (hi >= lo) {
-      const float lo2 = fmaxf(0.f, lo * lo * (1.f - 1e-5f) - E);
-      const float hi2 = hi * hi * (1.f + 1e-5f) + E;
-      hlo = lo2;
-      hscale = hi2 > lo2 ? (float)kHistBins / (hi2 - lo2) : 0.f;
-    }
-    tp.hlo[q] = hlo;
-    tp.hscale[q] = hscale;
-    tp.E[q] = E;
-    tp.cntA[q] = 0;
-    tp.cntB[q] = 0;
-  }
-}
-
-// The bin of a histogram holding the want-th smallest value (1 <= want <=
-// total) and the count below it, by a warp: four bins a lane, a warp scan of
-// the lanes' totals.  Every lane returns the same pair.
-__device__ __forceinline__ void warp_hist_rank(const uint32_t* __restrict__ h, uint32_t want,
-                                               int& bin_out, uint32_t& below_out) {
-  constexpr int kPer = kHistBins / 32;
-  const int lane = threadIdx.x & 31;
-  uint32_t c[kPer], s = 0;
-#pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    c[i] = h[lane * kPer + i];
-    s += c[i];
-  }
-  uint32_t incl = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const uint32_t excl = incl - s;
-  int bin = -1;
-  uint32_t below = 0;
-  if (excl < want && want <= incl) {
-    uint32_t run = excl;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {  // the running count crosses `want` in one bin
-      if (run < want && want <= run + c[i]) {
-        bin = lane * kPer + i;
-        below = run;
-      }
-      run += c[i];
-    }
-  }
-  const unsigned owner = __ballot_sync(0xffffffffu, bin >= 0);
-  const int src = owner ? __ffs(owner) - 1 : 0;
-  bin_out = __shfl_sync(0xffffffffu, bin, src);
-  below_out = __shfl_sync(0xffffffffu, below, src);
-}
-
-// Upper edge of bin b of a histogram from lo with `scale` bins per unit,
-// widened by a few units of rounding; +inf for the last bin (it also holds
-// every value beyond the range) or a degenerate range.
-__device__ __forceinline__ float bin_upper_edge(int b, float lo, float scale) {
-  if (!(scale > 0.f) || b >= kHistBins - 1) return __int_as_float(0x7f800000);
-  const float e = lo + (float)(b + 1) / scale;
-  return e + fabsf(e) * 1e-6f + 1e-30f;
-}
-
-// Stage 0, after the histogram pass: b* = the bin holding the k-th smallest
-// approximate distance t_k, and the band edge thr = (upper edge of b*) + 2E.
-// Every point of the exact top k has an approximate distance <= t_k + 2E (the
-// true k-th distance is at most t_k + E), so the candidates below bin b* and
-// those up to thr hold the exact top k.  A query with at most k candidates
-// takes them all (b* = kHistBins).  A bin b* with more than kRefineMin
-// candidates is marked for the refinement pass: its interval split into
-// kHistBins sub-bins, and k2 the k-th's rank among the bin's candidates.
-// Stage 1, after that pass: f* = the sub-bin holding rank k2, and the band
-// edge moves down to (upper edge of f*) + 2E.  One warp per query.
-__global__ void k_search_threshold(const int64_t* __restrict__ q_real, int64_t nq, int k,
-                                   int stage, TwoPass tp) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * kNW + (threadIdx.x >> 5);
-  if (q >= nq) return;
-  if (stage == 0) {
-    if (q_real[q] <= (int64_t)k) {
-      if (lane == 0) {
-        tp.bstar[q] = kHistBins;
-        tp.rbin[q] = -1;
-        tp.thr[q] = __int_as_float(0x7f800000);
-      }
-      return;
-    }
-    int b;
-    uint32_t below;
-    warp_hist_rank(tp.hist + q * kHistBins, (uint32_t)k, b, below);
-    const float lo = tp.hlo[q], scale = tp.hscale[q];
-    const uint32_t in_bin = tp.hist[q * kHistBins + b];
-    const bool refine = scale > 0.f && in_bin > (uint32_t)kRefineMin;
-    if (refine)
-      for (int i = lane; i < kHistBins; i += 32) tp.hist2[q * kHistBins + i] = 0u;
-    if (lane == 0) {
-      tp.bstar[q] = b;
-      tp.thr[q] = bin_upper_edge(b, lo, scale) + 2.f * tp.E[q];
-      tp.rbin[q] = refine ? b : -1;
-      if (refine) {
-        tp.flo[q] = lo + (float)b / scale;
-        tp.fscale[q] = scale * (float)kHistBins;
-        tp.k2[q] = k - (int)below;
-      }
-      tp.fstar[q] = 0;
-    }
-    return;
-  }
-  if (tp.rbin[q] < 0) return;
-  int f;
-  uint32_t below;
-  warp_hist_rank(tp.hist2 + q * kHistBins, (uint32_t)tp.k2[q], f, below);
-  if (lane == 0) {
-    tp.fstar[q] = f;
-    // the last sub-bin ends where the bin b* ends
-    const float edge = f < kHistBins - 1 ? bin_upper_edge(f, tp.flo[q], tp.fscale[q])
-                                         : bin_upper_edge(tp.rbin[q], tp.hlo[q], tp.hscale[q]);
-    tp.thr[q] = edge + 2.f * tp.E[q];
-  }
-}
-
-// Ranking of the keys the emission pass wrote: region A (the candidates
-// below the k-th bin) and region B (the band), both FP32-rescored.  More
-// than fits in either region marks the query uncertified (kde_stats).
-__global__ void __launch_bounds__(kNT, 4) k_select_compact(SelectArgs a, TwoPass tp) {
-  extern __shared__ uint4 sel_dyn4[];
-  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
-  const int64_t q = blockIdx.x;
-  const int tid = threadIdx.x;
-  if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
-    for (int j = tid; j < a.k; j += kNT) {
-      a.nbr[q * a.k + j] = -1;
-      if (a.nd2) a.nd2[q * a.k + j] = __int_as_float(0x7f800000);
-    }
-    if (tid == 0) {
-      if (a.s1) a.s1[q] = 0.f;
-      if (a.kcount) a.kcount[q] = 0;
-    }
-    return;
-  }
-  const int capB = kSelectCap - tp.kA;
-  const int cA = tp.cntA[q], cB = tp.cntB[q];
-  const int nA = min(cA, tp.kA), nB = min(cB, capB);
-  if (tid == 0 && (cA > tp.kA || cB > capB)) {
-    atomicOr(a.err, KDE_ERRBIT_MARGIN);
-    atomicAdd(a.err + 1, 1u);
-  }
-  const unsigned long long* kq = tp.keys + q * kSelectCap;
-  for (int j = tid; j < nA; j += kNT) sm.key[j] = kq[j];
-  for (int j = tid; j < nB; j += kNT) sm.key[nA + j] = kq[tp.kA + j];
-  __syncthreads();
-  rank_keys(a, sm, nA + nB, q, a.Y + q * a.dp);
+  rank_keys(a, sm, K, q, y, rescore ? 0.f : 2.f * s_E);
 }
 
 }  // namespace
@@ -1271,29 +1152,6 @@ void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
   set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), sizeof(SelectSmem));
   k_select_neighbors<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a);
-}
-
-void launch_search_bounds(const int32_t* probes, const float* probe_d2, const float* rad,
-                          int64_t nq, int P, float err_scale, const int64_t* active, int64_t q0,
-                          const TwoPass& tp, cudaStream_t s) {
-  (void)active;  // an inactive row has no probes: its bounds select nothing
-  (void)q0;
-  if (nq <= 0) return;
-  k_search_bounds<<<(unsigned)((nq + kNW - 1) / kNW), kNT, 0, s>>>(probes, probe_d2, rad, nq, P,
-                                                                 err_scale, tp);
-}
-
-void launch_search_threshold(const int64_t* q_real, int64_t nq, int k, int stage,
-                             const TwoPass& tp, cudaStream_t s) {
-  if (nq <= 0) return;
-  k_search_threshold<<<(unsigned)((nq + kNW - 1) / kNW), kNT, 0, s>>>(q_real, nq, k, stage,
-                                                                    tp);
-}
-
-void launch_select_compact(const SelectArgs& a, const TwoPass& tp, cudaStream_t s) {
-  if (a.nq <= 0) return;
-  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_compact), sizeof(SelectSmem));
-  k_select_compact<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a, tp);
 }
 
 }  // namespace deann

@@ -56,17 +56,19 @@ def test_stage_work_and_alu_peak():
     # the estimator's bytes are m rows of d FP32 values (+ query, ids, output)
     b, f = bench.stage_work("estimate", 10, 1000, 128, 8, 16, 100, 5.0)
     assert b == 10 * (100 * 128 * 4 + 128 * 4 + 16 * 4 + 4) and f == 0.0
-    # BF16 list-major search: the lists once in BF16 and once in FP32, ~k keys
+    # the scan reads the lists once and writes every candidate's value
     b, f = bench.stage_work("scan", 10, 1000, 128, 8, 16, 100, 50.0)
-    assert f == 2.0 * 10 * 50.0 * 128
-    assert b == 1000 * 128 * 2 + 1000 * 128 * 4 + 10 * 16 * 8
-    b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0)
-    assert b == 10 * (16 * 8 + 16 * 4 + 4)
-    # FP32 scan: every candidate's value to HBM and back, rows per query
+    assert f == 2.0 * 10 * 50.0 * 128 and b == 1000 * 128 * 2 + 10 * 50.0 * 4
     b, _ = bench.stage_work("scan", 10, 1000, 130, 8, 16, 100, 50.0, "fp32")
     assert b == 1000 * 132 * 4 + 10 * 50.0 * 4
+    b, _ = bench.stage_work("scan", 10, 1000, 130, 8, 16, 100, 50.0, "bf16x3")
+    assert b == 3 * 1000 * 192 * 2 + 10 * 50.0 * 4
+    # the selection reads them back and, unless the scan was the split one,
+    # the k neighbours' FP32 rows
     b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0, "fp32")
     assert b == 10 * (50.0 * 4 + 16 * 128 * 4 + 16 * 4)
+    b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0, "bf16x3")
+    assert b == 10 * (50.0 * 4 + 16 * 4)
     assert bench.fp32_alu_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
@@ -150,7 +152,7 @@ def _representative_headline():
                 "d2h_bytes_per_step": 40000},
         "gpu_launches": 480,
         "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
-                   "samples": 7, "samples_in_region": 7, "samples_total": 500},
+                   "samples": 7},
         "roofline": {"bound": "hbm", "achieved": 7412.3456, "peak": 6781.4, "unit": "GB/s",
                      "frac": 1.0930123, "traffic": 17212345678, "stage": "estimate",
                      "ms_per_call": 2.7712345, "t_min_ms": 3.0212345,
@@ -159,35 +161,40 @@ def _representative_headline():
                                                      "select", "estimate")},
         "path_roofline": {"frac": 0.8912345, "t_min_ms": 4.5712345},
         "cpu_baseline": {"value": 1321.12345, "unit": "queries/s", "cores": 16, "kind": "oracle",
-                         "sample": "first 16384 of 10000 test queries, IVF search + DEANN in "
-                                   "FP64, 12.3 s", "single_thread_qps": 72.512345},
+                         "sample": "10000 test queries, IVF search + DEANN, FP64, 12.3 s",
+                         "single_thread_qps": 72.512345},
         "baselines": {"exact": {"qps": 551234.5, "tflops_algorithmic": 141.23456,
                                 "frac_algorithmic": 0.0741234, "split_products": 6,
                                 "peak": 1901.8},
                       "rs_qps": 12612.345, "rs_m": 1310720, "rs_rel_err": 0.0089123,
-                      "fp32_scan": r, "deannp": r},
+                      "scans": {"fp32": r, "bf16": r, "bf16x3": r}, "deannp": r},
         "forms": {"fixed_params_exp": {"deannp_qps": 2.5e6, "deannp_err": 0.036,
                                        "deann_qps": 2.1e6, "deann_err": 0.04, "recall": 0.83},
                   "recall": 0.9912345, "adjoint": {"qps": 2.02e6, "frac": 0.84123},
                   "mean_shift_qsteps": 6.8e6, "exponential": {"row": r, "exact_qps": 91234.5},
                   "d784": {"exact_qps": 121234.0, "fp32_fixed": r, "fp32": r, "bf16_fixed": r,
-                           "bf16": r, "same_nbrs": True},
+                           "bf16": r, "bf16x3_fixed": r, "bf16x3": r, "same_nbrs": True},
                   "n4M_batched": {"fixed": r, "tuned": r,
                                   "one_call_qps": [1.45123e6, 1.41234e6]}},
-        "row_fields": bench.ROW_FIELDS, "margin_failures": 0, "build_s": 3.2123456,
+        "margin_failures": 0, "build_s": 3.2123456,
     }, 4)
 
 
 def test_headline_line_fits_the_driver_tail():
-    """The full headline, with every summary, fits in the 2,700 bytes kept for
-    it; when it would not, optional sections move to a side line and the
-    required keys stay."""
+    """The full headline fits in the bytes kept for it and the forms summary
+    printed before it in its own; together they fit the driver's 3 KB tail.
+    When the headline would not fit, optional sections move to a side line and
+    the required keys stay."""
+    import json
     line = _representative_headline()
+    forms = dict(line.pop("forms"), row_fields=bench.ROW_FIELDS)
     text, moved = bench.fit_headline(line)
     assert moved == {} and len(text) <= bench.HEADLINE_LIMIT, len(text)
+    ftext = json.dumps({"side": "forms", **bench.sig(forms, 4)})
+    assert len(ftext) <= bench.FORMS_LIMIT, len(ftext)
+    assert len(text) + len(ftext) + 40 <= 3000
     text, moved = bench.fit_headline(line, limit=1500)
-    assert len(text) <= 1500 and "forms" in moved
-    import json
+    assert len(text) <= 1500 and "baselines" in moved
     got = json.loads(text)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                 "higher_is_better", "dtype", "config", "e2e", "clocks", "roofline",

@@ -63,7 +63,7 @@ def test_adjoint_wide_rows(pkg, d):
     assert np.allclose(dl.cpu().numpy(), wdl, rtol=1e-4, atol=1e-9)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_most_probes(pkg, precision):
     X, Y = _data(30_000, 8, 50, seed=4)
     index = pkg.KDEIndex(_dev(X), "gaussian", 1.0, nlist=512, seed=3)
@@ -118,7 +118,7 @@ def test_k_equals_n_at_the_largest_k(pkg):
     assert_kde_close(out.cpu().numpy(), oracle.exact(X, Y, "laplacian", 3.0))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_largest_k_search_and_estimate(pkg, precision):
     """k = 2048 of n = 30,000 through the IVF: neighbours against the oracle's
     search of the same lists, estimates against the oracle with them."""

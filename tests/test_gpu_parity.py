@@ -311,15 +311,70 @@ def test_bf16_tensor_core_scan(pkg, which):
                      oracle.deann(X, Y, "gaussian", 2.0, nb.cpu().numpy(), 300, 9))
 
 
-def test_bf16_scan_many_queries_per_list(pkg):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_bf16_scan_many_queries_per_list(pkg, precision):
     """Hundreds of queries probing the same lists: several CTAs per list, ragged
     last query group and ragged last 128-point tile."""
     X, Y, _ = workloads.mixture_iso(n=3000, d=32, nq=900, n_centres=3)
     index = pkg.KDEIndex(_dev(X), "gaussian", 2.0, nlist=5, seed=4)
     C, assign = index.export_ivf()
-    nbr, _ = index.search(_dev(Y), 64, nprobe=2, precision=1)
+    nbr, _ = index.search(_dev(Y), 64, nprobe=2, precision=precision)
     _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, 2, 64)
     assert_neighbours_match(X, Y, nbr.cpu().numpy(), want, want_d2)
+
+
+@pytest.mark.parametrize("which", ["iso16", "embed128", "unit300", "sparse784"])
+@pytest.mark.parametrize("kernel", ["gaussian", "exponential", "laplacian"])
+def test_split_scan_matches_oracle(pkg, which, kernel):
+    """The three-way split BF16 scan (precision 2): its distances are used
+    without rescoring the neighbours' rows, so the sorted neighbours, their
+    distances and the estimates (the neighbours' kernel values come from the
+    scan) must match the oracle as the rescored paths do; sets equal the FP32
+    scan's."""
+    if which == "iso16":
+        X, Y, _ = workloads.mixture_iso(n=7000, d=16, nq=300)
+        h = 2.0
+    elif which == "embed128":
+        X, Y, _ = workloads.mixture_embed(n=9000, nq=300, n_centres=30)
+        h = 6.0
+    elif which == "unit300":
+        X, Y, _ = workloads.unit_powerlaw(n=6000, nq=200, n_centres=40)
+        h = 0.3
+    else:
+        X, Y, _ = workloads.sparse_image(n=5000, nq=120)
+        h = 1.5
+    if kernel == "laplacian":
+        h *= 3.0
+    index = pkg.KDEIndex(_dev(X), kernel, h, nlist=12, seed=2)
+    C, assign = index.export_ivf()
+    for P, k in ((1, 25), (3, 60), (12, 100)):
+        nbr, d2 = index.search(_dev(Y), k, nprobe=P, precision=2)
+        _, want, want_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y, P, k)
+        assert_neighbours_match(X, Y, nbr.cpu().numpy(), want, want_d2)
+        # the split's error is absolute, on the scale of the centred operands:
+        # bounded against each query's k-th distance
+        d2 = d2.cpu().numpy().astype(np.float64)
+        scale = np.maximum(np.where(want >= 0, want_d2, 0.0).max(1, keepdims=True), 1.0)
+        ok = want >= 0
+        assert np.all((np.abs(d2 - want_d2) <= 1e-5 * scale)[ok])
+        f32, _ = index.search(_dev(Y), k, nprobe=P, precision=0)
+        assert np.array_equal(np.sort(f32.cpu().numpy(), 1), np.sort(nbr.cpu().numpy(), 1))
+    assert index.margin_failures() == 0
+    out, nb = index.query(_dev(Y), 30, 300, nprobe=3, seed=9, precision=2, return_neighbors=True)
+    assert_kde_close(out.cpu().numpy(),
+                     oracle.deann(X, Y, kernel, h, nb.cpu().numpy(), 300, 9))
+    # the neighbour part alone (m = 0): s1 / n from the scan's values
+    out0, nb0 = index.query(_dev(Y), 60, 0, nprobe=3, precision=2, return_neighbors=True)
+    assert_kde_close(out0.cpu().numpy(),
+                     oracle.deann(X, Y, kernel, h, nb0.cpu().numpy(), 0, 0))
+
+
+def test_split_scan_rejects_wide_rows(pkg):
+    X, Y = _data(400, 1200, 3, seed=2)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 30.0, nlist=4)
+    with pytest.raises(pkg.KDEError, match="EINVAL"):
+        index.search(_dev(Y), 5, nprobe=1, precision=2)
+    assert index.search(_dev(Y), 5, nprobe=1, precision=1)[0].shape == (3, 5)
 
 
 def test_query_k_equals_n_is_exact(pkg):
@@ -367,7 +422,7 @@ def test_gradient_matches_oracle(pkg, kernel, d):
 
 
 @pytest.mark.parametrize("kernel,precision", [("gaussian", 1), ("exponential", 0),
-                                              ("laplacian", 0)])
+                                              ("laplacian", 0), ("gaussian", 2)])
 def test_grad_entry_point_matches_oracle(pkg, kernel, precision):
     """kde_grad (search + adjoint in one call, dlogh reduced on the device)
     against the oracle: the IVF search re-run from the exported index, then

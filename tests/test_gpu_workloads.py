@@ -56,7 +56,7 @@ def embed(pkg):
     return X, Y, index, C.numpy(), assign.numpy()
 
 
-@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("precision", [1, 0, 2])
 def test_embed_full_size_sampled(embed, precision):
     X, Y, index, C, assign = embed
     k, m, P, h = 1536, 4000, 8, 12.85
