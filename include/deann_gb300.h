@@ -122,8 +122,20 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
                      int32_t nlist, uint64_t seed, const kde_opts* opts, kde_index** out);
 
 /* kde_free -- release the index and all device memory it owns (NULL is a
- * no-op).  Synchronises the device first. */
+ * no-op).  Synchronises the device first.  For a view (kde_index_view) only
+ * the view's own memory is released. */
 void kde_free(kde_index* index);
+
+/* kde_index_view -- a second handle on the same index for concurrent work:
+ * it shares the dataset copies, the inverted file and (when prepared first on
+ * the index) the permuted copy of Algorithm 2, and has its own scratch
+ * memory, device error words, statistics and profiling state, so calls on
+ * different views may run on different streams at the same time.  The view
+ * starts with the index's bandwidth; kde_set_bandwidth on either changes only
+ * that handle.  The index must outlive its views; free each with kde_free.
+ * Views of a view are refused (take another view of the index).
+ * Errors: EINVAL, ENOMEM. */
+kde_status kde_index_view(kde_index* index, kde_index** out);
 
 /* kde_prepare_permuted -- Algorithm 2's preprocessing: a random permutation
  * pi of [0, n) and the permuted copy XP[i] = X[pi(i)] (n x d FP32 more device

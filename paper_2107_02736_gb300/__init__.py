@@ -92,6 +92,7 @@ def load_library():
         "kde_reserve": [P, i64, i32, i32, i32, O],
         "kde_prepare_permuted": [P, P, O],
         "kde_fit_bandwidth": [P, P, i64, i32, i32, i32, u64, i32, f32, P, P, P, O],
+        "kde_index_view": [P, ctypes.POINTER(ctypes.c_void_p)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +175,18 @@ class KDEIndex:
         if Y.dim() != 2 or Y.shape[1] != self.d:
             raise ValueError(f"Y must be nq x {self.d}")
         return Y
+
+    def view(self) -> "KDEIndex":
+        """A second handle on this index (kde_index_view): the same data, its
+        own scratch, so that it can serve work on another stream at the same
+        time.  This index must outlive the view."""
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self._device):
+            _check(_lib.kde_index_view(self._h, ctypes.byref(handle)))
+        v = KDEIndex.__new__(KDEIndex)
+        v._h, v._device, v.n, v.d = handle, self._device, self.n, self.d
+        v.kernel, v.nlist, v._base = self.kernel, self.nlist, self
+        return v
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -477,49 +490,102 @@ class GraphedQuery:
 class BatchServer:
     """Serves uneven batches with CUDA graphs captured per power-of-two
     capacity class (16 ... max_batch); the query ids run on across batches.
+
+    With streams > 1 consecutive batches go round-robin to that many CUDA
+    streams, each with its own view of the index (its own scratch) and its
+    own graphs, so that small batches, which leave most of the GPU idle, run
+    side by side.  A batch's results stay valid until its stream serves again
+    (`streams` calls later); copy them out before then.  Work on the caller's
+    stream before a call is ordered before the batch, and the caller's stream
+    waits for the batch's stream when it uses the result (sync()).
     With neighbors=True each call returns (estimates, neighbour ids) and
-    backward() runs the adjoint of the last batch served (its sets fixed)."""
+    backward() runs the adjoint of the last batch served (its sets fixed) on
+    that batch's stream."""
 
     def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192,
-                 sample_mode=0, neighbors=False):
+                 sample_mode=0, neighbors=False, streams=1):
         self.index, self.args = index, dict(k=k, m=m, nprobe=nprobe, seed=seed,
                                             precision=precision, sample_mode=sample_mode,
                                             neighbors=neighbors)
         self.max_batch = int(max_batch)
-        # the scratch for the largest capacity class up front, so that every
-        # graph is captured on the same buffer
         cap = 16
         while cap < self.max_batch:
             cap *= 2
-        index.reserve(cap, k, m, nprobe, precision)
-        self.graphs = {}
+        dev = index.device
+        self.lanes = []
+        for i in range(max(1, int(streams))):
+            ix = index if i == 0 else index.view()
+            # the scratch for the largest capacity class up front, so that every
+            # graph of the lane is captured on the same buffer
+            ix.reserve(cap, k, m, nprobe, precision)
+            self.lanes.append({"index": ix, "graphs": {},
+                               "stream": (torch.cuda.current_stream(dev) if i == 0 and streams <= 1
+                                          else torch.cuda.Stream(device=dev))})
+        self.turn = 0
         self.next_qid = 0
         self.last_qid = 0
+        self.last_lane = self.lanes[0]
 
-    def _graph(self, nb):
+    @property
+    def graphs(self):
+        """Capacity classes captured so far (over all lanes)."""
+        caps = {}
+        for lane in self.lanes:
+            caps.update(lane["graphs"])
+        return caps
+
+    def _graph(self, lane, nb):
         cap = 16
         while cap < nb:
             cap *= 2
-        if cap not in self.graphs:
-            self.graphs[cap] = GraphedQuery(self.index, cap, **self.args)
-        return self.graphs[cap]
+        if cap not in lane["graphs"]:
+            with torch.cuda.stream(lane["stream"]):
+                lane["graphs"][cap] = GraphedQuery(lane["index"], cap, **self.args)
+        return lane["graphs"][cap]
 
-    def __call__(self, Yb):
+    def __call__(self, Yb, out=None):
+        """Serves one batch; returns the graph's result views.  With `out`
+        given (a float32 tensor of the batch's length), the estimates are
+        copied there on the batch's stream, so they survive the lane's next
+        batch."""
         nb = int(Yb.shape[0])
         if nb > self.max_batch:
             raise ValueError(f"batch of {nb} exceeds max_batch {self.max_batch}")
-        out = self._graph(nb)(Yb, self.next_qid)
-        self.last_qid = self.next_qid
+        lane = self.lanes[self.turn % len(self.lanes)]
+        self.turn += 1
+        caller = torch.cuda.current_stream(self.index.device)
+        lane["stream"].wait_stream(caller)
+        g = self._graph(lane, nb)
+        with torch.cuda.stream(lane["stream"]):
+            res = g(Yb, self.next_qid)
+            if out is not None:
+                out.copy_(res[0] if isinstance(res, tuple) else res)
+        self.last_qid, self.last_lane = self.next_qid, lane
         self.next_qid += nb
-        return out
+        return res
+
+    @property
+    def last_stream(self):
+        """The stream of the last batch served: its results (and those of
+        backward()) are written there."""
+        return self.last_lane["stream"]
+
+    def sync(self):
+        """Makes the caller's stream wait for every lane's work."""
+        caller = torch.cuda.current_stream(self.index.device)
+        for lane in self.lanes:
+            caller.wait_stream(lane["stream"])
 
     def backward(self, Yb, nbr, gout=None):
         """(estimate, dY, dlogh per query) of the last batch served, from its
-        neighbour ids and its regenerated sample streams."""
-        a = self.args
-        return self.index.grad_with_neighbors(Yb, nbr, a["m"], seed=a["seed"], gout=gout,
-                                              sample_mode=a["sample_mode"],
-                                              qid_offset=self.last_qid)
+        neighbour ids and its regenerated sample streams.  They are computed
+        on the batch's stream (last_stream): read them there, or after
+        sync()."""
+        a, lane = self.args, self.last_lane
+        with torch.cuda.stream(lane["stream"]):
+            return lane["index"].grad_with_neighbors(Yb, nbr, a["m"], seed=a["seed"], gout=gout,
+                                                     sample_mode=a["sample_mode"],
+                                                     qid_offset=self.last_qid)
 
 
 class DeannKDE(torch.autograd.Function):

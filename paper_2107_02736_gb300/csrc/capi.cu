@@ -344,7 +344,7 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     {
       // with one list the probe is list 0; the step still yields |y - c_0|^2
       StageTimer t(ix, ST_COARSE, st, 2);
-      launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, st);
+      launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, active, q0, st);
       launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
                            s.probes, s.probe_d2, active, q0, st);
     }
@@ -754,10 +754,48 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   return KDE_OK;
 }
 
+kde_status kde_index_view(kde_index* ix, kde_index** out) {
+  if (out == nullptr) return fail(KDE_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  TRY(check_index(ix));
+  if (ix->base != nullptr) return fail(KDE_EINVAL, "a view of a view: take the view of its base");
+  DeviceGuard g(ix->device);
+  kde_index* v = new kde_index(*ix);
+  // shared: the dataset copies, the inverted file, tensor maps, the permuted
+  // copy; the view's own: scratch, error words, statistics and profiling
+  v->base = ix;
+  v->scratch = deann::Arena();
+  v->retired.clear();
+  v->events.clear();
+  v->prof = false;
+  v->margin_failures = 0;
+  for (int i = 0; i < kde_index::kStages; ++i) v->launches[i] = v->calls[i] = 0;
+  v->err = nullptr;
+  if (dev_alloc(&v->err, 4) != KDE_OK || cudaMemset(v->err, 0, 4 * sizeof(uint32_t)) !=
+                                             cudaSuccess) {
+    cudaFree(v->err);
+    delete v;
+    return fail(KDE_ENOMEM, "could not allocate the view's error words");
+  }
+  *out = v;
+  return KDE_OK;
+}
+
 void kde_free(kde_index* ix) {
   if (ix == nullptr) return;
   DeviceGuard g(ix->device);
   cudaDeviceSynchronize();
+  if (ix->base != nullptr) {  // a view frees only what is its own
+    cudaFree(ix->err);
+    if (ix->scratch.base) cudaFree(ix->scratch.base);
+    for (char* p : ix->retired) cudaFree(p);
+    for (const auto& e : ix->events) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    delete ix;
+    return;
+  }
   cudaFree(ix->X);
   cudaFree(ix->Xn);
   cudaFree(ix->XL);
@@ -792,6 +830,8 @@ void kde_free(kde_index* ix) {
 }
 
 kde_status kde_prepare_permuted(kde_index* ix, int32_t* perm_out, const kde_opts* opts) {
+  if (ix != nullptr && ix->base != nullptr && ix->XP == nullptr)
+    return fail(KDE_ESTATE, "prepare the permuted copy on the base index before taking views");
   TRY(check_index(ix));
   const kde_opts* o = opts ? opts : &kDefaultOpts;
   TRY(check_opts(o));

@@ -62,6 +62,7 @@ struct Arena {
 }  // namespace deann
 
 struct kde_index {
+  const kde_index* base = nullptr;  // non-null: a view sharing base's device data
   int device = 0;
   int64_t n = 0;
   int d = 0;
@@ -171,8 +172,10 @@ void launch_exact_simt(const float* Y, const float* Yn, int64_t nq, const float*
                        double* acc, float* out, cudaStream_t s);
 void launch_assign_simt(const float* P, int64_t np, const float* C, int L, int d, int dp,
                         int32_t* assign, float* best_d2, cudaStream_t s);
+// active / row0: rows row0 + q >= *active (when active is not NULL) are skipped
 void launch_dist_matrix(const float* Y, const float* Yn, int64_t nq, const float* C,
-                        const float* Cn, int L, int dp, float* D, cudaStream_t s);
+                        const float* Cn, int L, int dp, float* D, const int64_t* active,
+                        int64_t row0, cudaStream_t s);
 struct ScanPlan {
   const int32_t* pair_q;      // query of each (query, probe) pair, bucketed by list
   const int64_t* pair_dst;    // destination offset of the pair's segment in cand

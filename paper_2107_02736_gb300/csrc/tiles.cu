@@ -253,12 +253,16 @@ __global__ void __launch_bounds__(256) k_dist_matrix(const float* __restrict__ Y
                                                      const float* __restrict__ Yn, int64_t nq,
                                                      const float* __restrict__ C,
                                                      const float* __restrict__ Cn, int L, int dp,
-                                                     float* __restrict__ D) {
+                                                     float* __restrict__ D,
+                                                     const int64_t* __restrict__ active,
+                                                     int64_t row0) {
   __shared__ TileSmem sm;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t q0 = (int64_t)blockIdx.x * kTile;
   const int c0 = blockIdx.y * kTile;
+  // rows at or past the device row count get no probes: no distances needed
+  if (active != nullptr && row0 + q0 >= *active) return;
   const float* aptr[2];
   const float* bptr[2];
 #pragma unroll
@@ -392,9 +396,10 @@ void launch_assign_simt(const float* P, int64_t np, const float* C, int L, int d
 }
 
 void launch_dist_matrix(const float* Y, const float* Yn, int64_t nq, const float* C,
-                        const float* Cn, int L, int dp, float* D, cudaStream_t s) {
+                        const float* Cn, int L, int dp, float* D, const int64_t* active,
+                        int64_t row0, cudaStream_t s) {
   dim3 grid((unsigned)((nq + kTile - 1) / kTile), (unsigned)((L + kTile - 1) / kTile));
-  k_dist_matrix<<<grid, 256, 0, s>>>(Y, Yn, nq, C, Cn, L, dp, D);
+  k_dist_matrix<<<grid, 256, 0, s>>>(Y, Yn, nq, C, Cn, L, dp, D, active, row0);
 }
 
 void launch_scan_simt(const float* Y, const float* Yn, const float* XL, const float* XLn,

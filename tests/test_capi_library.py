@@ -110,3 +110,10 @@ def test_structs_match_binding(tmp_path, cname, pyname):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(mirror)] + [getattr(mirror, f).offset for f in fields]
     assert got == want
+
+
+def test_view_argument_errors_without_gpu(lib):
+    out = ctypes.c_void_p()
+    assert lib.kde_index_view(None, ctypes.byref(out)) == 1
+    assert b"NULL" in lib.kde_last_error()
+    assert lib.kde_index_view(None, None) == 1

@@ -208,6 +208,69 @@ def test_graph_replays_serve_uneven_batches(pkg):
     assert len(server.graphs) >= 3
 
 
+def _data_small(n=3000, d=8, nq=40, seed=0):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((n, d)).astype(np.float32),
+            rng.standard_normal((nq, d)).astype(np.float32))
+
+
+def test_batches_on_several_streams_equal_direct_calls(pkg):
+    """Uneven batches served round-robin on three streams, each with its own
+    view of the index (own scratch and graphs), give exactly the direct calls'
+    results, and the backward passes on their lanes match the oracle's
+    gradient with the same sets."""
+    X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=2_000, n_centres=100)
+    h, k, m = 0.2, 100, 1000
+    index = pkg.KDEIndex(_dev(X), "exponential", h, nlist=64, seed=5)
+    sizes = workloads.uneven_batches(total=2_000, nbatch=12, lo=16, hi=700, seed=4)
+    server = pkg.BatchServer(index, k, m, nprobe=4, seed=11, precision=2, max_batch=1024,
+                             neighbors=True, streams=3)
+    Yd = _dev(Y)
+    res = torch.empty(Y.shape[0], dtype=torch.float32, device="cuda")
+    start, grads = 0, []
+    for b, nb in enumerate(sizes):
+        nb = int(nb)
+        Yb = Yd[start:start + nb]
+        _, ids = server(Yb, out=res[start:start + nb])
+        if b % 4 == 0:
+            est, dY, dl = server.backward(Yb, ids)
+            with torch.cuda.stream(server.last_stream):  # where both were written
+                grads.append((start, nb, ids.clone(), dY.clone()))
+        start += nb
+    server.sync()
+    torch.cuda.synchronize()
+    want = index.query(Yd, k, m, nprobe=4, seed=11, precision=2)
+    assert torch.equal(res, want)
+    assert len(server.lanes) == 3 and len(server.graphs) >= 3
+    for start, nb, ids, dY in grads:
+        r = nb // 2
+        q = start + r
+        _, w_dY, _ = oracle.deann_grad(X, Y[q:q + 1], "exponential", h,
+                                       ids[r:r + 1].cpu().numpy(), m, 11, qid_offset=q)
+        assert np.linalg.norm(dY[r].cpu().numpy() - w_dY[0]) <= 1e-4 * np.linalg.norm(w_dY[0])
+
+
+def test_index_views_share_data_and_keep_their_own_state(pkg):
+    """A view answers like its index, keeps its own bandwidth and error
+    state, and a second view of a view is refused."""
+    X, Y = _data_small()
+    index = pkg.KDEIndex(_dev(X), "gaussian", 1.5, nlist=8, seed=2)
+    v = index.view()
+    a = index.query(_dev(Y), 20, 300, nprobe=3, seed=4, precision=1)
+    b = v.query(_dev(Y), 20, 300, nprobe=3, seed=4, precision=1)
+    assert torch.equal(a, b) and v.h == index.h
+    v.set_bandwidth(3.0)
+    assert v.h == 3.0 and index.h == 1.5
+    bad = torch.tensor([[0, 5000]], dtype=torch.int32)
+    with pytest.raises(pkg.KDEError, match="EINVAL"):
+        v.query_with_neighbors(torch.from_numpy(Y[:1]), bad, 10)
+    index.sync()  # the index's own error words are clean
+    with pytest.raises(pkg.KDEError, match="EINVAL"):
+        v.view()
+    v.close()
+    assert torch.equal(index.query(_dev(Y), 20, 300, nprobe=3, seed=4, precision=1), a)
+
+
 def test_graphs_stay_valid_when_the_scratch_grows(pkg):
     """A graph captured while the index's scratch was small is replayed after
     larger calls (other shapes, the FP32 scan) made the library allocate a
