@@ -191,6 +191,8 @@ struct SearchBufs {
   int64_t *ord_cnt = nullptr, *ord_off = nullptr, *ord_fill = nullptr;
   int32_t* order = nullptr;
   float* cand = nullptr;
+  void* Ys = nullptr;     // the queries' BF16 parts [3][qc][dpb] (tensor-core coarse quantiser)
+  float* ysn = nullptr;   // |y - mean|^2
 };
 
 constexpr size_t kCandCap = size_t(8) << 30;  // candidate buffer per chunk of queries
@@ -220,6 +222,8 @@ void carve_search(Bump& b, const kde_index* ix, int64_t nq, int P, SearchBufs& s
   s.ord_off = b.take<int64_t>(L + 1);
   s.ord_fill = b.take<int64_t>(L);
   s.order = b.take<int32_t>(qc);
+  s.Ys = b.take<uint16_t>((size_t)3 * qc * ix->dpb);
+  s.ysn = b.take<float>(qc);
   s.cand = b.take<float>((size_t)qc * (size_t)P * ((size_t)std::max<int64_t>(ix->max_list, 1) + 32));
 }
 
@@ -342,9 +346,20 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     const float* Yc = cb.Yp + q0 * ix->dp;
     const float* Ync = cb.Yn + q0;
     {
-      // with one list the probe is list 0; the step still yields |y - c_0|^2
-      StageTimer t(ix, ST_COARSE, st, 2);
-      launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, active, q0, st);
+      // with one list the probe is list 0; the step still yields |y - c_0|^2.
+      // The tensor-core scans take the query-centroid distances from the
+      // split-BF16 tensor-core GEMM, the FP32 scan from the SIMT tiles.
+      const bool tc_coarse = (precision == KDE_PREC_BF16 || precision == KDE_PREC_BF16X3) &&
+                             ix->cs_ok;
+      StageTimer t(ix, ST_COARSE, st, tc_coarse ? 3 : 2);
+      if (tc_coarse) {
+        launch_split3(Yc, nc, ix->dp, ix->mean, s.Ys, nc, ix->dpb, s.ysn, st);
+        if (!launch_coarse_tc(ix->tmap_cs, ix->csn, L, s.Ys, s.ysn, nc, ix->dpb, s.D, active, q0,
+                              ix->err, st))
+          return fail(KDE_ECUDA, "could not configure the tensor-core coarse quantiser");
+      } else {
+        launch_dist_matrix(Yc, Ync, nc, ix->C, ix->Cn, L, ix->dp, s.D, active, q0, st);
+      }
       launch_select_probes(s.D, nc, L, Yc, ix->d, ix->dp, ix->C, P, std::max(8, P / 2),
                            s.probes, s.probe_d2, active, q0, st);
     }
@@ -651,6 +666,7 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   cnt.take<uint32_t>((n + 31) / 32 + 1);
   cnt.take<int32_t>(L);            // chosen
   cnt.take<int64_t>(L);            // counts
+  cnt.take<double>((size_t)col_mean_slices(n) * ix->dp);  // column-mean partials
   BTRY(ensure_scratch(ix, cnt.used));
   Bump b;
   b.base = ix->scratch.base;
@@ -662,6 +678,7 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   uint32_t* bitmap = b.take<uint32_t>((n + 31) / 32 + 1);
   int32_t* chosen = b.take<int32_t>(L);
   int64_t* counts = b.take<int64_t>(L);
+  double* colpart = b.take<double>((size_t)col_mean_slices(n) * ix->dp);
 
   const float* src = X;
   if (xs == SPACE_HOST) {
@@ -706,14 +723,24 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
                          ix->XLsn, st);
     ix->xls_ok = make_parts_map(ix->tmap_xls, ix->XLs, 3 * n, ix->dpb);
   }
+  // the dataset mean: the centre of the tensor-core coarse quantiser's and
+  // exact KDE's operands
+  BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
+  launch_col_mean(ix->X, n, ix->dp, ix->mean, colpart, st);
+  {
+    uint16_t* cs = nullptr;
+    BTRY(dev_alloc(&cs, (size_t)3 * L * ix->dpb));
+    ix->Cs = cs;
+    BTRY(dev_alloc(&ix->csn, (size_t)L));
+    launch_split3(ix->C, L, ix->dp, ix->mean, ix->Cs, L, ix->dpb, ix->csn, st);
+    ix->cs_ok = make_parts_map(ix->tmap_cs, ix->Cs, 3 * L, ix->dpb);
+  }
   if (kernel != KDE_LAPLACIAN) {
     // exact KDE on tensor cores: centred rows split into three BF16 parts
-    BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
     BTRY(dev_alloc(&ix->xsn, (size_t)n));
     uint16_t* xs = nullptr;
     BTRY(dev_alloc(&xs, (size_t)3 * n * ix->dpb));
     ix->Xs = xs;
-    launch_col_mean(ix->X, n, ix->dp, ix->mean, st);
     launch_split3(ix->X, n, ix->dp, ix->mean, ix->Xs, n, ix->dpb, ix->xsn, st);
     ix->xs_ok = make_parts_map(ix->tmap_xs, ix->Xs, 3 * n, ix->dpb);
     launch_max_f32(ix->xsn, n, ix->xmax_d + 1, st);
@@ -803,6 +830,8 @@ void kde_free(kde_index* ix) {
   cudaFree(ix->XLb);
   cudaFree(ix->XLs);
   cudaFree(ix->XLsn);
+  cudaFree(ix->Cs);
+  cudaFree(ix->csn);
   cudaFree(ix->perm);
   cudaFree(ix->assign);
   cudaFree(ix->lorder);

@@ -109,6 +109,12 @@ struct kde_index {
   alignas(64) unsigned char tmap_xs[128] = {0};
   bool xs_ok = false;
   float xs_max2 = 0.f;        // max |x - mean|^2 (accuracy guard of the tensor-core path)
+  // the centroids minus the mean split into three BF16 parts [3][nlist][dpb],
+  // their squared norms and TMA descriptor (the tensor-core coarse quantiser)
+  void* Cs = nullptr;
+  float* csn = nullptr;
+  alignas(64) unsigned char tmap_cs[128] = {0};
+  bool cs_ok = false;
   // permuted sampling (Algorithm 2): pi and the dataset in pi order,
   // XP[i] = X[pi(i)]; built by kde_prepare_permuted
   int32_t* wperm = nullptr;   // [n] window position -> original id
@@ -199,7 +205,16 @@ bool launch_scan_tc(bool split, const void* tmap, const float* Yp, const float* 
                     const ScanPlan& plan, float* cand, uint32_t* err, cudaStream_t s);
 
 // ---- tc_exact.cu (tcgen05 exact KDE, three-way BF16 split) -----------------
-void launch_col_mean(const float* X, int64_t n, int dp, float* mean, cudaStream_t s);
+// column means in FP64 over fixed row slices; part holds col_mean_slices(n) x dp
+int col_mean_slices(int64_t n);
+void launch_col_mean(const float* X, int64_t n, int dp, float* mean, double* part,
+                     cudaStream_t s);
+// D[q][c] for the coarse quantiser on tensor cores (split BF16, FP32-level):
+// tmap_c over the centroids' parts [3][L][dpb] (centred on the dataset mean),
+// Ys the queries' parts [3][nq][dpb]; rows row0 + q >= *active skipped
+bool launch_coarse_tc(const void* tmap_c, const float* cn, int L, const void* Ys, const float* yn,
+                      int64_t nq, int dpb, float* D, const int64_t* active, int64_t row0,
+                      uint32_t* err, cudaStream_t s);
 void launch_split3(const float* V, int64_t rows, int dp, const float* mean, void* dst,
                    int64_t rows_pad, int dpb, float* norms, cudaStream_t s);
 bool make_parts_map(void* map_out, const void* base, int64_t rows_total, int dpb);

@@ -211,6 +211,133 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Query-centroid squared distances for the coarse quantiser on the tensor
+// cores, FP32-level: D[q][c] = |y~|^2 + |c~|^2 - 2 <y~, c~> with both sides
+// centred on the dataset mean and split into three BF16 parts (the six
+// products above, main and correction accumulators).  One CTA = one tile of
+// 128 centroids (MMA M; a thread per centroid in the epilogue, so a warp's
+// stores for one query are 32 consecutive floats) x 128 queries (MMA N).
+// Rows past rows_active (a device count; may be NULL) are not computed.
+constexpr int kCoarseThreads = 64 + 32 * 4;
+
+__global__ void __launch_bounds__(kCoarseThreads, 1)
+    k_coarse_tc(const __grid_constant__ CUtensorMap tmap_c, const __grid_constant__ CUtensorMap tmap_y,
+                const float* __restrict__ cn, int L, const float* __restrict__ yn, int64_t nq,
+                int64_t nqp, int dpb, float* __restrict__ D, const int64_t* __restrict__ active,
+                int64_t row0, uint32_t* __restrict__ err) {
+  __shared__ ExactShared sh;
+  extern __shared__ uint8_t dyn_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.x * kQM;
+  const int64_t q0 = (int64_t)blockIdx.y * kPN;
+  if (active != nullptr && row0 + q0 >= *active) return;
+  const uint32_t raw = tc::smem_u32(dyn_raw);
+  uint8_t* ring = dyn_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const int KB = dpb / kKC;
+  if (tid == 0) {
+    sh.abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&sh.full[s], 1);
+      tc::mbar_init(&sh.empty[s], 1);
+    }
+    tc::mbar_init(&sh.tfull[0], 1);
+    tc::mbar_init(&sh.drain, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(&sh.tmem_base, 2 * kPN);  // main, correction
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort = &sh.abort;
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int kb = 0; kb < KB && !*abort; ++kb, ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+        if (!tc::mbar_wait(&sh.empty[s], ph ^ 1u, abort)) break;
+        uint8_t* st = ring + s * kStageBytes;
+        tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
+        for (int p = 0; p < kParts; ++p) {
+          tc::tma_load_2d(st + p * kPartBytes, &tmap_c, kb * kKC, p * L + c0, &sh.full[s]);
+          tc::tma_load_2d(st + (kParts + p) * kPartBytes, &tmap_y, kb * kKC,
+                          (int)(p * nqp + q0), &sh.full[s]);
+        }
+      }
+      if (*abort) {
+        volatile int no_abort = 0;
+        for (int j = it > kStages ? it - kStages : 0; j < it; ++j)
+          tc::mbar_wait(&sh.full[j % kStages], (uint32_t)(j / kStages) & 1u, &no_abort);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::make_idesc(kQM, kPN, 1u);
+      const int pa[6] = {0, 0, 1, 0, 1, 2};
+      const int pb[6] = {0, 1, 0, 2, 1, 0};
+      bool ok = true;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        if (!tc::mbar_wait(&sh.full[s], ph, abort)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t st = tc::smem_u32(ring + s * kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kKC / 16; ++kk) {
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const uint64_t da = tc::desc_sw128(st + pa[j] * kPartBytes + kk * 32);
+            const uint64_t db = tc::desc_sw128(st + (kParts + pb[j]) * kPartBytes + kk * 32);
+            if (j == 0)
+              tc::mma_f16(tmem, da, db, idesc, (kb | kk) != 0 ? 1u : 0u);
+            else
+              tc::mma_f16(tmem + kPN, da, db, idesc, (kb | kk | (j - 1)) != 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&sh.empty[s]);
+      }
+      if (ok) tc::mma_commit(&sh.tfull[0]);
+      tc::mma_commit(&sh.drain);
+      volatile int no_abort = 0;
+      tc::mbar_wait(&sh.drain, 0u, &no_abort);
+    }
+  } else {
+    // one TMEM lane = one centroid per thread
+    const int lg = (warp & 3) * 32;
+    const int c = c0 + lg + lane;
+    int ok = 1;
+    if (lane == 0) ok = tc::mbar_wait(&sh.tfull[0], 0u, abort) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      tc::tc_fence_after();
+      const float cnc = c < L ? cn[c] : 0.f;
+      const uint32_t taddr = tmem + ((uint32_t)lg << 16);
+      for (int j0 = 0; j0 < kPN; j0 += 16) {
+        uint32_t v[16], w[16];
+        tc::tmem_ld16(taddr + (uint32_t)j0, v);
+        tc::tmem_ld16(taddr + (uint32_t)(kPN + j0), w);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t q = q0 + j0 + j;
+          if (c < L && q < nq) {
+            const float dot = __uint_as_float(v[j]) + __uint_as_float(w[j]);
+            D[q * L + c] = fmaxf(yn[q] + cnc - 2.f * dot, 0.f);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && sh.abort) atomicOr(err, KDE_ERRBIT_TMA);
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * kPN);
+  }
+}
+
 // Three-way BF16 split of (v - mean) for rows of a row-major FP32 matrix:
 // part p of row r goes to dst[(p * rows_pad + r) * dpb + j].  The squared
 // norm of (v - mean) is accumulated in FP64 and rounded once.
@@ -237,12 +364,34 @@ __global__ void k_split3(const float* __restrict__ V, int64_t rows, int dp, cons
   if (lane == 0) norms[r] = (float)s;
 }
 
-// Column means of X (FP64 accumulation), one thread per dimension.
-__global__ void k_col_mean(const float* __restrict__ X, int64_t n, int dp, float* __restrict__ mean) {
+// Column sums of X in FP64 over fixed row slices: block (bx, by) sums rows
+// [by * rows, (by + 1) * rows) of the 32 columns from 32 bx, a warp per 32
+// rows at a time in row order, then its 8 warps in order; part[by][j].
+__global__ void k_col_partial(const float* __restrict__ X, int64_t n, int dp, int64_t rows,
+                              double* __restrict__ part) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int64_t r0 = (int64_t)blockIdx.y * rows, r1 = min(n, r0 + rows);
+  double s = 0.0;
+  if (j < dp)
+    for (int64_t i = r0 + warp; i < r1; i += 8) s += (double)X[i * dp + j];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && j < dp) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    part[(int64_t)blockIdx.y * dp + j] = t;
+  }
+}
+
+// Column means from the slices' partial sums, added in slice order.
+__global__ void k_col_finish(const double* __restrict__ part, int slices, int64_t n, int dp,
+                             float* __restrict__ mean) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= dp) return;
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += (double)X[i * dp + j];
+  for (int b = 0; b < slices; ++b) s += part[(int64_t)b * dp + j];
   mean[j] = (float)(s / (double)n);
 }
 
@@ -267,8 +416,32 @@ bool encode_parts_map(CUtensorMap* map, const void* base, int64_t rows_total, in
 
 }  // namespace
 
-void launch_col_mean(const float* X, int64_t n, int dp, float* mean, cudaStream_t s) {
-  k_col_mean<<<(unsigned)((dp + 127) / 128), 128, 0, s>>>(X, n, dp, mean);
+size_t exact_tc_smem() { return 1024 + (size_t)kStages * kStageBytes; }
+
+int col_mean_slices(int64_t n) { return (int)std::min<int64_t>(256, (n + 4095) / 4096); }
+
+void launch_col_mean(const float* X, int64_t n, int dp, float* mean, double* part,
+                     cudaStream_t s) {
+  const int slices = col_mean_slices(n);
+  const int64_t rows = (n + slices - 1) / slices;
+  k_col_partial<<<dim3((unsigned)((dp + 31) / 32), (unsigned)slices), 256, 0, s>>>(X, n, dp, rows,
+                                                                                 part);
+  k_col_finish<<<(unsigned)((dp + 127) / 128), 128, 0, s>>>(part, slices, n, dp, mean);
+}
+
+bool launch_coarse_tc(const void* tmap_c, const float* cn, int L, const void* Ys, const float* yn,
+                      int64_t nq, int dpb, float* D, const int64_t* active, int64_t row0,
+                      uint32_t* err, cudaStream_t s) {
+  if (nq <= 0) return true;
+  CUtensorMap tmap_y;
+  if (!encode_parts_map(&tmap_y, Ys, kParts * nq, dpb)) return false;
+  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_coarse_tc), exact_tc_smem()))
+    return false;
+  const dim3 grid((unsigned)((L + kQM - 1) / kQM), (unsigned)((nq + kPN - 1) / kPN));
+  k_coarse_tc<<<grid, kCoarseThreads, exact_tc_smem(), s>>>(
+      *reinterpret_cast<const CUtensorMap*>(tmap_c), tmap_y, cn, L, yn, nq, nq, dpb, D, active,
+      row0, err);
+  return true;
 }
 
 void launch_split3(const float* V, int64_t rows, int dp, const float* mean, void* dst,
@@ -282,7 +455,6 @@ bool make_parts_map(void* map_out, const void* base, int64_t rows_total, int dpb
   return encode_parts_map(reinterpret_cast<CUtensorMap*>(map_out), base, rows_total, dpb);
 }
 
-size_t exact_tc_smem() { return 1024 + (size_t)kStages * kStageBytes; }
 
 bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_t nq, int64_t nqp,
                      const float* xn, int64_t n, int dpb, int kern, float h, double* acc,
