@@ -169,6 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t q = q0 + lg + lane;
     const bool qvalid = q < nq;
     const float ynq = qvalid ? yn[q] : 0.f;
+    const bool gauss = kern == KDE_KERN_GAUSSIAN;
+    const float lam = 1.4426950408889634f * inv;  // log2(e) / (2 h^2) (Gaussian)
+    const float lam2 = 2.f * lam, by = -lam * ynq;
     double rowsum = 0.0;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -181,18 +184,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t xrow = x_begin + (int64_t)t * kPN;
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * 2 * kPN);
       float part = 0.f;
-      for (int c0 = cbeg; c0 < cbeg + kRun; c0 += 16) {
-        uint32_t v[16];
-        uint32_t w[16];
-        tc::tmem_ld16(taddr + (uint32_t)c0, v);
-        tc::tmem_ld16(taddr + (uint32_t)(kPN + c0), w);
+      const bool full = xrow + cbeg + kRun <= x_end;  // every point of the run exists
+      if (gauss && full) {
+        // Gaussian: K = 2^(lam (2 <x~, y~> - |x~|^2 - |y~|^2)), lam = log2(e) / (2 h^2),
+        // the exponent clamped at 0 (D^2 >= 0); the run's norms in float4 loads
+        // (the same addresses on every lane)
+        const float4* xn4 = reinterpret_cast<const float4*>(xn + xrow + cbeg);
+        for (int c0 = 0; c0 < kRun; c0 += 16) {
+          uint32_t v[16];
+          uint32_t w[16];
+          tc::tmem_ld16(taddr + (uint32_t)(cbeg + c0), v);
+          tc::tmem_ld16(taddr + (uint32_t)(kPN + cbeg + c0), w);
+          float nx[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t pt = xrow + c0 + j;
-          if (pt < x_end) {
+          for (int j4 = 0; j4 < 4; ++j4) {
+            const float4 f = xn4[(c0 >> 2) + j4];
+            nx[4 * j4 + 0] = f.x;
+            nx[4 * j4 + 1] = f.y;
+            nx[4 * j4 + 2] = f.z;
+            nx[4 * j4 + 3] = f.w;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
             const float dot = __uint_as_float(v[j]) + __uint_as_float(w[j]);
-            const float d2 = xn[pt] + ynq - 2.f * dot;
-            part += kernel_from_dist(kern, d2, inv);
+            const float e = fmaf(lam2, dot, fmaf(-lam, nx[j], by));
+            part += exp2f(fminf(e, 0.f));
+          }
+        }
+      } else {
+        for (int c0 = cbeg; c0 < cbeg + kRun; c0 += 16) {
+          uint32_t v[16];
+          uint32_t w[16];
+          tc::tmem_ld16(taddr + (uint32_t)c0, v);
+          tc::tmem_ld16(taddr + (uint32_t)(kPN + c0), w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t pt = xrow + c0 + j;
+            if (pt < x_end) {
+              const float dot = __uint_as_float(v[j]) + __uint_as_float(w[j]);
+              const float d2 = xn[pt] + ynq - 2.f * dot;
+              part += kernel_from_dist(kern, d2, inv);
+            }
           }
         }
       }
