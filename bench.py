@@ -264,10 +264,13 @@ def ncu_traffic(stage, sched):
             t = json.load(f)
     except OSError:
         return None
-    e = t.get(stage)
-    if not e or e.get("src_sha") != src_digest(e["source"]) or e.get("schedule") != sched:
-        return None
-    return e.get("bytes_per_launch_full")
+    entries = t.get(stage)
+    if isinstance(entries, dict):
+        entries = [entries]
+    for e in entries or []:
+        if e.get("src_sha") == src_digest(e["source"]) and e.get("schedule") == sched:
+            return e.get("bytes_per_launch_full")
+    return None
 
 
 # --------------------------------------------------------------- workload ---

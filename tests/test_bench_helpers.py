@@ -89,6 +89,11 @@ def test_ncu_traffic_requires_same_schedule_and_source(tmp_path, monkeypatch):
     assert bench.ncu_traffic("estimate", dict(sched)) == 123
     assert bench.ncu_traffic("estimate", dict(sched, m=8000)) is None
     assert bench.ncu_traffic("estimate", dict(sched, precision="fp32")) is None
+    # several entries per stage: the one captured at the run's schedule
+    other = dict(entry, schedule=dict(sched, precision="bf16x3"), bytes_per_launch_full=456)
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"estimate": [entry, other]}))
+    assert bench.ncu_traffic("estimate", dict(sched, precision="bf16x3")) == 456
+    assert bench.ncu_traffic("estimate", dict(sched)) == 123
     assert bench.ncu_traffic("select", sched) is None
     (src / "sample.cu").write_text("kernel v2")
     assert bench.ncu_traffic("estimate", sched) is None
