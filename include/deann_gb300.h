@@ -339,10 +339,15 @@ kde_status kde_reserve(kde_index* index, int64_t nq, int32_t k, int32_t m, int32
  *   Y, out  DEVICE pointers of the index's GPU, which must be current; Y is
  *           nq x d with d a multiple of 4 and 16-byte aligned; out is nq.
  *   nq      0 <= nq <= 65536; larger batches are rejected with KDE_EINVAL.
- * Same result as kde_exact.  The first call on a device looks up the array's
- * address (make it before any stream capture).  Calls share the array and
- * clear it at their start, so calls that overlap on the GPU race: order them
- * on one stream.  Asynchronous like every device-pointer call. */
+ *   opts    only opts->stream is read (NULL: the legacy default stream).
+ * It runs the CUDA-core path of kde_exact (FP32 difference-form distances,
+ * any kernel), so it agrees with kde_exact(opts.exact_path = 1) and with the
+ * default path within the FP32 tolerance.  The first call on a device looks
+ * up the array's address (make it before any stream capture); the address is
+ * kept for the process, so the call is not valid after cudaDeviceReset.
+ * Calls share the array and clear it at their start, so calls that overlap on
+ * the GPU race: order them on one stream.  Asynchronous like every
+ * device-pointer call. */
 kde_status kde_exact_noalloc(kde_index* index, const float* Y, int64_t nq, float* out,
                              const kde_opts* opts);
 

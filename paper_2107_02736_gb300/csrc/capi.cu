@@ -434,9 +434,10 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
     a.rad = ix->rad;
     a.centered = tcore ? 1 : 0;
     a.rescore = split ? 0 : 1;
-    // 2.5 times the largest D^2 error per unit of (|x~| + |y~|)^2 measured for
-    // the split scan on GB300 (dpb / 16 units of 2^-24: one per MMA along a
-    // row), and s1 kept unrescored up to a relative error of 8e-6
+    // dpb / 16 units of 2^-24 per unit of (|x~| + |y~|)^2, one per MMA along a
+    // row: 2 to 2.5 times the largest D^2 error measured for the split scan on
+    // GB300 (1.9e-7 r^2 at d = 128, 6.1e-7 r^2 at d = 300), and s1 kept
+    // unrescored up to a relative error of 8e-6
     a.XLsn = ix->XLsn;
     a.acc_scale = (float)ix->dpb / 16.0f / 16777216.0f;
     a.acc_tol = 8e-6f;

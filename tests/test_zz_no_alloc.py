@@ -35,25 +35,32 @@ def _close(got, want, rel=1e-5, floor=1e-6):
     assert np.all(np.abs(got[~mask] - want[~mask]) <= rel * floor)
 
 
-def test_exact_noalloc_matches_exact_on_consecutive_calls():
+@pytest.mark.parametrize("kernel,h", [("gaussian", 2.5), ("laplacian", 9.0)])
+def test_exact_noalloc_matches_exact_on_consecutive_calls(kernel, h):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import oracle
     pkg, lib = _lib()
     rng = np.random.default_rng(0)
     n, d = 5000, 16
     X = rng.standard_normal((n, d)).astype(np.float32)
-    index = pkg.KDEIndex(torch.from_numpy(X).cuda(), "gaussian", 2.5)
+    index = pkg.KDEIndex(torch.from_numpy(X).cuda(), kernel, h)
     # two calls in a row with different query sets and sizes: the shared
-    # array must not carry the first call's sums into the second
+    # array must not carry the first call's sums into the second.  The
+    # reference is kde_exact's CUDA-core path (the path this call runs) and
+    # the FP64 oracle.
     for call, nq in enumerate((300, 177)):
-        Y = torch.from_numpy(rng.standard_normal((nq, d)).astype(np.float32)).cuda()
-        want = index.exact(Y).cpu().numpy()
+        Yh = rng.standard_normal((nq, d)).astype(np.float32)
+        Y = torch.from_numpy(Yh).cuda()
+        want = index.exact(Y, path="cuda").cpu().numpy()
         out = torch.full((nq,), float("nan"), device="cuda")
         st = lib.kde_exact_noalloc(index._h, ctypes.c_void_p(Y.data_ptr()), nq,
                                    ctypes.c_void_p(out.data_ptr()), None)
         assert st == 0, lib.kde_last_error()
         torch.cuda.synchronize()
-        _close(out.cpu().numpy(), want)
+        got = out.cpu().numpy()
+        _close(got, want)
+        _close(got, oracle.exact(X, Yh, kernel, h))
     index.close()
 
 
