@@ -627,7 +627,8 @@ def batched_form(torch, pkg, dev):
     exponential kernel, h bisected to a mean exact KDE of 1e-3 on 1,000
     validation queries; BF16 scan, 4,096 lists): 100,000 test queries in 64
     batches of 16 to 8,192 served by CUDA-graph replays (one graph per
-    power-of-two capacity), the backward pass on every tenth batch; error
+    power-of-two capacity) on four lanes, forward only and with the backward
+    pass on every tenth batch, each against the same work in one call; error
     against the exact KDE on 4,096 of the test queries.  Served at the
     configuration's k = 200, m = 2,000 (nprobe tuned) and at the cheapest
     (k, m, nprobe) meeting a mean relative error <= 1e-2 on the validation
@@ -654,32 +655,46 @@ def batched_form(torch, pkg, dev):
         server = pkg.BatchServer(index, k, m, nprobe=P, seed=9, precision=1, max_batch=8192,
                                  neighbors=True, streams=4)
 
-        def serve():
+        def serve(backward):
             server.next_qid, start = 0, 0
             for b, nb in enumerate(sizes):
                 nb = int(nb)
                 Yb = Yd[start:start + nb]
                 _, ids = server(Yb, out=res[start:start + nb])
-                if b % 10 == 0:
+                if backward and b % 10 == 0:
                     server.backward(Yb, ids)
                 start += nb
             server.sync()
 
-        serve()  # captures the graphs
+        def timed(backward):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            serve(backward)
+            ev1.record()
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1)
+
+        serve(True)  # captures the graphs
         torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        serve()
-        ev1.record()
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
+        ms = timed(False)
+        ms_bw = timed(True)
         err = rel_err(res.cpu().numpy()[sub], exact_s)
         ms_one = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=9, precision=1), 2,
                             torch)
+        # the one-call form of the same work: every query forward in one call,
+        # then one backward call over the batches that the server differentiates
+        bw_rows = torch.cat([torch.arange(int(o), int(o) + int(nb)) for b, (o, nb) in
+                             enumerate(zip(np.cumsum(sizes) - sizes, sizes)) if b % 10 == 0])
+        Ybw = Yd[bw_rows.to(dev)]
+        _, nbr_bw = index.query(Ybw, k, m, nprobe=P, seed=9, precision=1, return_neighbors=True)
+        ms_one_bw = ms_one + time_calls(lambda: index.grad_with_neighbors(Ybw, nbr_bw, m, seed=9),
+                                        2, torch)
         r = {"k": k, "m": m, "nprobe": P, "graphs": len(server.graphs),
-             "streams": len(server.lanes), "served_ms": ms,
-             "served_qps": nq / (ms / 1e3), "one_call_qps": nq / (ms_one / 1e3),
-             "rel_err_4096": err}
+             "streams": len(server.lanes), "served_ms": ms, "served_qps": nq / (ms / 1e3),
+             "one_call_qps": nq / (ms_one / 1e3), "served_ratio": ms_one / ms,
+             "served_with_backward_qps": nq / (ms_bw / 1e3),
+             "one_call_with_backward_qps": nq / (ms_one_bw / 1e3),
+             "backward_rows": int(bw_rows.numel()), "rel_err_4096": err}
         del server
         return r
 
@@ -711,7 +726,9 @@ def batched_form(torch, pkg, dev):
     short = {"fixed": row(k, m, P, fixed["served_qps"], fixed["rel_err_4096"]),
              "tuned": row(tuned["k"], tuned["m"], tuned["nprobe"], tuned["served_qps"],
                           tuned["rel_err_4096"]),
-             "one_call_qps": sig([fixed["one_call_qps"], tuned["one_call_qps"]])}
+             "one_call_qps": sig([fixed["one_call_qps"], tuned["one_call_qps"]]),
+             "with_backward_qps": sig([fixed["served_with_backward_qps"],
+                                       fixed["one_call_with_backward_qps"]])}
     index.close()
     return out, short
 

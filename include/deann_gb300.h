@@ -69,7 +69,12 @@ typedef enum {
  * distances; the split scan's distances are FP32-level themselves (operands
  * split into three BF16 parts, six partial products), so only the candidates
  * within its error band of the k-th distance are rescored, with compensated
- * FP32 difference-form distances, to settle the order there. */
+ * FP32 difference-form distances, to settle the order there.  With the split
+ * scan the neighbours' kernel values come from its distances; a query whose
+ * neighbour sum could be off by more than 8e-6 relative (a per-candidate
+ * error of 2^-24 (d_pad / 16) (|x - c| + |y - c|)^2 assumed) has its
+ * neighbours' rows rescored in FP32, unless the FP32 difference form's own
+ * bound on that sum is no smaller. */
 typedef enum {
   KDE_PREC_FP32 = 0,  /* FP32 operands */
   KDE_PREC_BF16 = 1,  /* BF16 operands, FP32 accumulation, FP32 rescoring */

@@ -644,88 +644,153 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
   if (tid == 1023) out[count] = part[1023];
 }
 
-// Ranks the K FP32-rescored keys in sm.key (distance key << 32 | id; ~0 for
-// an empty slot) of query q and writes its outputs: the k nearest (as a set
-// with s1 on the query path, else sorted with their distances), k' and s1.
-// Only candidates inside the FP32 error band of the k-th distance are
-// re-ranked with compensated distances.  Called by the whole block after a
-// barrier.
+// Ranks the K keys in sm.key (distance key << 32 | id; ~0 for an empty
+// slot) of query q and writes its outputs: the k nearest (as a set with s1 on
+// the query path, else sorted with their distances), k' and s1.  Only
+// candidates inside the error band of the k-th distance are re-ranked with
+// compensated distances.  Called by the whole block after a barrier.
 // band_abs widens the re-ranked band to the keys' own error bound when they
-// come unrescored from the split scan (0 for FP32-rescored keys).
+// come unrescored from the split scan (0 for FP32-rescored keys).  tk_lo >= 0
+// is a lower bound on the k-th smallest distance that the keys' own values
+// were bracketed with (then the k-th is found among the keys at or above it),
+// else -1.  kmin is the smallest key when the caller has it, else ~0.
 __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
-                          const float* __restrict__ y, float band_abs) {
+                          const float* __restrict__ y, float band_abs, float tk_lo,
+                          unsigned long long kmin) {
   __shared__ float s_red[kNW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (a.ids_only && K > a.k && a.kern != KDE_KERN_LAPLACIAN) {
+  if (a.ids_only && a.kern != KDE_KERN_LAPLACIAN) {
     // The query path needs the set and s1, not the order: find the k-th
-    // smallest rescored distance T, take every candidate clearly below it,
-    // and rank only those within the FP32 error band of T by compensated
-    // distance.
+    // smallest distance T, take every candidate clearly below it, and rank
+    // only those within the error band of T by compensated distance.  With
+    // K <= k every candidate is a neighbour.
     const int k = a.k;
-    const float T = __uint_as_float(smem_kth_dist(sm, K, k));
-    const float bw =
-        fmaxf(4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T, band_abs);
-    const uint32_t lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
-    const uint32_t hi_key = dist_key(T + bw);
     unsigned long long* amb = reinterpret_cast<unsigned long long*>(sm.slot);  // 1024 keys
+    __shared__ int s_cnt[3];  // keys below tk_lo, keys at or above it, ambiguous keys
+    __shared__ uint32_t s_T;
+    __shared__ int s_ws[kNW];
+    if (tid == 0) {
+      s_cnt[0] = 0;
+      s_cnt[1] = 0;
+      s_cnt[2] = 0;
+      s_T = kInfKey;
+    }
+    if (kmin == ~0ull) {
+      unsigned long long mn = ~0ull;
+      for (int j = tid; j < K; j += kNT) mn = min(mn, sm.key[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      __shared__ unsigned long long s_mn[kNW];
+      if (lane == 0) s_mn[warp] = mn;
+      __syncthreads();
+      kmin = s_mn[0];
+      for (int w = 1; w < kNW; ++w) kmin = min(kmin, s_mn[w]);
+    }
+    __syncthreads();
+    float T = __int_as_float(0x7f800000);
+    if (K > k) {
+      bool found = false;
+      if (tk_lo >= 0.f) {
+        // Every key below tk_lo is among the k nearest; the k-th is the
+        // (k - below)-th smallest of the rest, a short list (the bracketing
+        // bin and the band above it) ranked by comparing all its pairs.
+        const uint32_t lob = dist_key(tk_lo);
+        int below = 0;
+        for (int j = tid; j < K; j += kNT) {
+          const unsigned long long key = sm.key[j];
+          if ((uint32_t)(key >> 32) < lob) {
+            ++below;
+          } else {
+            const int r = atomicAdd(&s_cnt[1], 1);
+            if (r < 1024) amb[r] = key;
+          }
+        }
+        below = __reduce_add_sync(0xffffffffu, below);
+        if (lane == 0) atomicAdd(&s_cnt[0], below);
+        __syncthreads();
+        const int M = s_cnt[1], want = k - s_cnt[0];
+        if (M <= 1024 && want >= 1 && want <= M) {
+          for (int t = tid; t < M; t += kNT) {
+            const unsigned long long v = amb[t];
+            int r = 0;
+            for (int i = 0; i < M; ++i) r += amb[i] < v ? 1 : 0;
+            if (r == want - 1) s_T = (uint32_t)(v >> 32);
+          }
+          found = true;
+        }
+        __syncthreads();
+      }
+      T = found ? __uint_as_float(s_T) : __uint_as_float(smem_kth_dist(sm, K, k));
+    }
+    uint32_t lo_key = kInfKey, hi_key = 0u;  // K <= k: every key is a neighbour
+    if (K > k) {
+      const float bw =
+          fmaxf(4.f * (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f) * T, band_abs);
+      lo_key = T - bw > 0.f ? dist_key(T - bw) : 0u;
+      hi_key = dist_key(T + bw);
+    }
     const float inv = kernel_inv(a.kern, a.h);
     // s1 is summed in 64-bit fixed point with its unit 2^-52 of the largest
     // term (the nearest candidate's kernel value), so that the sum does not
     // depend on the order in which the keys arrived: integer addition is
     // associative.  Each term is truncated by less than 2^-51 of the largest.
-    __shared__ unsigned long long s_mn[kNW], s_fx[kNW];
-    unsigned long long mn = ~0ull;
-    for (int j = tid; j < K; j += kNT) mn = min(mn, sm.key[j]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if (lane == 0) s_mn[warp] = mn;
-    __syncthreads();
-    mn = s_mn[0];
-    for (int w = 1; w < kNW; ++w) mn = min(mn, s_mn[w]);
     int ex = 0;
-    frexpf(kernel_from_dist(a.kern, __uint_as_float((uint32_t)(mn >> 32)), inv), &ex);
+    if (kmin != ~0ull)
+      frexpf(kernel_from_dist(a.kern, __uint_as_float((uint32_t)(kmin >> 32)), inv), &ex);
     const int fx_shift = 52 - ex;  // every term is below 2^ex: its fixed value below 2^52
     unsigned long long part = 0ull;
     auto add_term = [&](uint32_t dk) {
       part += (unsigned long long)ldexpf(kernel_from_dist(a.kern, __uint_as_float(dk), inv),
                                          fx_shift);
     };
-    int c_in = 0, n_amb = 0;
-    const unsigned below = (1u << lane) - 1u;
-    for (int j0 = 0; j0 < K; j0 += kNT) {
-      const int j = j0 + tid;
-      const unsigned long long key = j < K ? sm.key[j] : ~0ull;
+    // each thread takes a contiguous run of keys: the certain neighbours are
+    // written in key order after one block scan of the runs' counts; the
+    // ambiguous ones are gathered (any order: they are ranked below) and
+    // their rows requested into L2 for the compensated distances
+    const int run = (K + kNT - 1) / kNT;
+    const int j_beg = min(K, tid * run), j_end = min(K, j_beg + run);
+    const int lines = (a.dp * 4 + 127) >> 7;
+    int mine = 0;
+    for (int j = j_beg; j < j_end; ++j) {
+      const unsigned long long key = sm.key[j];
       const uint32_t dk = (uint32_t)(key >> 32);
-      const bool cert = j < K && dk < lo_key;
-      const bool ambi = j < K && dk >= lo_key && dk <= hi_key;
-      const unsigned mc = __ballot_sync(0xffffffffu, cert), ma = __ballot_sync(0xffffffffu, ambi);
-      if (lane == 0) {
-        sm.warp_a[warp] = __popc(mc);
-        sm.warp_b[warp] = __popc(ma);
-      }
-      __syncthreads();
-      int oc = c_in, oa = n_amb, tc = 0, ta = 0;
-      for (int w = 0; w < kNW; ++w) {
-        if (w < warp) {
-          oc += sm.warp_a[w];
-          oa += sm.warp_b[w];
+      if (dk < lo_key) {
+        ++mine;
+      } else if (dk <= hi_key) {
+        const int r = atomicAdd(&s_cnt[2], 1);
+        if (r < 1024) amb[r] = key;
+        const int64_t id = (int64_t)(key & 0xffffffffu);
+        if (id < a.n) {
+          const char* row = reinterpret_cast<const char*>(a.X + id * a.dp);
+          for (int ln = 0; ln < lines; ++ln) prefetch_l2(row + ((size_t)ln << 7));
         }
-        tc += sm.warp_a[w];
-        ta += sm.warp_b[w];
       }
-      if (cert) {
-        a.nbr[q * k + oc + __popc(mc & below)] = (int32_t)(key & 0xffffffffu);
+    }
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_ws[warp] = incl;
+    __syncthreads();
+    int before = 0, c_in = 0;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) {
+      if (w < warp) before += s_ws[w];
+      c_in += s_ws[w];
+    }
+    int o = before + incl - mine;
+    for (int j = j_beg; j < j_end; ++j) {
+      const unsigned long long key = sm.key[j];
+      const uint32_t dk = (uint32_t)(key >> 32);
+      if (dk < lo_key) {
+        a.nbr[q * k + o++] = (int32_t)(key & 0xffffffffu);
         add_term(dk);
       }
-      if (ambi) {
-        const int r = oa + __popc(ma & below);
-        if (r < 1024) amb[r] = key;
-      }
-      c_in += tc;
-      n_amb += ta;
-      __syncthreads();
     }
-    const int need = k - c_in;  // 1 <= need <= n_amb
+    const int n_amb = s_cnt[2];
+    const int need = k - c_in;  // 1 <= need <= n_amb when K > k; K <= k: padding
     if (n_amb <= 1024) {
       // compensated distances for the ambiguous candidates, then their order
       const int grp = lane >> 3, lig = lane & 7;
@@ -739,24 +804,21 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
         if (valid && lig == 0) amb[j] = pack_key(d2, (int)id);
       }
       __syncthreads();
-      if (tid == 0) {
-        for (int i = 1; i < n_amb; ++i) {  // short in practice: insertion sort
-          const unsigned long long v = amb[i];
-          int j = i - 1;
-          while (j >= 0 && amb[j] > v) {
-            amb[j + 1] = amb[j];
-            --j;
-          }
-          amb[j + 1] = v;
+      // rank of each (unique) key among the ambiguous ones; the need smallest
+      // are the remaining neighbours
+      for (int t = tid; t < n_amb; t += kNT) {
+        const unsigned long long v = amb[t];
+        int r = 0;
+        for (int i = 0; i < n_amb; ++i) r += amb[i] < v ? 1 : 0;
+        if (r < need) {
+          a.nbr[q * k + c_in + r] = (int32_t)(v & 0xffffffffu);
+          add_term((uint32_t)(v >> 32));
         }
       }
-      __syncthreads();
-      for (int j = tid; j < need; j += kNT) {
-        a.nbr[q * k + c_in + j] = (int32_t)(amb[j] & 0xffffffffu);
-        add_term((uint32_t)(amb[j] >> 32));
-      }
+      for (int j = n_amb + tid; j < need; j += kNT) a.nbr[q * k + c_in + j] = -1;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      for (int sh = 16; sh > 0; sh >>= 1) part += __shfl_xor_sync(0xffffffffu, part, sh);
+      __shared__ unsigned long long s_fx[kNW];
       if (lane == 0) s_fx[warp] = part;
       __syncthreads();
       if (tid == 0) {
@@ -768,6 +830,7 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
     }
     // a very wide ambiguous band (many equal distances): fall through to the
     // full sort below, which rewrites the whole output
+    __syncthreads();
   }
   block_sort_keys(sm, K);
   const int kk = min(a.k, K);
@@ -859,13 +922,22 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
 // --------------------------------------------------------------------------
 // Neighbour selection from the scan's candidate buffer.
 // --------------------------------------------------------------------------
+constexpr size_t kSelectTablesOffset = (sizeof(SelectSmem) + 15) & ~size_t(15);
+size_t select_smem_bytes(int P) {
+  return kSelectTablesOffset + (size_t)(3 * P + 1) * sizeof(int64_t) +
+         (size_t)P * sizeof(float);
+}
+
 __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
-  extern __shared__ uint4 sel_dyn4[];  // SelectSmem, in dynamic shared memory (> 48 KB)
+  // SelectSmem, then the per-probe tables sized by P, in dynamic shared
+  // memory (> 48 KB; sized so that four blocks fit an SM)
+  extern __shared__ uint4 sel_dyn4[];
   SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
-  __shared__ int64_t s_seg[kMaxProbe + 1];
-  __shared__ int64_t s_lstart[kMaxProbe];
-  __shared__ int64_t s_llen[kMaxProbe];
-  __shared__ float s_dc[kMaxProbe];  // |y - c_l| of each probe
+  int64_t* s_seg = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(sel_dyn4) +
+                                              kSelectTablesOffset);  // [P + 1]
+  int64_t* s_lstart = s_seg + (a.P + 1);                              // [P]
+  int64_t* s_llen = s_lstart + a.P;                                   // [P]
+  float* s_dc = reinterpret_cast<float*>(s_llen + a.P);               // [P] |y - c_l|
   const int64_t q = a.order != nullptr ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (a.active != nullptr && a.q0 + q >= *a.active) {  // inactive row: empty neighbour set
@@ -928,10 +1000,10 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   // top k.  Beyond kSelectCap candidates the kSelectCap smallest are kept and
   // the query is counted as uncertified.
   int K;
+  float tk_lo = -1.f, tk_hi;  // t_k lies in [tk_lo, tk_hi]
   if (cnt_real <= (int64_t)a.k) {
     K = block_collect_le(vals, cnt, kInfKey, kSelectCap, sm);  // every finite value
   } else {
-    float tk_lo, tk_hi;  // t_k lies in [tk_lo, tk_hi]
     block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi, s_hint_lo, s_hint_hi);
     const uint32_t thr = dist_key(tk_hi + 2.f * s_E);
     K = block_collect_le(vals, cnt, thr, kSelectCap, sm);
@@ -951,61 +1023,109 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   // scan's values are FP32-level already: their keys are formed directly.
   //
   // The split scan's keys are used unrescored when the kernel values they
-  // give are accurate enough for this query: the D^2 error of a candidate is
+  // give are accurate enough for this query.  The D^2 error of a candidate is
   // taken as a.acc_scale r^2 with r = |x~| + |y~| its centred operands'
   // magnitude (the scale the split's FP32 accumulation error follows; the
-  // constant is 2.5 times the largest measured), so the relative error of the
-  // neighbour sum is at most sum K e / sum K over the collected candidates;
-  // above a.acc_tol the query's rows are rescored like the BF16 scan's.  A caller that asks for
-  // the neighbours' distances (kde_search) gets FP32 difference-form ones, so
-  // those calls rescore too.
+  // constant is 2 to 2.5 times the largest measured), which bounds the
+  // relative error of the neighbour sum by sum K e / sum K over the collected
+  // candidates.  The query's rows are rescored like the BF16 scan's when that
+  // bound is above a.acc_tol and above the bound of the FP32 difference form
+  // itself, ((d + 7) / 8 + 8) 2^-24 D^2 per candidate: where the split's bound
+  // is the smaller one (queries far from every probed list, where both are
+  // set by the FP32 rounding of D^2), rescoring would not tighten it.  A
+  // caller that asks for the neighbours' distances (kde_search) gets FP32
+  // difference-form ones, so those calls rescore too.
+  //
+  // The keys are formed four candidates a thread at a time, so that the loads
+  // of their values, ids and norms are all in flight together.
   __shared__ int s_rescore;
+  __shared__ unsigned long long s_kmin;
   bool rescore = a.rescore != 0 || a.nd2 != nullptr;
+  unsigned long long kmin = ~0ull;
   if (!rescore) {
     const float inv = kernel_inv(a.kern, a.h);
-    float ksum = 0.f, esum = 0.f;
-    for (int j = tid; j < K; j += kNT) {
-      const int s = sm.slot[j];
-      int lo = 0, hi = a.P - 1;  // last segment with start <= s
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+    const float c32 = (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
+    const bool lap = a.kern == KDE_KERN_LAPLACIAN;
+    float ksum = 0.f, esum = 0.f, e32sum = 0.f;
+    constexpr int kKU = 4;
+    for (int j0 = tid; j0 < K; j0 += kKU * kNT) {
+      int sl[kKU], pr[kKU];
+      int64_t pos[kKU];
+      bool row[kKU];
+#pragma unroll
+      for (int u = 0; u < kKU; ++u) {
+        const int j = j0 + u * kNT;
+        const int s = j < K ? sm.slot[j] : 0;
+        int lo = 0, hi = a.P - 1;  // last segment with start <= s
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_seg[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        const int64_t off = s - s_seg[lo];
+        sl[u] = s;
+        pr[u] = lo;
+        row[u] = j < K && off < s_llen[lo];
+        pos[u] = s_lstart[lo] + off;  // list-order row of the candidate
       }
-      const int64_t off = s - s_seg[lo];
-      const bool row = off < s_llen[lo];
-      const float d2 = vals[s];
-      const int64_t pos = s_lstart[lo] + off;  // list-order row of the candidate
-      sm.key[j] = row ? pack_key(d2, a.perm[pos]) : ~0ull;
-      if (row && a.kern != KDE_KERN_LAPLACIAN) {
-        const float kv = kernel_from_dist(a.kern, d2, inv);
-        const float r = sqrtf(a.XLsn[pos]) + s_dc[lo];
-        const float ed = a.acc_scale * r * r;  // the D^2 error taken
-        // d log K / d D^2: 1 / (2 h^2) (Gaussian), 1 / (2 h r) (exponential)
-        const float rel = a.kern == KDE_KERN_GAUSSIAN
-                              ? ed * inv
-                              : ed * inv / (2.f * sqrtf(fmaxf(d2, ed)));
-        ksum += kv;
-        esum += kv * fminf(rel, 1.f);
+      float d2[kKU], xs[kKU];
+      int32_t id[kKU];
+#pragma unroll
+      for (int u = 0; u < kKU; ++u) {
+        d2[u] = j0 + u * kNT < K ? vals[sl[u]] : 0.f;
+        id[u] = row[u] ? a.perm[pos[u]] : 0;
+        xs[u] = row[u] && !lap ? a.XLsn[pos[u]] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kKU; ++u) {
+        const int j = j0 + u * kNT;
+        if (j >= K) continue;
+        const unsigned long long key = row[u] ? pack_key(d2[u], id[u]) : ~0ull;
+        sm.key[j] = key;
+        kmin = min(kmin, key);
+        if (row[u] && !lap) {
+          const float kv = kernel_from_dist(a.kern, d2[u], inv);
+          const float r = sqrtf(xs[u]) + s_dc[pr[u]];
+          const float ed = a.acc_scale * r * r;  // the D^2 error taken
+          const float e32 = c32 * d2[u];         // the FP32 difference form's
+          // d log K / d D^2: 1 / (2 h^2) (Gaussian), 1 / (2 h r) (exponential)
+          const float g = a.kern == KDE_KERN_GAUSSIAN
+                              ? inv
+                              : inv / (2.f * sqrtf(fmaxf(d2[u], fmaxf(ed, e32))));
+          ksum += kv;
+          esum += kv * fminf(ed * g, 1.f);
+          e32sum += kv * fminf(e32 * g, 1.f);
+        }
       }
     }
     ksum = warp_sum(ksum);
     esum = warp_sum(esum);
-    __shared__ float s_ks[kNW], s_es[kNW];
+    e32sum = warp_sum(e32sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    __shared__ float s_ks[kNW], s_es[kNW], s_e32[kNW];
+    __shared__ unsigned long long s_km[kNW];
     if (lane == 0) {
       s_ks[warp] = ksum;
       s_es[warp] = esum;
+      s_e32[warp] = e32sum;
+      s_km[warp] = kmin;
     }
     __syncthreads();
     if (tid == 0) {
-      float kt = 0.f, et = 0.f;
+      float kt = 0.f, et = 0.f, e32t = 0.f;
+      unsigned long long km = ~0ull;
       for (int w = 0; w < kNW; ++w) {
         kt += s_ks[w];
         et += s_es[w];
+        e32t += s_e32[w];
+        km = min(km, s_km[w]);
       }
-      s_rescore = et > a.acc_tol * kt ? 1 : 0;
+      s_rescore = et > a.acc_tol * kt && et > e32t ? 1 : 0;
+      s_kmin = km;
     }
     __syncthreads();
     rescore = s_rescore != 0;
+    kmin = rescore ? ~0ull : s_kmin;
   }
   if (rescore) {
     const int dp4 = a.dp >> 2;
@@ -1085,7 +1205,8 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
     }
   }
   __syncthreads();
-  rank_keys(a, sm, K, q, y, rescore ? 0.f : 2.f * s_E);
+  // the split scan's keys are the values the bracket was taken on
+  rank_keys(a, sm, K, q, y, rescore ? 0.f : 2.f * s_E, rescore ? -1.f : tk_lo, kmin);
 }
 
 }  // namespace
@@ -1150,8 +1271,9 @@ void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_
 
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
-  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), sizeof(SelectSmem));
-  k_select_neighbors<<<(unsigned)a.nq, kNT, sizeof(SelectSmem), s>>>(a);
+  const size_t bytes = select_smem_bytes(a.P);
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), select_smem_bytes(kMaxProbe));
+  k_select_neighbors<<<(unsigned)a.nq, kNT, bytes, s>>>(a);
 }
 
 }  // namespace deann

@@ -180,7 +180,8 @@ def _representative_headline():
                   "d784": {"exact_qps": 121234.0, "fp32_fixed": r, "fp32": r, "bf16_fixed": r,
                            "bf16": r, "bf16x3_fixed": r, "bf16x3": r, "same_nbrs": True},
                   "n4M_batched": {"fixed": r, "tuned": r,
-                                  "one_call_qps": [1.45123e6, 1.41234e6]}},
+                                  "one_call_qps": [1.45123e6, 1.41234e6],
+                                  "with_backward_qps": [1.09123e6, 1.31234e6]}},
         "margin_failures": 0, "build_s": 3.2123456,
     }, 4)
 
