@@ -33,7 +33,9 @@
 //   three-way split: every operand v = v0 + v1 + v2 in BF16 (to 2^-27 |v|),
 //     the six products that carry weight down to 2^-24 (a0b0 into a main
 //     accumulator, a0b1 + a1b0 + a0b2 + a1b1 + a2b0 into a correction one, so
-//     the large sum is rounded six times less often), squared norms in FP64:
+//     the large sum is rounded six times less often), squared norms carried
+//     beyond FP32 (the points' in FP64 at build, the queries' as double-word
+//     FP32 sums) and rounded once:
 //     FP32-level distances, which the selection uses as they are.
 #include <cuda_bf16.h>
 
@@ -50,14 +52,16 @@ constexpr int kPartBytes = kBM * 128;  // one part of one 128 x 64 tile
 constexpr int kEpiWarps = 8;     // epilogue warps, a multiple of 4 (the TMEM lane quadrants)
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 4;
-// plain BF16: 4 stages of one part; split: 2 stages of three parts
+constexpr int kAhead = 2;  // tiles of the list requested into L2 ahead of their loads
+// plain BF16: 3 stages of one part (so that two CTAs fit an SM at d <= 128);
+// split: 2 stages of three parts
 template <bool Split>
 struct ScanCfg {
   static constexpr int kParts = Split ? 3 : 1;
-  static constexpr int kStages = Split ? 2 : 4;
+  static constexpr int kStages = Split ? 2 : 3;
   static constexpr int kStageBytes = kParts * kPartBytes;
 };
-constexpr size_t kDynBudget = 210 * 1024;  // dynamic shared memory of one CTA
+constexpr size_t kDynBudget = 222 * 1024;  // dynamic shared memory of one CTA (+ ~4 KB static)
 
 struct ScanShared {
   uint64_t full[kMaxStages];
@@ -69,8 +73,10 @@ struct ScanShared {
   int abort;
   int list;
   int pos;  // the list's place in the scan order
+  int issued;  // ring loads issued before the queries' staging
   int64_t dst[256];
   float yn[256];
+  int qrow[256];
 };
 
 template <bool Split>
@@ -98,14 +104,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int KB = dpb / kBK;
   const size_t b_part = (size_t)KB * BN * 128;  // one part of the resident queries
 
-  if (tid == 0) {
+  int pos0 = 0;
+  if (warp == 0) {
+    // the list of tile t: the last scan position whose first tile is <= t,
+    // found by warp 0 in 32-way steps (tile_off is nondecreasing and
+    // tile_off[0] = 0 <= t)
     int lo = 0, hi = L - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    while (hi - lo >= 32) {
+      const int step = (hi - lo + 32) / 32;
+      const int probe = lo + lane * step;
+      const unsigned m = __ballot_sync(0xffffffffu, probe <= hi && tile_off[probe] <= t);
+      lo += (31 - __clz(m)) * step;
+      hi = min(hi, lo + step - 1);
     }
-    sh.pos = lo;
-    sh.list = lorder[lo];
+    const int probe = lo + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, probe <= hi && tile_off[probe] <= t);
+    pos0 = lo + 31 - __clz(m);
+  }
+  if (tid == 0) {
+    sh.pos = pos0;
+    sh.list = lorder[pos0];
     sh.abort = 0;
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&sh.full[s], 1);
@@ -117,6 +135,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc::mbar_init(&sh.drain, 1);
     tc::fence_mbar_init();
+    // the ring is empty: its first loads go out now, ahead of the queries'
+    // staging (the producer below continues from sh.issued)
+    const int l0 = sh.list;
+    const int64_t xb0 = list_off[l0];
+    const int nt0 = (int)((list_off[l0 + 1] - xb0 + kBM - 1) / kBM);
+    const int total = nt0 * (dpb / kBK);
+    int it = 0;
+    for (; it < kStages && it < total; ++it) {
+      const int tt = it / (dpb / kBK), kb = it - tt * (dpb / kBK);
+      tc::mbar_arrive_expect_tx(&sh.full[it], kStageBytes);
+      const int row = (int)(xb0 + (int64_t)tt * kBM);
+#pragma unroll
+      for (int p = 0; p < kParts; ++p)
+        tc::tma_load_2d(A + it * kStageBytes + p * kPartBytes, &tmap, kb * kBK,
+                        (int)((int64_t)p * n + row), &sh.full[it]);
+    }
+    sh.issued = it;
+    // and the next kAhead tiles are requested into L2, so that their loads,
+    // when the ring frees, wait on L2 rather than HBM
+    for (int tt = 1; tt <= kAhead && tt < nt0; ++tt)
+      for (int kb = 0; kb < dpb / kBK; ++kb)
+#pragma unroll
+        for (int p = 0; p < kParts; ++p)
+          tc::tma_prefetch_2d(&tmap, kb * kBK, (int)((int64_t)p * n + xb0 + (int64_t)tt * kBM));
   }
   __syncthreads();
   const int l = sh.list;
@@ -130,63 +172,107 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t len = list_off[l + 1] - xb;
   const int ntiles = (int)((len + kBM - 1) / kBM);
 
+  // this CTA's queries (ids and candidate destinations), all loads at once
+  for (int r = tid; r < nN; r += kThreads) {
+    sh.qrow[r] = r < npairs ? pair_q[pb + r] : -1;
+    sh.dst[r] = r < npairs ? pair_dst[pb + r] : -1;
+  }
+  __syncthreads();
   // stage the queries centred on this list's centroid, y~ = y - c_l, in BF16
   // (split: three parts): row r of block kb of part p at
   // B + p*b_part + kb*BN*128 + r*128, 16-byte chunk c stored at chunk
-  // position c ^ (r & 7) (the 128-byte swizzle)
-  const float* cl = C + (int64_t)l * dp;
-  const int chunks = nN * KB * 8;
-  for (int i = tid; i < chunks; i += kThreads) {
-    const int r = i / (KB * 8);
-    const int rem = i - r * (KB * 8);
-    const int kb = rem >> 3, c = rem & 7;
-    uint32_t w[kParts][4];
+  // position c ^ (r & 7) (the 128-byte swizzle), and |y~|^2 (for the split
+  // scan as a double-word FP32 sum, rounded once).  G lanes take the C8 chunks of 8 dimensions of
+  // one row (G the smallest power of two >= C8, at most 32), so a warp stages
+  // 32 / G rows at once, two such groups of rows with their loads issued
+  // together; a row's chunk sums are added over its lanes in a fixed order.
+  {
+    const float* cl = C + (int64_t)l * dp;
+    const int C8 = KB * 8;
+    int G = 32;
+    while (G / 2 >= C8) G >>= 1;
+    const int R = 32 / G, gl = lane & (G - 1), gr = lane / G;
+    constexpr int kU = 2;
+    const int rstep = (kThreads / 32) * R;
+    for (int r0 = warp * R; r0 < nN; r0 += kU * rstep) {
+      float sh_[kU], sl_[kU];  // |y~|^2 as an unevaluated sum hi + lo (split) or plain (sh_)
 #pragma unroll
-    for (int p = 0; p < kParts; ++p) w[p][0] = w[p][1] = w[p][2] = w[p][3] = 0u;
-    if (r < npairs) {
-      const float* yq = Yp + (int64_t)pair_q[pb + r] * dp;
-      const int j0 = kb * kBK + c * 8;
+      for (int u = 0; u < kU; ++u) {
+        sh_[u] = 0.f;
+        sl_[u] = 0.f;
+      }
+      for (int c8 = gl; c8 < C8; c8 += G) {
+        const int kb = c8 >> 3, c = c8 & 7, j0 = c8 * 8;
+        float4 y[kU][2];
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c0 = j0 < dp ? *reinterpret_cast<const float4*>(cl + j0) : z;
+        const float4 c1 = j0 + 4 < dp ? *reinterpret_cast<const float4*>(cl + j0 + 4) : z;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + 2 * u;
-        const float f0 = j < dp ? yq[j] - cl[j] : 0.f;
-        const float f1 = j + 1 < dp ? yq[j + 1] - cl[j + 1] : 0.f;
-        const __nv_bfloat162 h0 = __floats2bfloat162_rn(f0, f1);
-        w[0][u] = *reinterpret_cast<const uint32_t*>(&h0);
-        if (Split) {
-          const float2 g0 = __bfloat1622float2(h0);
-          const float r0 = f0 - g0.x, r1 = f1 - g0.y;  // exact
-          const __nv_bfloat162 h1 = __floats2bfloat162_rn(r0, r1);
-          const float2 g1 = __bfloat1622float2(h1);
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0 - g1.x, r1 - g1.y);
-          w[kParts > 1 ? 1 : 0][u] = *reinterpret_cast<const uint32_t*>(&h1);
-          w[kParts > 2 ? 2 : 0][u] = *reinterpret_cast<const uint32_t*>(&h2);
+        for (int u = 0; u < kU; ++u) {
+          const int r = r0 + u * rstep + gr;
+          const int qr = r < nN ? sh.qrow[r] : -1;
+          const float* yq = Yp + (int64_t)(qr >= 0 ? qr : 0) * dp;
+          y[u][0] = qr >= 0 && j0 < dp ? *reinterpret_cast<const float4*>(yq + j0) : c0;
+          y[u][1] = qr >= 0 && j0 + 4 < dp ? *reinterpret_cast<const float4*>(yq + j0 + 4) : c1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int r = r0 + u * rstep + gr;
+          if (r >= nN) continue;
+          const float f[8] = {y[u][0].x - c0.x, y[u][0].y - c0.y, y[u][0].z - c0.z,
+                              y[u][0].w - c0.w, y[u][1].x - c1.x, y[u][1].y - c1.y,
+                              y[u][1].z - c1.z, y[u][1].w - c1.w};
+          uint32_t w[kParts][4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const float f0 = f[2 * t], f1 = f[2 * t + 1];
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(f0, f1);
+            w[0][t] = *reinterpret_cast<const uint32_t*>(&h0);
+            if (Split) {
+              const float2 g0 = __bfloat1622float2(h0);
+              const float e0 = f0 - g0.x, e1 = f1 - g0.y;  // exact
+              const __nv_bfloat162 h1 = __floats2bfloat162_rn(e0, e1);
+              const float2 g1 = __bfloat1622float2(h1);
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(e0 - g1.x, e1 - g1.y);
+              w[kParts > 1 ? 1 : 0][t] = *reinterpret_cast<const uint32_t*>(&h1);
+              w[kParts > 2 ? 2 : 0][t] = *reinterpret_cast<const uint32_t*>(&h2);
+              // squares exact as p + e (FMA), added with TwoSum: the
+              // double-word sum carries far more than the FP32 result keeps
+              const float p0 = f0 * f0, q0 = fmaf(f0, f0, -p0);
+              const float p1 = f1 * f1, q1 = fmaf(f1, f1, -p1);
+              float t0, d0, t1, d1;
+              two_sum(sh_[u], p0, t0, d0);
+              two_sum(t0, p1, t1, d1);
+              sh_[u] = t1;
+              sl_[u] += (d0 + d1) + (q0 + q1);
+            } else {
+              sh_[u] = fmaf(f0, f0, fmaf(f1, f1, sh_[u]));
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < kParts; ++p)
+            *reinterpret_cast<uint4*>(B + p * b_part + (size_t)kb * BN * 128 + r * 128 +
+                                      ((c ^ (r & 7)) << 4)) =
+                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
         }
       }
-    }
 #pragma unroll
-    for (int p = 0; p < kParts; ++p)
-      *reinterpret_cast<uint4*>(B + p * b_part + (size_t)kb * BN * 128 + r * 128 +
-                                ((c ^ (r & 7)) << 4)) = make_uint4(w[p][0], w[p][1], w[p][2],
-                                                                   w[p][3]);
-  }
-  // |y~|^2 (FP64 for the split scan, rounded once) and the candidate
-  // destinations, one warp per query row
-  for (int r = warp; r < nN; r += kThreads / 32) {
-    double s = 0.0;
-    if (r < npairs) {
-      const float* yq = Yp + (int64_t)pair_q[pb + r] * dp;
-      float sf = 0.f;
-      for (int j = lane; j < dp; j += 32) {
-        const float v = yq[j] - cl[j];
-        if (Split) s += (double)v * (double)v;
-        else sf = fmaf(v, v, sf);
+      for (int u = 0; u < kU; ++u) {
+        for (int o = G / 2; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, sh_[u], o);
+          const float ol = __shfl_xor_sync(0xffffffffu, sl_[u], o);
+          if (Split) {
+            float t, d;
+            two_sum(sh_[u], oh, t, d);
+            sh_[u] = t;
+            sl_[u] += ol + d;
+          } else {
+            sh_[u] += oh;
+          }
+        }
+        const int r = r0 + u * rstep + gr;
+        if (gl == 0 && r < nN) sh.yn[r] = sh.qrow[r] >= 0 ? sh_[u] + sl_[u] : 0.f;
       }
-      s = Split ? warp_sum_d(s) : (double)warp_sum(sf);
-    }
-    if (lane == 0) {
-      sh.dst[r] = r < npairs ? pair_dst[pb + r] : -1;
-      sh.yn[r] = (float)s;
     }
   }
   tc::fence_proxy_async_smem();
@@ -205,8 +291,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       int it = 0;  // loads issued so far
+      const int pre = sh.issued;
       for (int tt = 0; tt < ntiles && !*abort; ++tt) {
+        if (tt >= 1 && tt + kAhead < ntiles) {
+          const int prow = (int)(xb + (int64_t)(tt + kAhead) * kBM);
+          for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+            for (int p = 0; p < kParts; ++p)
+              tc::tma_prefetch_2d(&tmap, kb * kBK, (int)((int64_t)p * n + prow));
+        }
         for (int kb = 0; kb < KB; ++kb) {
+          if (it < pre) {  // issued before the staging
+            ++it;
+            continue;
+          }
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
           if (!tc::mbar_wait(&sh.empty[s], ph ^ 1u, abort)) break;
@@ -223,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let the last (at most kStages) loads land before the CTA's shared
         // memory goes away; every earlier load was consumed by the MMA warp
         volatile int no_abort = 0;
+        if (it < pre) it = pre;
         for (int j = it > kStages ? it - kStages : 0; j < it; ++j)
           tc::mbar_wait(&sh.full[j % kStages], (uint32_t)(j / kStages) & 1u, &no_abort);
       }
@@ -282,29 +381,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue: warps 2..9 ----------------
-    // one TMEM lane (= one list point) per thread; for each query the warp's
-    // 32 points go out as one coalesced 128-byte store.  Points past the list
-    // up to its 32-float padded length get +inf (the segment's padding).
-    // A warp reads only its own lane quadrant (warp id mod 4); the second
-    // warp of a quadrant starts at column 16.
+    // one TMEM lane (= one list point) per thread.  A warp reads only its own
+    // lane quadrant (warp id mod 4); the second warp of a quadrant starts at
+    // column 16.  Each group of 16 query columns goes through a 16 x 32
+    // transpose tile in shared memory, so that every lane stores 4
+    // consecutive points of one query with one 16-byte store: a warp's store
+    // instruction covers 128 bytes of four queries' candidate segments.
+    // Points past the list up to its 32-float padded length get +inf (the
+    // segment's padding).
     const int lg = (warp & 3) * 32;
     const int cstart = ((warp - 2) >> 2) * 16;
     constexpr int cstep = 16 * (kEpiWarps / 4);
     const int row = lg + lane;
     const int64_t padlen = (len + 31) & ~(int64_t)31;
+    float* tp = reinterpret_cast<float*>(B + kParts * b_part) + (warp - 2) * (16 * 32);
+    const int tj = lane >> 3, ti = lane & 7;  // the lane's column (+ 4 g) and row quad
+    // the point norms of the next tile are loaded while this one's
+    // accumulator is awaited and stored
+    float xn_next = row < len ? XLcn[xb + row] : 0.f;
     for (int tt = 0; tt < ntiles; ++tt) {
       const int b = tt & 1;
       const uint32_t tph = (uint32_t)(tt >> 1) & 1u;
+      const int64_t pt = (int64_t)tt * kBM + row;
+      const bool valid = pt < len;
+      // the warp's 32 points lie in the segment's padded length, or all past it
+      const bool live = (int64_t)tt * kBM + lg < padlen;
+      const float xn = xn_next;
+      xn_next = pt + kBM < len ? XLcn[xb + pt + kBM] : 0.f;
       int ok = 1;
       if (lane == 0) ok = tc::mbar_wait(&sh.tfull[b], tph, abort) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc::tc_fence_after();
-      const int64_t pt = (int64_t)tt * kBM + row;
-      const bool valid = pt < len, pad = !valid && pt < padlen;
-      const float xn = valid ? XLcn[xb + pt] : 0.f;
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)b * acc_cols;
-      for (int c0 = cstart; c0 < npairs; c0 += cstep) {
+      float* dst_tile = cand + (int64_t)tt * kBM + lg + 4 * ti;
+      for (int c0 = cstart; c0 < npairs && live; c0 += cstep) {
         uint32_t v[16];
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
         if (Split) {
@@ -315,13 +426,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          if ((valid || pad) && col < npairs)
-            cand[sh.dst[col] + pt] =
-                valid ? fmaxf(xn + sh.yn[col] - 2.f * __uint_as_float(v[j]), 0.f)
-                      : __int_as_float(0x7f800000);
+        for (int j = 0; j < 16; ++j)
+          tp[j * 32 + lane] = valid ? fmaxf(xn + sh.yn[c0 + j] - 2.f * __uint_as_float(v[j]), 0.f)
+                                    : __int_as_float(0x7f800000);
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int j = tj + 4 * g, col = c0 + j;
+          const float4 q4 = *reinterpret_cast<const float4*>(tp + j * 32 + 4 * ti);
+          if (col < npairs) *reinterpret_cast<float4*>(dst_tile + sh.dst[col]) = q4;
         }
+        __syncwarp();
       }
       // the accumulator was read synchronously (tcgen05.wait::ld): a relaxed
       // arrive frees it without waiting for this tile's stores to land
@@ -341,10 +456,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 size_t scan_tc_smem(int dpb, int BN, bool split) {
-  // alignment slack, the A ring, the resident queries
+  // alignment slack, the A ring, the resident queries, the epilogue warps'
+  // transpose tiles
   const size_t ring = split ? (size_t)ScanCfg<true>::kStages * ScanCfg<true>::kStageBytes
                             : (size_t)ScanCfg<false>::kStages * ScanCfg<false>::kStageBytes;
-  return 1024 + ring + (size_t)(split ? 3 : 1) * (dpb / kBK) * BN * 128;
+  return 1024 + ring + (size_t)(split ? 3 : 1) * (dpb / kBK) * BN * 128 +
+         (size_t)kEpiWarps * 16 * 32 * sizeof(float);
 }
 
 int scan_tc_bn(int dpb, bool split) {
