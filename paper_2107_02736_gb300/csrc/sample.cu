@@ -64,6 +64,35 @@ __device__ __forceinline__ bool is_member_f(const EstSmem& sm, int kk, int64_t i
   return is_member(sm.nb, kk, id);
 }
 
+// Hash set of the neighbour ids (open addressing, linear probing, at most
+// kMaxK ids in twice as many slots), for the query path, where the estimator
+// needs X_1 only for membership and k': it replaces the sort.  Slots hold an
+// id or -1.
+constexpr int kHashBits = 12;
+constexpr int kHashSlots = 1 << kHashBits;
+static_assert(kHashSlots >= 2 * kMaxK, "the hash set keeps its load at most 1/2");
+__device__ __forceinline__ uint32_t hash_slot(int id) {
+  return ((uint32_t)id * 2654435761u) >> (32 - kHashBits);  // Knuth's multiplicative hash
+}
+
+__device__ __forceinline__ bool hash_has(const int* hs, int id) {
+  uint32_t h = hash_slot(id);
+  for (int p = 0; p < kHashSlots; ++p) {  // ends at the id or at the first empty slot
+    const int v = hs[h];
+    if (v == id) return true;
+    if (v < 0) return false;
+    h = (h + 1) & (kHashSlots - 1);
+  }
+  return false;
+}
+
+// Membership with the filter first (one shared load rules most ids out).
+__device__ __forceinline__ bool is_member_h(const EstSmem& sm, const int* hs, int64_t id) {
+  const uint32_t w = sm.filt[(id >> 5) & (kFiltWords - 1)];
+  if (((w >> (id & 31)) & 1u) == 0u) return false;
+  return hash_has(hs, (int)id);
+}
+
 // Ascending bitonic sort of v[0..P2) (P2 a power of two) by the whole CTA;
 // ends with a barrier.
 __device__ void block_bitonic_sort(int* v, int P2) {
@@ -133,6 +162,43 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
   __syncthreads();
 }
 
+// Inserts the neighbour row into the hash set hs and the filter: sm.kk
+// receives the number of distinct valid ids, sm.status = 1 when an id is >= n.
+__device__ void load_neighbours_hash(const int32_t* __restrict__ row, int k, int64_t n,
+                                     EstSmem& sm, int* hs) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < kHashSlots; i += kNT) hs[i] = -1;
+  for (int i = tid; i < kFiltWords; i += kNT) sm.filt[i] = 0u;
+  if (tid == 0) {
+    sm.status = 0;
+    sm.kk = 0;
+  }
+  __syncthreads();
+  int mine = 0;
+  for (int i = tid; i < k; i += kNT) {
+    const int32_t id = row[i];
+    if (id < 0) continue;
+    if ((int64_t)id >= n) {
+      sm.status = 1;
+      continue;
+    }
+    uint32_t h = hash_slot(id);
+    for (int p = 0; p < kHashSlots; ++p) {
+      const int prev = atomicCAS(&hs[h], -1, id);
+      if (prev == -1) {
+        ++mine;
+        atomicOr(&sm.filt[(id >> 5) & (kFiltWords - 1)], 1u << (id & 31));
+        break;
+      }
+      if (prev == id) break;  // a duplicate
+      h = (h + 1) & (kHashSlots - 1);
+    }
+  }
+  mine = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) atomicAdd(&sm.kk, mine);
+  __syncthreads();
+}
+
 // Fills sm.S[0..sm.cnt) with the next accepted sample indices (at most
 // `room`), starting at draw t0; sets sm.tnext to the first unused draw.
 // mode 0 rejects members of X_1; mode 1 accepts every draw.  Returns false
@@ -140,8 +206,10 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
 // draws, thread i taking kDraws of them in a row, so the accepted draws are
 // ranked in draw order by a block prefix sum of the per-thread counts.
 constexpr int kDraws = 4;
+// Membership is tested on the hash set hs when given, else on sm.nb.
 __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, int64_t cap,
-                           int room, int mode, const EstSmem& smc, EstSmem& sm) {
+                           int room, int mode, const EstSmem& smc, EstSmem& sm,
+                           const int* hs = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int filled = 0;
   int64_t t = t0;
@@ -159,7 +227,9 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
       ids[r] = 0;
       if (tb + r < cap) {
         ids[r] = (int)draw_index(seed, qid, (uint32_t)(tb + r), 0u, n);
-        if (mode == 1 || !is_member_f(smc, smc.kk, ids[r])) accm |= 1u << r;
+        if (mode == 1 ||
+            !(hs != nullptr ? is_member_h(smc, hs, ids[r]) : is_member_f(smc, smc.kk, ids[r])))
+          accm |= 1u << r;
       }
     }
     const int mine = __popc(accm);
@@ -377,7 +447,9 @@ __device__ __forceinline__ int64_t window_order(int64_t b, int64_t nq, int64_t P
 template <int G>
 __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   __shared__ EstSmem sm;
-  __shared__ int tmp[kMaxK];
+  // the sort's scratch, or the hash set of X_1 on the query path (s1 given,
+  // rejection sampling): there only membership and k' are needed
+  __shared__ int tmp[kHashSlots];
   extern __shared__ float4 ys4[];
   float* ys = reinterpret_cast<float*>(ys4);
   const int64_t q = a.mode == 2 ? window_order(blockIdx.x, a.nq, a.win_period) : blockIdx.x;
@@ -386,7 +458,10 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
   const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;
-  if (k > 0) {
+  const bool hashed = k > 0 && a.s1_in != nullptr && a.mode == 0;
+  if (hashed) {
+    load_neighbours_hash(a.nbr + q * a.k, k, a.n, sm, tmp);
+  } else if (k > 0) {
     load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
   } else {
     if (tid == 0) {
@@ -433,7 +508,8 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
     float part = 0.f;
     while (got < a.m) {
       const int room = min(kChunk, a.m - got);
-      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm)) {
+      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm,
+                      hashed ? tmp : nullptr)) {
         ok = false;
         break;
       }
@@ -911,15 +987,22 @@ int group_lanes(int dp) {
 
 }  // namespace
 
+template <int G>
+void launch_estimate_inst(const SampleArgs& a, size_t dyn, cudaStream_t s) {
+  // the query row in dynamic shared memory: past 48 KB with the static part
+  // (37 KB) for rows wider than 2,048 floats, which needs the opt-in
+  if (dyn > 8192) set_dynamic_smem(reinterpret_cast<const void*>(&k_estimate<G>), dyn);
+  k_estimate<G><<<(unsigned)a.nq, kNT, dyn, s>>>(a);
+}
+
 void launch_estimate(const SampleArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
   const size_t dyn = sizeof(float) * a.dp;
-  const unsigned grid = (unsigned)a.nq;
   switch (group_lanes(a.dp)) {
-    case 4: k_estimate<4><<<grid, kNT, dyn, s>>>(a); break;
-    case 8: k_estimate<8><<<grid, kNT, dyn, s>>>(a); break;
-    case 16: k_estimate<16><<<grid, kNT, dyn, s>>>(a); break;
-    default: k_estimate<32><<<grid, kNT, dyn, s>>>(a); break;
+    case 4: launch_estimate_inst<4>(a, dyn, s); break;
+    case 8: launch_estimate_inst<8>(a, dyn, s); break;
+    case 16: launch_estimate_inst<16>(a, dyn, s); break;
+    default: launch_estimate_inst<32>(a, dyn, s); break;
   }
 }
 
