@@ -47,8 +47,8 @@ import workloads  # noqa: E402
 # the cheapest that `bench.py --tune` finds with a mean relative error <= 0.9e-2
 # on the 4,000 validation queries.  Both arms run it unless --schedule or --tune
 # says otherwise.
-DEFAULT_SCHEDULE = {"bf16": (1536, 4000, 8), "fp32": (1536, 4000, 8),
-                    "bf16x3": (1536, 4000, 8)}
+DEFAULT_SCHEDULE = {"bf16": (1280, 4000, 4), "fp32": (1280, 4000, 4),
+                    "bf16x3": (1280, 4000, 4)}
 TARGET_ERR = 1e-2
 # the tuners aim 10 % below the target on the validation queries, so that
 # every timed step (each with its own seed) stays within it on the test queries
@@ -83,7 +83,7 @@ def parse():
     p.add_argument("--profile-case", type=int, default=0, metavar="NQ",
                    help="run one call of each query-path kernel on NQ queries of the workload "
                         "(for a profiler) and exit")
-    p.add_argument("--profile-schedule", default="1536,4000,8", metavar="K,M,NPROBE",
+    p.add_argument("--profile-schedule", default="1280,4000,4", metavar="K,M,NPROBE",
                    help="the DEANN schedule --profile-case runs (BF16 scan); the default is "
                         "the one the tuner picks on this workload")
     return p.parse_args()
@@ -314,8 +314,8 @@ def time_calls(fn, reps, torch):
 M_GRID = [int(round(1000 * 2 ** (i / 4))) for i in range(25)]
 
 
-def tune(index, Yv_d, exact_v, torch, precision, ks=(800, 1024, 1536, 2048), Ps=(8, 16),
-         m_grid=None):
+def tune(index, Yv_d, exact_v, torch, precision, ks=(800, 1024, 1280, 1536, 1792, 2048),
+         Ps=(4, 6, 8, 16), m_grid=None):
     """Cheapest (k, m, nprobe) whose validation mean rel. err is <= 0.9e-2.  For
     every (k, nprobe), m grows in quarter-octave steps until the target is met
     (more samples only cost more); the time is that of a call on the
@@ -474,7 +474,7 @@ def schedules_and_recall(index, X, Yd, Yv_d, exact_v, head_sched, prec, h, torch
         ms = time_calls(run, 3, torch)
         fixed[name] = {"qps": nq / (ms / 1e3), "test_rel_err": rel_err(run().cpu().numpy(), et)}
     fixed["recall"] = recall_at_k(ex, brute, Yv_d[:1000], 100, 1, prec)
-    tuned_x, _ = tune(ex, Yv_d, ev, torch, prec)
+    tuned_x, _ = tune(ex, Yv_d, ev, torch, prec, ks=(512, 800, 1024, 1280, 1536), Ps=(4, 8))
     run = lambda: ex.query(Yd, tuned_x["k"], tuned_x["m"], nprobe=tuned_x["nprobe"],
                            precision=prec)
     ms = time_calls(run, 3, torch)
@@ -609,7 +609,8 @@ def exponential_form(X, Yd, Yv_d, torch, pkg, dev, nlist):
     exact_t = index.exact(Yd).cpu().numpy()
     nq = Yd.shape[0]
     ms_exact = time_calls(lambda: index.exact(Yd), 2, torch)
-    best, grid = tune(index, Yv_d, exact_v, torch, 1)
+    best, grid = tune(index, Yv_d, exact_v, torch, 1, ks=(512, 800, 1024, 1280, 1536),
+                      Ps=(4, 8))
     k, m, P = best["k"], best["m"], best["nprobe"]
     ms = time_calls(lambda: index.query(Yd, k, m, nprobe=P, seed=5, precision=1), 3, torch)
     err = rel_err(index.query(Yd, k, m, nprobe=P, seed=6, precision=1).cpu().numpy(), exact_t)

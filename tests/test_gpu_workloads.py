@@ -2,8 +2,9 @@
 
 The low-dimensional workload runs at full size on every query.  The
 1M-point d=128 workload runs at full size in the launch configuration the
-benchmark times (BF16 tcgen05 scan, k = 1536, m = 4000, nprobe = 8, 10k
-queries; DEANNP with m = 8000) and sampled queries are checked one by one.
+benchmark times (k = 1280, m = 4000, nprobe = 4, 10k queries, every scan
+precision; DEANNP with m = 8000), and at the earlier k = 1536, nprobe = 8,
+and sampled queries are checked one by one.
 The others run here at reduced n with their own dimension, kernel and
 parameters (their full sizes are in test_gpu_full_size.py).
 """
@@ -56,10 +57,11 @@ def embed(pkg):
     return X, Y, index, C.numpy(), assign.numpy()
 
 
+@pytest.mark.parametrize("sched", [(1280, 4000, 4), (1536, 4000, 8)])
 @pytest.mark.parametrize("precision", [1, 0, 2])
-def test_embed_full_size_sampled(embed, precision):
+def test_embed_full_size_sampled(embed, precision, sched):
     X, Y, index, C, assign = embed
-    k, m, P, h = 1536, 4000, 8, 12.85
+    (k, m, P), h = sched, 12.85
     out, nbr = index.query(_dev(Y), k, m, nprobe=P, seed=3, precision=precision,
                            return_neighbors=True)
     out, nbr = out.cpu().numpy(), nbr.cpu().numpy()
@@ -78,7 +80,7 @@ def test_embed_full_size_deannp_sampled(embed):
     """DEANNP (Algorithm 2) at full size: the 1M-entry permutation is
     bit-exact and sampled estimates match the oracle's windows."""
     X, Y, index, _, _ = embed
-    k, m, P, h = 1536, 8000, 8, 12.85
+    k, m, P, h = 1280, 8000, 4, 12.85
     perm = index.prepare_permuted(return_perm=True).cpu().numpy()
     want_perm = oracle.feistel_perm(1, X.shape[0])
     assert np.array_equal(perm, want_perm)
