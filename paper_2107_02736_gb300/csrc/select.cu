@@ -504,7 +504,8 @@ __global__ void __launch_bounds__(kNT) k_select_probes_warp(
     }
   };
   if (K > 0) fill(0ull);
-  u64 mine = kNone;
+  // the K smallest approximate distances: lane r keeps the r-th one's list
+  int cand = 0;
   for (int r = 0; r < K; ++r) {
     u64 best = b0;
 #pragma unroll
@@ -519,9 +520,17 @@ __global__ void __launch_bounds__(kNT) k_select_probes_warp(
       b3 = kNone;
       if (b0 == kNone) fill(best);
     }
-    const int c = (int)((best - 1ull) & 0xffffffffull);
-    const float d2 = precise_sq_dist<32>(C + (int64_t)c * dp, y, d, lane);
-    if (lane == r) mine = pack_key(d2, c);
+    if (lane == r) cand = (int)((best - 1ull) & 0xffffffffull);
+  }
+  // their compensated distances, 8 lanes a list and four lists at once (the
+  // rows' loads in flight together); lane r receives its own list's
+  u64 mine = kNone;
+  const int grp = lane >> 3, lig = lane & 7;
+  for (int r0 = 0; r0 < K; r0 += 4) {
+    const int c = __shfl_sync(0xffffffffu, cand, min(r0 + grp, 31));
+    const float d2 = precise_sq_dist<8>(C + (int64_t)c * dp, y, d, lig);
+    const float d2r = __shfl_sync(0xffffffffu, d2, ((lane - r0) & 3) * 8);
+    if (lane >= r0 && lane < r0 + 4 && lane < K) mine = pack_key(d2r, cand);
   }
   // rank of lane j's key among the K keys (all distinct: they carry the id)
   int rank = 0;
