@@ -44,6 +44,7 @@ struct EstSmem {
   int cnt;
   int64_t tnext;
   int status;
+  int dup;                     // the hash set met a repeated id
 };
 
 __device__ __forceinline__ bool is_member(const int* nb, int kk, int64_t id) {
@@ -172,6 +173,7 @@ __device__ void load_neighbours_hash(const int32_t* __restrict__ row, int k, int
   if (tid == 0) {
     sm.status = 0;
     sm.kk = 0;
+    sm.dup = 0;
   }
   __syncthreads();
   int mine = 0;
@@ -190,7 +192,10 @@ __device__ void load_neighbours_hash(const int32_t* __restrict__ row, int k, int
         atomicOr(&sm.filt[(id >> 5) & (kFiltWords - 1)], 1u << (id & 31));
         break;
       }
-      if (prev == id) break;  // a duplicate
+      if (prev == id) {  // a duplicate
+        sm.dup = 1;
+        break;
+      }
       h = (h + 1) & (kHashSlots - 1);
     }
   }
@@ -849,12 +854,44 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
   extern __shared__ float4 dyn4[];
   float* ys = reinterpret_cast<float*>(dyn4);
   float* gpart = ys + a.dp;  // [kNT / G][dp]: each lane group's partial gradient
+  int* hs = reinterpret_cast<int*>(gpart + (size_t)(kNT / G) * a.dp);  // [kHashSlots]
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x;
   const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
   for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
   const int k = a.rs ? 0 : a.k;
-  if (k > 0) {
+  // Rejection mode outside held-out fitting: X_1 in a hash set for the draws'
+  // membership tests, and its rows taken in the row's own order (no sort) when
+  // no id repeats; with a repeated id the sorted, deduplicated array is built
+  // instead (the order of the X_1 rows fixes the gradient's summation order).
+  bool use_hash = false;
+  int k1h = 0;
+  if (k > 0 && a.mode == 0 && !a.loo) {
+    const int32_t* row = a.nbr + q * a.k;
+    load_neighbours_hash(row, k, a.n, sm, hs);
+    use_hash = sm.dup == 0;
+    if (use_hash && !sm.status) {
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int b0 = 0; b0 < k; b0 += kNT) {  // the valid ids in row order
+        const int i = b0 + tid;
+        const int32_t id = i < k ? row[i] : -1;
+        const bool keep = id >= 0;
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) sm.warp_cnt[warp] = __popc(mk);
+        __syncthreads();
+        int off = k1h, tot = 0;
+        for (int w = 0; w < kNW; ++w) {
+          if (w < warp) off += sm.warp_cnt[w];
+          tot += sm.warp_cnt[w];
+        }
+        if (keep) tmp[off + __popc(mk & ((1u << lane) - 1u))] = id;
+        k1h += tot;
+        __syncthreads();
+      }
+    } else if (!sm.status) {
+      load_neighbours(row, k, a.n, sm, tmp);
+    }
+  } else if (k > 0) {
     load_neighbours(a.nbr + q * a.k, k, a.n, sm, tmp);
   } else {
     if (tid == 0) {
@@ -881,8 +918,8 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
   // estimate is of KDE over X \ {z} at z: z stays in X_1 (never sampled) but
   // its own term is left out, and the weights use n - 1 points.
   const double nw = a.loo ? nd - 1.0 : nd;
-  const int* rows1 = sm.nb;
-  int k1 = kk;
+  const int* rows1 = use_hash ? tmp : sm.nb;
+  int k1 = use_hash ? k1h : kk;
   if (a.loo && k > 0) {
     const int32_t z = a.nbr[q * a.k];
     int w = 0;
@@ -908,7 +945,8 @@ __global__ void __launch_bounds__(kNT) k_estimate_grad(SampleArgs a) {
     int got = 0;
     while (got < a.m) {
       const int room = min(kChunk, a.m - got);
-      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm)) {
+      if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, a.mode, sm, sm,
+                      use_hash ? hs : nullptr)) {
         ok = false;
         break;
       }
@@ -1131,8 +1169,9 @@ void launch_estimate_grad(const SampleArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
   const unsigned grid = (unsigned)a.nq;
   const int G = group_lanes(a.dp);
-  // the staged query and one partial gradient per lane group (<= 36 KB at d = 1024)
-  const size_t dyn = sizeof(float) * (size_t)a.dp * (1 + kNT / G);
+  // the staged query, one partial gradient per lane group (<= 36 KB at d = 1024)
+  // and the hash set of X_1
+  const size_t dyn = sizeof(float) * (size_t)a.dp * (1 + kNT / G) + sizeof(int) * kHashSlots;
   const int dp4 = a.dp / 4;
   if (G < 32) {  // d <= 64: shorter lane groups (measured faster than the warp-wide path)
     switch (G) {
