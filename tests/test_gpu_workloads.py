@@ -194,19 +194,34 @@ def test_unit_powerlaw_uneven_batches(pkg):
 def test_graph_replays_serve_uneven_batches(pkg):
     """Batches of uneven size served by CUDA-graph replays (one graph per
     power-of-two capacity) give exactly the direct calls' results, each batch
-    on its own sample streams (query ids continue across batches)."""
+    on its own sample streams (query ids continue across batches); one query
+    of every batch, with the neighbour set the replay returned, matches the
+    oracle's estimate from the same stream."""
     X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=1_500, n_centres=100)
-    index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=64, seed=5)
+    h = 0.2
+    index = pkg.KDEIndex(_dev(X), "exponential", h, nlist=64, seed=5)
+    C, assign = index.export_ivf()
     sizes = workloads.uneven_batches(total=1_500, nbatch=9, lo=16, hi=600, seed=3)
-    server = pkg.BatchServer(index, 100, 1000, nprobe=4, seed=11, precision=1, max_batch=1024)
+    server = pkg.BatchServer(index, 100, 1000, nprobe=4, seed=11, precision=1, max_batch=1024,
+                             neighbors=True)
     Yd = _dev(Y)
     start = 0
     for b in sizes:
-        got = server(Yd[start:start + b]).clone()
+        b = int(b)
+        got, ids = server(Yd[start:start + b])
+        got, ids = got.clone(), ids.clone()
         want = index.query(Yd[start:start + b], 100, 1000, nprobe=4, seed=11, precision=1,
                            qid_offset=start)
         assert torch.equal(got, want), b
-        start += int(b)
+        r = b // 3
+        q = start + r
+        nb = ids[r:r + 1].cpu().numpy()
+        _, w_nb, w_d2 = oracle.ivf_search(X, C.numpy(), assign.numpy(), Y[q:q + 1], 4, 100)
+        assert_neighbours_match(X, Y[q:q + 1], nb, w_nb, w_d2)
+        assert_kde_close(got[r:r + 1].cpu().numpy(),
+                         oracle.deann(X, Y[q:q + 1], "exponential", h, nb, 1000, 11,
+                                      qid_offset=q))
+        start += b
     assert len(server.graphs) >= 3
 
 
