@@ -654,7 +654,7 @@ def batched_form(torch, pkg, dev):
         # four lanes (streams with their own index views) so that the small
         # batches run side by side
         server = pkg.BatchServer(index, k, m, nprobe=P, seed=9, precision=1, max_batch=8192,
-                                 neighbors=True, streams=4)
+                                 neighbors=True, streams=4, tune_sample=Yv_d[:1000])
 
         def serve(backward):
             server.next_qid, start = 0, 0
@@ -691,7 +691,8 @@ def batched_form(torch, pkg, dev):
         ms_one_bw = ms_one + time_calls(lambda: index.grad_with_neighbors(Ybw, nbr_bw, m, seed=9),
                                         2, torch)
         r = {"k": k, "m": m, "nprobe": P, "graphs": len(server.graphs),
-             "streams": len(server.lanes), "served_ms": ms, "served_qps": nq / (ms / 1e3),
+             "streams": len(server.lanes), "scan_tile_ms": server.tile_times,
+             "served_ms": ms, "served_qps": nq / (ms / 1e3),
              "one_call_qps": nq / (ms_one / 1e3), "served_ratio": ms_one / ms,
              "served_with_backward_qps": nq / (ms_bw / 1e3),
              "one_call_with_backward_qps": nq / (ms_one_bw / 1e3),

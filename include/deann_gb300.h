@@ -106,8 +106,9 @@ typedef struct {
                                their out entries unspecified.  A call
                                captured in a CUDA graph at a fixed capacity
                                then serves a smaller batch per replay by
-                               rewriting A, with only the query-centroid
-                               distances computed for every row */
+                               rewriting A; rows past A cost at most the
+                               query-centroid distances of their tile of 128
+                               rows */
 } kde_opts;
 
 /* kde_build -- build an index over X (Section 4: FAISS-style inverted file).
@@ -161,6 +162,20 @@ kde_status kde_prepare_permuted(kde_index* index, int32_t* perm_out, const kde_o
 
 /* kde_set_bandwidth -- replace h (> 0, finite).  The IVF does not depend on h. */
 kde_status kde_set_bandwidth(kde_index* index, float h);
+
+/* kde_set_scan_tile -- the most queries one tensor-core list-scan tile takes
+ * (the MMA's N; the scan reads a probed list once per tile of its queries).
+ *   precision  KDE_PREC_BF16 or KDE_PREC_BF16X3 (the FP32 scan's tiles are
+ *              fixed).
+ *   tile       0 = automatic (the most that the operands' shared memory
+ *              holds, at most 128), or a multiple of 16 in [16, 128]; a value
+ *              above the automatic one is capped to it.
+ * The estimates, neighbour sets and distances do not depend on the tile (each
+ * distance is the same sum whatever the grouping); only the speed does.  The
+ * binding's KDEIndex.tune_scan_tile measures a few tiles on sample queries and
+ * keeps the fastest.  A view starts with its index's tiles.
+ * Errors: EINVAL. */
+kde_status kde_set_scan_tile(kde_index* index, int32_t precision, int32_t tile);
 
 /* kde_index_info -- any output pointer may be NULL. */
 kde_status kde_index_info(const kde_index* index, int64_t* n, int32_t* d, int32_t* nlist,

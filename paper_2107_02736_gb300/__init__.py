@@ -76,6 +76,7 @@ def load_library():
     sig = {
         "kde_build": [P, i64, i32, i32, f32, i32, u64, O, ctypes.POINTER(ctypes.c_void_p)],
         "kde_set_bandwidth": [P, f32],
+        "kde_set_scan_tile": [P, i32, i32],
         "kde_index_info": [P, P, P, P, P, P, P],
         "kde_export_ivf": [P, P, P],
         "kde_search": [P, P, i64, i32, i32, P, P, O],
@@ -217,6 +218,32 @@ class KDEIndex:
 
     def set_bandwidth(self, h: float):
         _check(_lib.kde_set_bandwidth(self._h, float(h)))
+
+    def set_scan_tile(self, precision: int, tile: int):
+        """kde_set_scan_tile: the most queries a tensor-core list-scan tile
+        takes for this precision (1 or 2); 0 = automatic."""
+        _check(_lib.kde_set_scan_tile(self._h, int(precision), int(tile)))
+
+    def tune_scan_tile(self, Y, k, m, nprobe, precision, tiles=(0, 96, 64, 48, 32), reps=3,
+                       seed=0):
+        """Times kde_query on the sample queries Y at each scan tile (CUDA
+        events on the current stream, one untimed call first) and keeps the
+        fastest for `precision` (kde_set_scan_tile).  Returns ({tile: ms per
+        call}, the tile kept); 0 stands for the automatic tile."""
+        times = {}
+        for t in tiles:
+            self.set_scan_tile(precision, t)
+            self.query(Y, k, m, nprobe=nprobe, seed=seed, precision=precision)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                self.query(Y, k, m, nprobe=nprobe, seed=seed, precision=precision)
+            e1.record()
+            e1.synchronize()
+            times[int(t)] = e0.elapsed_time(e1) / reps
+        best = min(times, key=times.get)
+        self.set_scan_tile(precision, best)
+        return times, best
 
     def export_ivf(self):
         """(centroids nlist x d float32, assign n int32) as CPU tensors."""
@@ -500,14 +527,21 @@ class BatchServer:
     waits for the batch's stream when it uses the result (sync()).
     With neighbors=True each call returns (estimates, neighbour ids) and
     backward() runs the adjoint of the last batch served (its sets fixed) on
-    that batch's stream."""
+    that batch's stream.  With tune_sample (queries of the workload) the
+    tensor-core scan's tile is measured and kept before any graph is
+    captured (KDEIndex.tune_scan_tile; tile_times holds the timings)."""
 
     def __init__(self, index: KDEIndex, k, m, nprobe=1, seed=0, precision=0, max_batch=8192,
-                 sample_mode=0, neighbors=False, streams=1):
+                 sample_mode=0, neighbors=False, streams=1, tune_sample=None):
         self.index, self.args = index, dict(k=k, m=m, nprobe=nprobe, seed=seed,
                                             precision=precision, sample_mode=sample_mode,
                                             neighbors=neighbors)
         self.max_batch = int(max_batch)
+        # the scan tile is fixed inside a captured graph: tune it (on sample
+        # queries of the workload) before the lanes take their views
+        self.tile_times = None
+        if tune_sample is not None and precision in (1, 2):
+            self.tile_times, _ = index.tune_scan_tile(tune_sample, k, m, nprobe, precision)
         cap = 16
         while cap < self.max_batch:
             cap *= 2

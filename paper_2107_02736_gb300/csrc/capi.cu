@@ -371,7 +371,8 @@ kde_status run_search(kde_index* ix, const CallBufs& cb, int64_t nq, int k, int 
       return fail(KDE_EINVAL, "the split BF16 scan needs d <= %d", kMaxSplitDim);
     if (tcore && !(split ? ix->xls_ok : ix->tmap_ok))
       return fail(KDE_ECUDA, "the BF16 tensor map could not be encoded on this driver");
-    const int qtile = tcore ? scan_tc_bn(ix->dpb, split) : kTile;
+    int qtile = tcore ? scan_tc_bn(ix->dpb, split) : kTile;
+    if (tcore && ix->scan_tile[precision] > 0) qtile = std::min(qtile, ix->scan_tile[precision]);
     if (qtile <= 0)
       return fail(KDE_EINVAL, "the split BF16 scan needs d <= %d", kMaxSplitDim);
     {
@@ -898,6 +899,16 @@ kde_status kde_set_bandwidth(kde_index* ix, float h) {
   TRY(check_index(ix));
   if (!(h > 0.f) || !std::isfinite(h)) return fail(KDE_EINVAL, "h must be positive and finite");
   ix->h = h;
+  return KDE_OK;
+}
+
+kde_status kde_set_scan_tile(kde_index* ix, int32_t precision, int32_t tile) {
+  TRY(check_index(ix));
+  if (precision != KDE_PREC_BF16 && precision != KDE_PREC_BF16X3)
+    return fail(KDE_EINVAL, "the scan tile is set for precision 1 (BF16) or 2 (BF16 x3 split)");
+  if (tile != 0 && (tile < 16 || tile > 128 || tile % 16 != 0))
+    return fail(KDE_EINVAL, "the scan tile must be 0 or a multiple of 16 in [16, 128]");
+  ix->scan_tile[precision] = tile;
   return KDE_OK;
 }
 

@@ -124,6 +124,7 @@ struct kde_index {
   float* xmax_d = nullptr;    // device max |x|^2
   float xmax = 0.f;           // max |x| over the dataset
   int64_t margin_failures = 0;
+  int scan_tile[3] = {0, 0, 0};  // per precision: the tensor-core scan's query tile, 0 = automatic
   deann::Arena scratch;
   std::vector<char*> retired;  // outgrown scratch buffers, freed by kde_free
   size_t scratch_limit = size_t(16) << 30;

@@ -75,6 +75,7 @@ def test_calls_reject_null_index(lib):
     assert lib.kde_query(None, None, 0, 1, 1, 1, 0, None, None, None) == 1
     assert lib.kde_exact(None, None, 0, None, None) == 1
     assert lib.kde_set_bandwidth(None, 1.0) == 1
+    assert lib.kde_set_scan_tile(None, 1, 64) == 1
     lib.kde_free(None)
 
 

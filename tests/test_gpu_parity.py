@@ -563,3 +563,28 @@ def test_fit_bandwidth_argument_errors(pkg):
         index.fit_bandwidth(np.array([0, 1], np.int32), 2048, 10)  # k > 2047
     with pytest.raises(pkg.KDEError):
         index.fit_bandwidth(np.array([0, 1], np.int32), 5, 10, sample_mode=2)
+
+
+def test_scan_tile_changes_speed_only(pkg):
+    """The tensor-core scan's query tile (kde_set_scan_tile) changes how the
+    probing queries are grouped, not a single distance: estimates, neighbour
+    sets and distances are the same bits for every tile, and the tuner keeps
+    one of the tiles it timed.  Bad tiles and the FP32 scan are refused."""
+    X, Y, _ = workloads.mixture_embed(n=20_000, nq=700, n_centres=40)
+    index = pkg.KDEIndex(_dev(X), "gaussian", 6.0, nlist=16, seed=3)
+    Yd = _dev(Y)
+    for prec in (1, 2):
+        want = index.query(Yd, 60, 500, nprobe=3, seed=4, precision=prec)
+        wn, wd = index.search(Yd, 30, nprobe=3, precision=prec)
+        for tile in (16, 48, 128):
+            index.set_scan_tile(prec, tile)
+            assert torch.equal(index.query(Yd, 60, 500, nprobe=3, seed=4, precision=prec), want)
+            gn, gd = index.search(Yd, 30, nprobe=3, precision=prec)
+            assert torch.equal(gn, wn) and torch.equal(gd, wd)
+        times, best = index.tune_scan_tile(Yd, 60, 500, 3, prec, tiles=(0, 64, 32), reps=1)
+        assert set(times) == {0, 64, 32} and best in times
+        assert torch.equal(index.query(Yd, 60, 500, nprobe=3, seed=4, precision=prec), want)
+        index.set_scan_tile(prec, 0)
+    for prec, tile in ((0, 64), (1, 40), (2, 144), (1, -16)):
+        with pytest.raises(pkg.KDEError):
+            index.set_scan_tile(prec, tile)
