@@ -669,6 +669,8 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   cnt.take<int32_t>(L);            // chosen
   cnt.take<int64_t>(L);            // counts
   cnt.take<double>((size_t)col_mean_slices(n) * ix->dp);  // column-mean partials
+  const size_t amin_keys = (size_t)2 * n * (L > 1 ? assign_tc_slices(n, (int)L) : 1);
+  cnt.take<unsigned long long>(amin_keys);                 // assignment keys
   BTRY(ensure_scratch(ix, cnt.used));
   Bump b;
   b.base = ix->scratch.base;
@@ -681,6 +683,7 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   int32_t* chosen = b.take<int32_t>(L);
   int64_t* counts = b.take<int64_t>(L);
   double* colpart = b.take<double>((size_t)col_mean_slices(n) * ix->dp);
+  unsigned long long* amin = b.take<unsigned long long>(amin_keys);
 
   const float* src = X;
   if (xs == SPACE_HOST) {
@@ -691,19 +694,53 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
   launch_row_norms(ix->X, n, ix->dp, ix->Xn, st);
   launch_max_f32(ix->Xn, n, ix->xmax_d, st);
 
+  // the dataset mean: the centre of the tensor-core operands (coarse
+  // quantiser, exact KDE, k-means assignment)
+  BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
+  launch_col_mean(ix->X, n, ix->dp, ix->mean, colpart, st);
+  {
+    uint16_t* cs = nullptr;
+    BTRY(dev_alloc(&cs, (size_t)3 * L * ix->dpb));
+    ix->Cs = cs;
+    BTRY(dev_alloc(&ix->csn, (size_t)L));
+    ix->cs_ok = make_parts_map(ix->tmap_cs, ix->Cs, 3 * L, ix->dpb);
+  }
+  if (kernel != KDE_LAPLACIAN) {
+    // the rows minus the mean split into three BF16 parts: exact KDE and the
+    // k-means assignment on the tensor cores
+    BTRY(dev_alloc(&ix->xsn, (size_t)n));
+    uint16_t* xs = nullptr;
+    BTRY(dev_alloc(&xs, (size_t)3 * n * ix->dpb));
+    ix->Xs = xs;
+    launch_split3(ix->X, n, ix->dp, ix->mean, ix->Xs, n, ix->dpb, ix->xsn, st);
+    ix->xs_ok = make_parts_map(ix->tmap_xs, ix->Xs, 3 * n, ix->dpb);
+    launch_max_f32(ix->xsn, n, ix->xmax_d + 1, st);
+  }
+  // Lloyd's assignment step: nearest centroid by the split tensor-core
+  // distances when the split rows exist, else by FP32 CUDA-core tiles
+  const bool tc_assign = ix->xs_ok && ix->cs_ok;
+  auto assign_step = [&]() -> bool {
+    if (!tc_assign) {
+      launch_assign_simt(ix->X, n, ix->C, (int)L, d, ix->dp, ix->assign, best_d2, st);
+      return true;
+    }
+    launch_split3(ix->C, L, ix->dp, ix->mean, ix->Cs, L, ix->dpb, ix->csn, st);
+    return launch_assign_tc(ix->tmap_xs, ix->xsn, n, ix->tmap_cs, ix->csn, (int)L, ix->dpb,
+                            ix->X, ix->C, d, ix->dp, amin, ix->assign, best_d2, ix->err, st);
+  };
   if (L == 1) {
     launch_fill_i32(ix->assign, n, 0, st);
   } else {
     launch_kmeans_init(ix->X, n, ix->dp, (int)L, seed, bitmap, chosen, ix->C, ix->err, st);
     for (int it = 0; it < iters; ++it) {
-      launch_assign_simt(ix->X, n, ix->C, (int)L, d, ix->dp, ix->assign, best_d2, st);
+      if (!assign_step()) return bail(fail(KDE_ECUDA, "could not configure the k-means assignment"));
       launch_list_hist(ix->assign, n, (int)L, counts, st);
       launch_exclusive_scan_i64(counts, L, ix->list_off, st);
       launch_stable_scatter(ix->assign, n, (int)L, ix->list_off, chunk_hist, ix->perm, st);
       launch_centroid_update(ix->X, ix->dp, ix->perm, ix->list_off, (int)L, ix->C, empty, st);
       launch_reseed_empty(ix->X, n, ix->dp, best_d2, empty, (int)L, ix->C, tmp_d2, st);
     }
-    launch_assign_simt(ix->X, n, ix->C, (int)L, d, ix->dp, ix->assign, best_d2, st);
+    if (!assign_step()) return bail(fail(KDE_ECUDA, "could not configure the k-means assignment"));
   }
   launch_list_hist(ix->assign, n, (int)L, counts, st);
   launch_exclusive_scan_i64(counts, L, ix->list_off, st);
@@ -725,28 +762,8 @@ kde_status kde_build(const float* X, int64_t n, int32_t d, kde_kernel kernel, fl
                          ix->XLsn, st);
     ix->xls_ok = make_parts_map(ix->tmap_xls, ix->XLs, 3 * n, ix->dpb);
   }
-  // the dataset mean: the centre of the tensor-core coarse quantiser's and
-  // exact KDE's operands
-  BTRY(dev_alloc(&ix->mean, (size_t)ix->dp));
-  launch_col_mean(ix->X, n, ix->dp, ix->mean, colpart, st);
-  {
-    uint16_t* cs = nullptr;
-    BTRY(dev_alloc(&cs, (size_t)3 * L * ix->dpb));
-    ix->Cs = cs;
-    BTRY(dev_alloc(&ix->csn, (size_t)L));
-    launch_split3(ix->C, L, ix->dp, ix->mean, ix->Cs, L, ix->dpb, ix->csn, st);
-    ix->cs_ok = make_parts_map(ix->tmap_cs, ix->Cs, 3 * L, ix->dpb);
-  }
-  if (kernel != KDE_LAPLACIAN) {
-    // exact KDE on tensor cores: centred rows split into three BF16 parts
-    BTRY(dev_alloc(&ix->xsn, (size_t)n));
-    uint16_t* xs = nullptr;
-    BTRY(dev_alloc(&xs, (size_t)3 * n * ix->dpb));
-    ix->Xs = xs;
-    launch_split3(ix->X, n, ix->dp, ix->mean, ix->Xs, n, ix->dpb, ix->xsn, st);
-    ix->xs_ok = make_parts_map(ix->tmap_xs, ix->Xs, 3 * n, ix->dpb);
-    launch_max_f32(ix->xsn, n, ix->xmax_d + 1, st);
-  }
+  // the final centroids' split parts (the tensor-core coarse quantiser)
+  launch_split3(ix->C, L, ix->dp, ix->mean, ix->Cs, L, ix->dpb, ix->csn, st);
   BCK(cudaGetLastError());
 
   ix->h_list_off = new int64_t[L + 1];

@@ -219,6 +219,17 @@ bool launch_coarse_tc(const void* tmap_c, const float* cn, int L, const void* Ys
 void launch_split3(const float* V, int64_t rows, int dp, const float* mean, void* dst,
                    int64_t rows_pad, int dpb, float* norms, cudaStream_t s);
 bool make_parts_map(void* map_out, const void* base, int64_t rows_total, int dpb);
+// k-means assignment on the tensor cores: for each point (its three BF16
+// parts centred on the dataset mean behind tmap_p, squared norms pn) the two
+// nearest centroids (parts behind tmap_c, norms cn) by the split distances,
+// then the nearer of the two by FP32 difference-form distances between the
+// rows X and C, ties to the lower id; amin is 2 np assign_tc_slices(np, L)
+// keys of scratch.
+int assign_tc_slices(int64_t np, int L);
+bool launch_assign_tc(const void* tmap_p, const float* pn, int64_t np, const void* tmap_c,
+                      const float* cn, int L, int dpb, const float* X, const float* C, int d,
+                      int dp, unsigned long long* amin, int32_t* assign, float* best_d2,
+                      uint32_t* err, cudaStream_t s);
 bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_t nq, int64_t nqp,
                      const float* xn, int64_t n, int dpb, int kern, float h, double* acc,
                      float* out, uint32_t* err, cudaStream_t s);

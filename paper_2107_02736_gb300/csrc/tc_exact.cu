@@ -53,11 +53,17 @@ struct ExactShared {
   int abort;
 };
 
+// kArgmin: the same tiles for the k-means assignment: rows are the dataset
+// points, columns the centroids, and each row keeps its two nearest columns,
+// (distance, column) packed as keys so that ties go to the lower column;
+// amin_out receives them per slice of columns, [slice][row][2].
+template <bool kArgmin>
 __global__ void __launch_bounds__(kThreads, 1)
     k_exact_tc(const __grid_constant__ CUtensorMap tmap_y, const __grid_constant__ CUtensorMap tmap_x,
                const float* __restrict__ yn, const float* __restrict__ xn, int64_t nq,
                int64_t nqp, int64_t n, int dpb, int64_t rows_per_slice, int kern, float inv,
-               double* __restrict__ acc_out, uint32_t* __restrict__ err) {
+               double* __restrict__ acc_out, unsigned long long* __restrict__ amin_out,
+               uint32_t* __restrict__ err) {
   __shared__ ExactShared sh;
   extern __shared__ uint8_t dyn_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -173,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float lam = 1.4426950408889634f * inv;  // log2(e) / (2 h^2) (Gaussian)
     const float lam2 = 2.f * lam, by = -lam * ynq;
     double rowsum = 0.0;
+    unsigned long long top1 = ~0ull, top2 = ~0ull;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       const uint32_t tph = (uint32_t)(t >> 1) & 1u;
@@ -185,7 +192,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t taddr = tmem + ((uint32_t)lg << 16) + (uint32_t)(b * 2 * kPN);
       float part = 0.f;
       const bool full = xrow + cbeg + kRun <= x_end;  // every point of the run exists
-      if (gauss && full) {
+      if (kArgmin) {
+        for (int c0 = cbeg; c0 < cbeg + kRun; c0 += 16) {
+          uint32_t v[16];
+          uint32_t w[16];
+          tc::tmem_ld16(taddr + (uint32_t)c0, v);
+          tc::tmem_ld16(taddr + (uint32_t)(kPN + c0), w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t pt = xrow + c0 + j;
+            if (pt < x_end) {
+              const float dot = __uint_as_float(v[j]) + __uint_as_float(w[j]);
+              const unsigned long long key = pack_key(xn[pt] + ynq - 2.f * dot, (int)pt);
+              if (key < top1) {
+                top2 = top1;
+                top1 = key;
+              } else if (key < top2) {
+                top2 = key;
+              }
+            }
+          }
+        }
+      } else if (gauss && full) {
         // Gaussian: K = 2^(lam (2 <x~, y~> - |x~|^2 - |y~|^2)), lam = log2(e) / (2 h^2),
         // the exponent clamped at 0 (D^2 >= 0); the run's norms in float4 loads
         // (the same addresses on every lane)
@@ -233,9 +261,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&sh.tempty[b]);
     }
-    if (qvalid && ntiles > 0) atomicAdd(acc_out + q, rowsum);
+    if (kArgmin) {
+      // the ring is free (every tile's MMAs completed): the four warps of
+      // this lane quadrant leave their column quarter's two nearest there
+      unsigned long long* top = reinterpret_cast<unsigned long long*>(ring);
+      const int quarter = (warp - 2) >> 2;
+      top[(quarter * kQM + lg + lane) * 2 + 0] = top1;
+      top[(quarter * kQM + lg + lane) * 2 + 1] = top2;
+    } else if (qvalid && ntiles > 0) {
+      atomicAdd(acc_out + q, rowsum);
+    }
   }
   __syncthreads();
+  if (kArgmin && tid < kQM && q0 + tid < nq) {
+    const unsigned long long* top = reinterpret_cast<const unsigned long long*>(ring);
+    unsigned long long t1 = ~0ull, t2 = ~0ull;
+    for (int qq = 0; qq < kEpiWarps / 4; ++qq)
+      for (int e = 0; e < 2; ++e) {
+        const unsigned long long key = top[(qq * kQM + tid) * 2 + e];
+        if (key < t1) {
+          t2 = t1;
+          t1 = key;
+        } else if (key < t2) {
+          t2 = key;
+        }
+      }
+    unsigned long long* o = amin_out + ((int64_t)blockIdx.y * nq + q0 + tid) * 2;
+    o[0] = t1;
+    o[1] = t2;
+  }
   if (tid == 0 && sh.abort) atomicOr(err, KDE_ERRBIT_TMA);
   if (warp == 1) {
     tc::tc_fence_after();
@@ -433,6 +487,46 @@ __global__ void k_exact_finish_tc(const double* __restrict__ acc, int64_t nq, do
   if (q < nq) out[q] = (float)(acc[q] * inv_n);
 }
 
+// The assignment's last step: the two nearest centroids by the tensor-core
+// distances (merged over the slices) are compared again by their FP32
+// difference-form distances, one warp per point, ties to the lower id, so
+// that the split distances' rounding (which scales with |x~|^2 + |c~|^2,
+// not with the distance) cannot flip a near tie.
+__global__ void k_assign_finish(const unsigned long long* __restrict__ top, int slices,
+                                int64_t np, const float* __restrict__ X,
+                                const float* __restrict__ C, int d, int dp,
+                                int32_t* __restrict__ assign, float* __restrict__ best_d2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  unsigned long long t1 = ~0ull, t2 = ~0ull;
+  for (int s = 0; s < slices; ++s)
+    for (int e = 0; e < 2; ++e) {
+      const unsigned long long key = top[((int64_t)s * np + p) * 2 + e];
+      if (key < t1) {
+        t2 = t1;
+        t1 = key;
+      } else if (key < t2) {
+        t2 = key;
+      }
+    }
+  const int c1 = (int)(t1 & 0xffffffffull);
+  const int c2 = t2 == ~0ull ? c1 : (int)(t2 & 0xffffffffull);
+  const float* x = X + p * dp;
+  float s1 = 0.f, s2 = 0.f;
+  for (int j = lane; j < d; j += 32) {
+    const float a = x[j] - C[(int64_t)c1 * dp + j], b = x[j] - C[(int64_t)c2 * dp + j];
+    s1 = fmaf(a, a, s1);
+    s2 = fmaf(b, b, s2);
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    const bool second = s2 < s1 || (s2 == s1 && c2 < c1);
+    assign[p] = second ? c2 : c1;
+    if (best_d2) best_d2[p] = second ? s2 : s1;
+  }
+}
 
 bool encode_parts_map(CUtensorMap* map, const void* base, int64_t rows_total, int dpb) {
   tc::EncodeTiledFn enc = tc::tensor_map_encoder();
@@ -493,7 +587,7 @@ bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_
                      float* out, uint32_t* err, cudaStream_t s) {
   CUtensorMap tmap_y;
   if (!encode_parts_map(&tmap_y, Ys, kParts * nqp, dpb)) return false;
-  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_exact_tc), exact_tc_smem()))
+  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_exact_tc<false>), exact_tc_smem()))
     return false;
   cudaMemsetAsync(acc, 0, sizeof(double) * nq, s);
   const int64_t qtiles = (nq + kQM - 1) / kQM;
@@ -505,10 +599,45 @@ bool launch_exact_tc(const void* tmap_x, const void* Ys, const float* yn, int64_
   const int64_t rows_per_slice = ((ptiles + slices - 1) / slices) * kPN;
   slices = (n + rows_per_slice - 1) / rows_per_slice;
   const dim3 grid((unsigned)qtiles, (unsigned)slices);
-  k_exact_tc<<<grid, kThreads, exact_tc_smem(), s>>>(
+  k_exact_tc<false><<<grid, kThreads, exact_tc_smem(), s>>>(
       tmap_y, *reinterpret_cast<const CUtensorMap*>(tmap_x), yn, xn, nq, nqp, n, dpb,
-      rows_per_slice, kern, kernel_inv(kern, h), acc, err);
+      rows_per_slice, kern, kernel_inv(kern, h), acc, nullptr, err);
   k_exact_finish_tc<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(acc, nq, 1.0 / (double)n, out);
+  return true;
+}
+
+int assign_tc_slices(int64_t np, int L) {
+  // about two waves of the 152 SMs, slices of whole centroid tiles
+  const int64_t ptiles = (np + kQM - 1) / kQM;
+  const int64_t ctiles = (L + kPN - 1) / kPN;
+  int64_t slices = (2 * 152 + ptiles - 1) / ptiles;
+  if (slices > ctiles) slices = ctiles;
+  if (slices < 1) slices = 1;
+  const int64_t cols_per_slice = ((ctiles + slices - 1) / slices) * kPN;
+  return (int)((L + cols_per_slice - 1) / cols_per_slice);
+}
+
+bool launch_assign_tc(const void* tmap_p, const float* pn, int64_t np, const void* tmap_c,
+                      const float* cn, int L, int dpb, const float* X, const float* C, int d,
+                      int dp, unsigned long long* amin, int32_t* assign, float* best_d2,
+                      uint32_t* err, cudaStream_t s) {
+  if (np <= 0) return true;
+  if (!set_dynamic_smem(reinterpret_cast<const void*>(&k_exact_tc<true>), exact_tc_smem()))
+    return false;
+  const int64_t ptiles = (np + kQM - 1) / kQM;
+  // about two waves of the 152 SMs, slices of whole centroid tiles
+  const int64_t ctiles = (L + kPN - 1) / kPN;
+  int64_t slices = (2 * 152 + ptiles - 1) / ptiles;
+  if (slices > ctiles) slices = ctiles;
+  if (slices < 1) slices = 1;
+  const int64_t cols_per_slice = ((ctiles + slices - 1) / slices) * kPN;
+  slices = (L + cols_per_slice - 1) / cols_per_slice;
+  const dim3 grid((unsigned)ptiles, (unsigned)slices);
+  k_exact_tc<true><<<grid, kThreads, exact_tc_smem(), s>>>(
+      *reinterpret_cast<const CUtensorMap*>(tmap_p), *reinterpret_cast<const CUtensorMap*>(tmap_c),
+      pn, cn, np, np, L, dpb, cols_per_slice, KDE_KERN_GAUSSIAN, 1.f, nullptr, amin, err);
+  k_assign_finish<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(amin, (int)slices, np, X, C, d, dp,
+                                                           assign, best_d2);
   return true;
 }
 
