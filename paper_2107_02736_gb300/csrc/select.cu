@@ -1045,7 +1045,7 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   // caller that asks for the neighbours' distances (kde_search) gets FP32
   // difference-form ones, so those calls rescore too.
   //
-  // The keys are formed four candidates a thread at a time, so that the loads
+  // The keys are formed six candidates a thread at a time, so that the loads
   // of their values, ids and norms are all in flight together.
   __shared__ int s_rescore;
   __shared__ unsigned long long s_kmin;
@@ -1056,7 +1056,7 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
     const float c32 = (float)((a.d + 7) / 8 + 8) * (1.0f / 16777216.0f);
     const bool lap = a.kern == KDE_KERN_LAPLACIAN;
     float ksum = 0.f, esum = 0.f, e32sum = 0.f;
-    constexpr int kKU = 4;
+    constexpr int kKU = 6;
     for (int j0 = tid; j0 < K; j0 += kKU * kNT) {
       int sl[kKU], pr[kKU];
       int64_t pos[kKU];
