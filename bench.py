@@ -872,24 +872,28 @@ def fp32_alu_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def stage_work(stage, nq, n, d, nlist, k, m, cbar, precision="bf16"):
+def stage_work(stage, nq, n, d, nlist, k, m, cbar, precision="bf16", method_only=False):
     """Algorithmic (bytes, flops) of one call of a query-path stage: what the
     method must move or compute, not padded tile work.  cbar = mean
     candidates per query (the probed lists' sizes).  The list scan reads the
     probed lists once (BF16, or three BF16 parts for the split scan, FP32 for
     the SIMT scan) and writes every candidate's distance; the selection reads
     them back, and with the FP32 and BF16 scans rescores the k neighbours'
-    FP32 rows per query (the split scan's distances need no rescoring)."""
+    FP32 rows per query (the split scan's distances need no rescoring).
+    method_only leaves out that write and read-back of the candidates: it is
+    this design's round trip between scan and selection, not work the
+    method itself needs."""
     dpb = (d + 63) // 64 * 64
     dp4 = (d + 3) // 4 * 4
+    cand = 0 if method_only else cbar * 4
     if stage == "estimate":   # m sampled FP32 rows (+ query, neighbour ids, output)
         return nq * (m * d * 4 + d * 4 + k * 4 + 4), 0.0
     if stage == "scan":
         lists = {"fp32": n * dp4 * 4, "bf16": n * dpb * 2, "bf16x3": 3 * n * dpb * 2}[precision]
-        return lists + nq * cbar * 4, 2.0 * nq * cbar * d
+        return lists + nq * cand, 2.0 * nq * cbar * d
     if stage == "select":
         rows = 0 if precision == "bf16x3" else k * d * 4
-        return nq * (cbar * 4 + rows + k * 4), 0.0
+        return nq * (cand + rows + k * 4), 0.0
     if stage == "coarse":     # query x centroid contraction (FP32 CUDA cores)
         return nq * d * 4, 2.0 * nq * nlist * d
     return 0, 0.0
@@ -917,6 +921,8 @@ def roofline(stage, prof, calls, nq, n, d, nlist, k, m, cbar, peaks, peak_kind, 
     r["stage"] = stage
     r["ms_per_call"] = ms
     r["t_min_ms"] = 1e3 * max(t_hbm, t_fl)
+    nb_m, _ = stage_work(stage, nq, n, d, nlist, k, m, cbar, sched["precision"], method_only=True)
+    r["t_min_method_ms"] = 1e3 * max(nb_m / (peaks["hbm_gbs"] * 1e9), t_fl)
     return r
 
 
@@ -1173,8 +1179,11 @@ def main():
     # whole query path: the sum of the stages' times at peak (their
     # algorithmic work, stage_work) over the step time
     path_roof = {"t_min_ms": sum(o["t_min_ms"] for o in others.values()),
+                 "t_min_method_ms": sum(o["t_min_method_ms"] for o in others.values()),
                  "t_measured_ms": ms_step, "mean_candidates": cbar}
     path_roof["frac"] = path_roof["t_min_ms"] / ms_step
+    # without the candidates' round trip between scan and selection
+    path_roof["frac_method"] = path_roof["t_min_method_ms"] / ms_step
     launches = sum(v["launches"] for v in prof.values())
     emit("stage_rooflines", {"stages": others, "path": path_roof})
     if tuned:
@@ -1238,7 +1247,7 @@ def main():
         "clocks": {key: clk.get(key) for key in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
         "roofline": roof_short,
         "stage_ms_per_step": stages,
-        "path_roofline": {key: path_roof[key] for key in ("frac", "t_min_ms")},
+        "path_roofline": {key: path_roof[key] for key in ("frac", "t_min_ms", "frac_method")},
         "cpu_baseline": cpu,
         "baselines": {"exact": exact, "rs_qps": nq / (ms_rs / 1e3), "rs_m": rs_m,
                       "rs_rel_err": rs_err,

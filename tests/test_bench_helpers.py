@@ -69,6 +69,12 @@ def test_stage_work_and_alu_peak():
     assert b == 10 * (50.0 * 4 + 16 * 128 * 4 + 16 * 4)
     b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0, "bf16x3")
     assert b == 10 * (50.0 * 4 + 16 * 4)
+    # the method-only count leaves out the candidates' write and read-back
+    b, f = bench.stage_work("scan", 10, 1000, 128, 8, 16, 100, 50.0, method_only=True)
+    assert b == 1000 * 128 * 2 and f == 2.0 * 10 * 50.0 * 128
+    b, _ = bench.stage_work("select", 10, 1000, 128, 8, 16, 100, 50.0, "bf16x3",
+                            method_only=True)
+    assert b == 10 * 16 * 4
     assert bench.fp32_alu_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
@@ -164,7 +170,7 @@ def _representative_headline():
                      "peak_source": "measured hbm_gbs"},
         "stage_ms_per_step": {s: 1.2345678 for s in ("stage", "coarse", "plan", "scan",
                                                      "select", "estimate")},
-        "path_roofline": {"frac": 0.8912345, "t_min_ms": 4.5712345},
+        "path_roofline": {"frac": 0.8912345, "t_min_ms": 4.5712345, "frac_method": 0.8512345},
         "cpu_baseline": {"value": 1321.12345, "unit": "queries/s", "cores": 16, "kind": "oracle",
                          "sample": "10000 test queries, IVF search + DEANN, FP64, 12.3 s",
                          "single_thread_qps": 72.512345},

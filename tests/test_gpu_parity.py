@@ -421,6 +421,31 @@ def test_gradient_matches_oracle(pkg, kernel, d):
     assert np.all(np.abs(dl - w_dl) <= 1e-4 * np.abs(w_dl) + 1e-9)
 
 
+def test_gradient_with_padding_and_repeated_ids(pkg):
+    """Neighbour rows with -1 padding between valid ids (the hash-set path,
+    rows taken in row order) and rows with a repeated id (the sorted,
+    deduplicated path): both give the oracle's gradient, k' counting each id
+    once."""
+    n, nq, k, m, d = 2500, 36, 30, 400, 16
+    X, Y = _data(n, d, nq, seed=71)
+    h = _bandwidth(d)
+    nbr, _ = oracle.knn(X, Y, k)
+    nbr[0::3, 4] = -1
+    nbr[0::3, 11] = -1
+    nbr[1::3, 7] = nbr[1::3, 2]
+    index = pkg.KDEIndex(_dev(X), "gaussian", h)
+    out, dY, dl = index.grad_with_neighbors(_dev(Y), _dev(nbr), m, seed=8)
+    w_out, w_dY, w_dl = oracle.deann_grad(X, Y, "gaussian", h, nbr, m, 8)
+    assert_kde_close(out.cpu().numpy(), w_out)
+    dY = dY.cpu().numpy().astype(np.float64)
+    for q in range(nq):
+        assert np.linalg.norm(dY[q] - w_dY[q]) <= 1e-4 * np.linalg.norm(w_dY[q]) + 1e-9
+    assert np.all(np.abs(dl.cpu().numpy() - w_dl) <= 1e-4 * np.abs(w_dl) + 1e-9)
+    # the forward estimate with the same rows (sorted path: s1 computed here)
+    assert_kde_close(index.query_with_neighbors(_dev(Y), _dev(nbr), m, seed=8).cpu().numpy(),
+                     w_out)
+
+
 @pytest.mark.parametrize("kernel,precision", [("gaussian", 1), ("exponential", 0),
                                               ("laplacian", 0), ("gaussian", 2)])
 def test_grad_entry_point_matches_oracle(pkg, kernel, precision):
