@@ -147,12 +147,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
           const uint32_t st = tc::smem_u32(ring + s * kStageBytes);
+          // the parts' descriptors once per stage; a K step of 16 BF16 (32
+          // bytes) adds 2 to the start-address field
+          uint64_t dA[kParts], dB[kParts];
+#pragma unroll
+          for (int p = 0; p < kParts; ++p) {
+            dA[p] = tc::desc_sw128(st + p * kPartBytes);
+            dB[p] = tc::desc_sw128(st + (kParts + p) * kPartBytes);
+          }
 #pragma unroll
           for (int kk = 0; kk < kKC / 16; ++kk) {
 #pragma unroll
             for (int j = 0; j < 6; ++j) {
-              const uint64_t da = tc::desc_sw128(st + pa[j] * kPartBytes + kk * 32);
-              const uint64_t db = tc::desc_sw128(st + (kParts + pb[j]) * kPartBytes + kk * 32);
+              const uint64_t da = dA[pa[j]] + (uint64_t)(2 * kk);
+              const uint64_t db = dB[pb[j]] + (uint64_t)(2 * kk);
               if (j == 0)
                 tc::mma_f16(d_main, da, db, idesc, (kb | kk) != 0 ? 1u : 0u);
               else
@@ -371,12 +379,18 @@ __global__ void __launch_bounds__(kCoarseThreads, 1)
         }
         tc::tc_fence_after();
         const uint32_t st = tc::smem_u32(ring + s * kStageBytes);
+        uint64_t dA[kParts], dB[kParts];
+#pragma unroll
+        for (int p = 0; p < kParts; ++p) {
+          dA[p] = tc::desc_sw128(st + p * kPartBytes);
+          dB[p] = tc::desc_sw128(st + (kParts + p) * kPartBytes);
+        }
 #pragma unroll
         for (int kk = 0; kk < kKC / 16; ++kk) {
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
-            const uint64_t da = tc::desc_sw128(st + pa[j] * kPartBytes + kk * 32);
-            const uint64_t db = tc::desc_sw128(st + (kParts + pb[j]) * kPartBytes + kk * 32);
+            const uint64_t da = dA[pa[j]] + (uint64_t)(2 * kk);
+            const uint64_t db = dB[pb[j]] + (uint64_t)(2 * kk);
             if (j == 0)
               tc::mma_f16(tmem, da, db, idesc, (kb | kk) != 0 ? 1u : 0u);
             else
