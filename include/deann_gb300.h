@@ -196,7 +196,9 @@ kde_status kde_export_ivf(kde_index* index, float* centroids, int32_t* assign);
  *          (With the split scan, passing d2 makes the call rescore the
  *          candidates' rows as the BF16 scan does.)
  * Candidates are ranked first by approximate distances from the scan (see
- * opts.precision) and the best k + margin are rescored exactly. */
+ * opts.precision); every candidate within the scan's error band of the k-th
+ * is then rescored in FP32 difference form, which makes the set the exact
+ * top k (ties at the k-th distance excepted). */
 kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t nprobe,
                       int32_t* nbr, float* d2, const kde_opts* opts);
 
