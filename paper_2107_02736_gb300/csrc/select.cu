@@ -20,8 +20,8 @@
 //    id), or as a set for the query path) and the exact neighbour
 //    contribution s1 = sum_{X_1} K_h(x, y) (Algorithm 1).
 //
-// More than kSelectCap candidates in the band cannot all be kept: the
-// kSelectCap smallest are rescored and the query is counted as uncertified in
+// More than the kept-candidate capacity in the band cannot all be kept: the
+// smallest that fit are rescored and the query is counted as uncertified in
 // the device error word (kde_stats).
 #include "common.cuh"
 
@@ -48,6 +48,7 @@ __global__ void k_query_norms(const float* __restrict__ Y, int64_t nq, int dp,
 
 template <int Cap>
 struct SelectSmemT {
+  static constexpr int kCap = Cap;
   int hist[256];
   int warp_a[kNW];
   int warp_b[kNW];
@@ -56,10 +57,16 @@ struct SelectSmemT {
   unsigned long long key[Cap];
 };
 using SelectSmem = SelectSmemT<kSelectCap>;  // neighbour selection
+// for k <= kSmallCapMaxK on the split scan's values: 3,072 candidates kept,
+// small enough (with 48 registers a thread) for five blocks an SM instead of
+// four
+constexpr int kSmallCap = 3072;
+constexpr int kSmallCapMaxK = 1536;
+using SelectSmemSmall = SelectSmemT<kSmallCap>;
 constexpr int kProbeCap = 512;               // probe selection: nprobe + margin <= 384
 using ProbeSmem = SelectSmemT<kProbeCap>;
 
-// Selects the K smallest of vals[0..cnt) (1 <= K <= min(cnt, kSelectCap)):
+// Selects the K smallest of vals[0..cnt) (1 <= K <= min(cnt, the capacity)):
 // sm.slot[0..K) receives their indices (those strictly below the K-th key in
 // index order, then the lowest-index ties).  Returns the K-th key.
 template <class SM>
@@ -196,8 +203,9 @@ constexpr uint32_t kInfKey = 0x7f800000u;  // dist_key(+inf)
 // order (rounds of kU * kNT float4s; within a round, thread by thread).
 // Returns the total count, which may exceed cap (then the slots hold only
 // the first cap).
+template <class SM>
 __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uint32_t thr, int cap,
-                                SelectSmem& sm) {
+                                SM& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float4* v4 = reinterpret_cast<const float4*>(vals);
   const int64_t n4 = (cnt + 3) >> 2;
@@ -253,8 +261,9 @@ __device__ int block_collect_le(const float* __restrict__ vals, int64_t cnt, uin
 // with two passes: the minimum and maximum, then a 4096-bin histogram on the
 // linear scale between them.  Returns lo <= (k-th smallest) <= hi, the bounds
 // of the bin that holds it, widened by a few units of rounding.
+template <class SM>
 __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, int k,
-                                  SelectSmem& sm, float& lo_out, float& hi_out,
+                                  SM& sm, float& lo_out, float& hi_out,
                                   float lo_hint, float hi_hint) {
   constexpr int kBins = 4096;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -345,7 +354,8 @@ __device__ void block_kth_bracket(const float* __restrict__ vals, int64_t cnt, i
 
 // k-th smallest distance key (upper 32 bits) among sm.key[0..K), 1 <= k <= K,
 // by four 8-bit radix passes over shared memory.
-__device__ uint32_t smem_kth_dist(SelectSmem& sm, int K, int k) {
+template <class SM>
+__device__ uint32_t smem_kth_dist(SM& sm, int K, int k) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t prefix = 0, pmask = 0;
   int want = k;
@@ -663,7 +673,8 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const int64_t* __restri
 // is a lower bound on the k-th smallest distance that the keys' own values
 // were bracketed with (then the k-th is found among the keys at or above it),
 // else -1.  kmin is the smallest key when the caller has it, else ~0.
-__device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
+template <class SM>
+__device__ void rank_keys(const SelectArgs& a, SM& sm, int K, int64_t q,
                           const float* __restrict__ y, float band_abs, float tk_lo,
                           unsigned long long kmin) {
   __shared__ float s_red[kNW];
@@ -931,19 +942,25 @@ __device__ void rank_keys(const SelectArgs& a, SelectSmem& sm, int K, int64_t q,
 // --------------------------------------------------------------------------
 // Neighbour selection from the scan's candidate buffer.
 // --------------------------------------------------------------------------
-constexpr size_t kSelectTablesOffset = (sizeof(SelectSmem) + 15) & ~size_t(15);
+template <class SM>
+__host__ __device__ constexpr size_t select_tables_offset() {
+  return (sizeof(SM) + 15) & ~size_t(15);
+}
+template <class SM>
 size_t select_smem_bytes(int P) {
-  return kSelectTablesOffset + (size_t)(3 * P + 1) * sizeof(int64_t) +
+  return select_tables_offset<SM>() + (size_t)(3 * P + 1) * sizeof(int64_t) +
          (size_t)P * sizeof(float);
 }
 
-__global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
-  // SelectSmem, then the per-probe tables sized by P, in dynamic shared
-  // memory (> 48 KB; sized so that four blocks fit an SM)
+template <class SM, int kMinBlocks>
+__global__ void __launch_bounds__(kNT, kMinBlocks) k_select_neighbors(SelectArgs a) {
+  // SM, then the per-probe tables sized by P, in dynamic shared memory
+  // (> 48 KB; sized so that kMinBlocks blocks fit an SM)
   extern __shared__ uint4 sel_dyn4[];
-  SelectSmem& sm = *reinterpret_cast<SelectSmem*>(sel_dyn4);
+  SM& sm = *reinterpret_cast<SM*>(sel_dyn4);
+  constexpr int kCap = SM::kCap;
   int64_t* s_seg = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(sel_dyn4) +
-                                              kSelectTablesOffset);  // [P + 1]
+                                              select_tables_offset<SM>());  // [P + 1]
   int64_t* s_lstart = s_seg + (a.P + 1);                              // [P]
   int64_t* s_llen = s_lstart + a.P;                                   // [P]
   float* s_dc = reinterpret_cast<float*>(s_llen + a.P);               // [P] |y - c_l|
@@ -1006,19 +1023,19 @@ __global__ void __launch_bounds__(kNT, 4) k_select_neighbors(SelectArgs a) {
   // of the k-th smallest approximate distance t_k.  The true k-th distance is
   // at most t_k + E, and a point of the true top k has an approximate
   // distance at most (t_k + E) + E, so this set always contains the exact
-  // top k.  Beyond kSelectCap candidates the kSelectCap smallest are kept and
+  // top k.  Beyond kCap candidates the kCap smallest are kept and
   // the query is counted as uncertified.
   int K;
   float tk_lo = -1.f, tk_hi;  // t_k lies in [tk_lo, tk_hi]
   if (cnt_real <= (int64_t)a.k) {
-    K = block_collect_le(vals, cnt, kInfKey, kSelectCap, sm);  // every finite value
+    K = block_collect_le(vals, cnt, kInfKey, kCap, sm);  // every finite value
   } else {
     block_kth_bracket(vals, cnt, a.k, sm, tk_lo, tk_hi, s_hint_lo, s_hint_hi);
     const uint32_t thr = dist_key(tk_hi + 2.f * s_E);
-    K = block_collect_le(vals, cnt, thr, kSelectCap, sm);
-    if (K > kSelectCap) {
-      block_select(vals, cnt, kSelectCap, sm);
-      K = kSelectCap;
+    K = block_collect_le(vals, cnt, thr, kCap, sm);
+    if (K > kCap) {
+      block_select(vals, cnt, kCap, sm);
+      K = kCap;
       if (tid == 0) {
         atomicOr(a.err, KDE_ERRBIT_MARGIN);
         atomicAdd(a.err + 1, 1u);
@@ -1280,9 +1297,18 @@ void launch_select_order(const int32_t* probes, int64_t nq, int P, int L, int64_
 
 void launch_select_neighbors(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
-  const size_t bytes = select_smem_bytes(a.P);
-  set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors), select_smem_bytes(kMaxProbe));
-  k_select_neighbors<<<(unsigned)a.nq, kNT, bytes, s>>>(a);
+  // the five-block instance spills a few registers: worth it where no rows
+  // are rescored (the split scan's keys), not in the rescoring loop
+  if (a.k <= kSmallCapMaxK && a.rescore == 0 && a.nd2 == nullptr) {
+    set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors<SelectSmemSmall, 5>),
+                     select_smem_bytes<SelectSmemSmall>(kMaxProbe));
+    k_select_neighbors<SelectSmemSmall, 5>
+        <<<(unsigned)a.nq, kNT, select_smem_bytes<SelectSmemSmall>(a.P), s>>>(a);
+  } else {
+    set_dynamic_smem(reinterpret_cast<const void*>(&k_select_neighbors<SelectSmem, 4>),
+                     select_smem_bytes<SelectSmem>(kMaxProbe));
+    k_select_neighbors<SelectSmem, 4><<<(unsigned)a.nq, kNT, select_smem_bytes<SelectSmem>(a.P), s>>>(a);
+  }
 }
 
 }  // namespace deann

@@ -225,6 +225,27 @@ def test_graph_replays_serve_uneven_batches(pkg):
     assert len(server.graphs) >= 3
 
 
+def test_batch_server_tunes_the_scan_tile_before_capture(pkg):
+    """BatchServer(tune_sample=...) times the scan tiles on the sample before
+    any graph is captured; the views the lanes take start with the tile kept,
+    and the served batches equal direct calls."""
+    X, Y, _ = workloads.unit_powerlaw(n=20_000, nq=900, n_centres=80)
+    index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=32, seed=5)
+    Yd = _dev(Y)
+    server = pkg.BatchServer(index, 80, 600, nprobe=3, seed=2, precision=2, max_batch=512,
+                             streams=2, tune_sample=Yd[:256])
+    assert server.tile_times and set(server.tile_times) >= {0, 32}
+    res = torch.empty(Y.shape[0], dtype=torch.float32, device="cuda")
+    start = 0
+    for nb in (17, 300, 64, 419):
+        server(Yd[start:start + nb], out=res[start:start + nb])
+        start += nb
+    server.sync()
+    torch.cuda.synchronize()
+    want = index.query(Yd[:start], 80, 600, nprobe=3, seed=2, precision=2)
+    assert torch.equal(res[:start], want)
+
+
 def _data_small(n=3000, d=8, nq=40, seed=0):
     rng = np.random.default_rng(seed)
     return (rng.standard_normal((n, d)).astype(np.float32),
