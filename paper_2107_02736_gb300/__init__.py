@@ -77,6 +77,7 @@ def load_library():
         "kde_build": [P, i64, i32, i32, f32, i32, u64, O, ctypes.POINTER(ctypes.c_void_p)],
         "kde_set_bandwidth": [P, f32],
         "kde_set_scan_tile": [P, i32, i32],
+        "kde_set_phase_window": [P, i64],
         "kde_index_info": [P, P, P, P, P, P, P],
         "kde_export_ivf": [P, P, P],
         "kde_search": [P, P, i64, i32, i32, P, P, O],
@@ -223,6 +224,11 @@ class KDEIndex:
         """kde_set_scan_tile: the most queries a tensor-core list-scan tile
         takes for this precision (1 or 2); 0 = automatic."""
         _check(_lib.kde_set_scan_tile(self._h, int(precision), int(tile)))
+
+    def set_phase_window(self, nbytes: int):
+        """kde_set_phase_window: the bytes of X one phase of the query
+        estimator reads (0 = per-query gathers always)."""
+        _check(_lib.kde_set_phase_window(self._h, int(nbytes)))
 
     def tune_scan_tile(self, Y, k, m, nprobe, precision, tiles=(0, 96, 64, 48, 32), reps=3,
                        seed=0):

@@ -248,6 +248,12 @@ struct CallBufs {
   int32_t* win_kk = nullptr;
   float* win_s1 = nullptr;
   double* win_part = nullptr;    // nq x nslices
+  // phased estimator (query calls)
+  PhasePlan ph;
+  int32_t* ph_ids = nullptr;     // nq x m
+  int32_t* ph_off = nullptr;     // nq x (P + 1)
+  int32_t* ph_info = nullptr;    // nq
+  float* ph_part = nullptr;      // P x nq
   // bandwidth fitting
   int32_t* fit_zid = nullptr;    // nq training point ids
   int32_t* fit_nbr = nullptr;    // nq x fit_k search neighbours
@@ -299,6 +305,15 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
       cb.win_kk = b.take<int32_t>(nq);
       cb.win_s1 = b.take<float>(nq);
       cb.win_part = b.take<double>((size_t)nq * cb.win.nslices);
+    }
+  }
+  if (c.search && c.k > 0 && c.m > 0) {
+    cb.ph = phase_plan(ix->n, ix->dp, c.m, c.nq, ix->phase_bytes);
+    if (cb.ph.P > 0) {
+      cb.ph_ids = b.take<int32_t>((size_t)nq * c.m);
+      cb.ph_off = b.take<int32_t>((size_t)nq * (cb.ph.P + 1));
+      cb.ph_info = b.take<int32_t>(nq);
+      cb.ph_part = b.take<float>((size_t)nq * cb.ph.P);
     }
   }
   if (c.fit_k >= 0) {
@@ -532,10 +547,25 @@ kde_status finish_call(kde_index* ix, bool host, cudaStream_t st) {
   return s;
 }
 
-// The estimator of a query call: per-query gathers (k_estimate), or, for
-// permuted windows that many queries of the batch share, the tiled window
-// path (prep, tiles, finish).
+// The estimator of a query call: per-query gathers (k_estimate); the phased
+// order (draws, window-by-window gathers, finish) when X is several L2-sized
+// windows and the batch is large; or, for permuted windows that many queries
+// of the batch share, the tiled window path (prep, tiles, finish).
 void run_estimate(kde_index* ix, const CallBufs& cb, const SampleArgs& a, cudaStream_t st) {
+  if (a.mode == 0 && a.k > 0 && a.rs == 0 && a.loo == 0 && a.s1_in != nullptr &&
+      a.out != nullptr && a.samples == nullptr && a.m > 0 && a.m <= kPhasedMaxM &&
+      cb.ph.P > 0 && cb.ph_ids != nullptr) {
+    StageTimer t(ix, ST_ESTIMATE, st, 3);
+    PhaseArgs ph;
+    ph.P = cb.ph.P;
+    ph.shift = cb.ph.shift;
+    ph.ids = cb.ph_ids;
+    ph.off = cb.ph_off;
+    ph.info = cb.ph_info;
+    ph.part = cb.ph_part;
+    launch_estimate_phased(a, ph, st);
+    return;
+  }
   if (a.mode == 2 && a.m > 0 && a.out != nullptr && a.samples == nullptr &&
       cb.win_part != nullptr) {
     StageTimer t(ix, ST_ESTIMATE, st, 3);
@@ -926,6 +956,13 @@ kde_status kde_set_scan_tile(kde_index* ix, int32_t precision, int32_t tile) {
   if (tile != 0 && (tile < 16 || tile > 128 || tile % 16 != 0))
     return fail(KDE_EINVAL, "the scan tile must be 0 or a multiple of 16 in [16, 128]");
   ix->scan_tile[precision] = tile;
+  return KDE_OK;
+}
+
+kde_status kde_set_phase_window(kde_index* ix, int64_t bytes) {
+  TRY(check_index(ix));
+  if (bytes < 0) return fail(KDE_EINVAL, "the phase window must be 0 (off) or a byte count");
+  ix->phase_bytes = bytes;
   return KDE_OK;
 }
 

@@ -125,6 +125,9 @@ struct kde_index {
   float xmax = 0.f;           // max |x| over the dataset
   int64_t margin_failures = 0;
   int scan_tile[3] = {0, 0, 0};  // per precision: the tensor-core scan's query tile, 0 = automatic
+  // bytes of X one phase of the phased estimator reads (an L2-sized window);
+  // 0 turns the phased order off
+  int64_t phase_bytes = int64_t(64) << 20;
   deann::Arena scratch;
   std::vector<char*> retired;  // outgrown scratch buffers, freed by kde_free
   size_t scratch_limit = size_t(16) << 30;
@@ -328,6 +331,34 @@ struct SampleArgs {
   uint32_t* err;
 };
 void launch_estimate(const SampleArgs& a, cudaStream_t s);
+
+// ---- sample.cu: the phased estimator ----------------------------------------
+// The sampled rows of a batch are gathered in P phases, phase p reading only
+// rows [p W, (p + 1) W) of X (W a power of two), so that the window a phase reads stays in L2
+// while every query's draws inside it are summed.  One kernel draws each
+// query's m accepted indices and sorts them stably by window; a phase-major
+// grid sums each (window, query) run; a last kernel combines the P partial
+// sums in window order into the estimate.
+constexpr int kMaxPhases = 64;       // more windows leave too few rows per run
+constexpr int kMinPhaseRows = 64;    // at least this many rows per run on average
+constexpr int kPhasedMaxM = 8192;    // the draws of a query sit in shared memory
+constexpr int64_t kPhasedMinQueries = 256;
+struct PhasePlan {
+  int P = 0;                 // windows; 0 = the per-query gathers instead
+  int shift = 0;             // rows per window W = 2^shift (the last may be shorter)
+};
+PhasePlan phase_plan(int64_t n, int dp, int m, int64_t nq, int64_t window_bytes);
+struct PhaseArgs {
+  int P = 0;
+  int shift = 0;             // row id -> window: id >> shift
+  int32_t* ids = nullptr;    // [nq x m] accepted draws, sorted stably by window
+  int32_t* off = nullptr;    // [nq x (P + 1)] start of each window's run; off[P] = m
+  int32_t* info = nullptr;   // [nq] k' of the query, or -1 when it failed
+  float* part = nullptr;     // [P x nq] per-window sums of kernel values
+};
+// Needs a.mode == 0, a.k > 0, a.s1_in, a.out, no a.samples, not a.rs, and
+// 0 < a.m <= kPhasedMaxM.
+void launch_estimate_phased(const SampleArgs& a, const PhaseArgs& ph, cudaStream_t s);
 
 // ---- window.cu + sample.cu: permuted windows shared by many queries --------
 // Queries whose ids agree mod P = n / gcd(n, m) read the same window; a batch

@@ -22,6 +22,8 @@
 // ell = (qid m) mod n, wrapping at n; window entries whose id pi(j) is in X_1
 // are dropped and the m' kept ones are normalised by m':
 // out = (s1 + ((n - k') / m') s2) / n (s1 / n when m' = 0).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace deann {
@@ -45,6 +47,20 @@ struct EstSmem {
   int64_t tnext;
   int status;
   int dup;                     // the hash set met a repeated id
+  static constexpr bool kSorted = true;  // nb holds X_1 sorted (binary search)
+};
+
+// The phased estimator's draw kernel needs X_1 only as the hash set and its
+// filter; its draws go straight to the caller's array.
+struct PhaseSmem {
+  uint32_t filt[kFiltWords];
+  int warp_cnt[kNW];
+  int kk;
+  int cnt;
+  int64_t tnext;
+  int status;
+  int dup;
+  static constexpr bool kSorted = false;
 };
 
 __device__ __forceinline__ bool is_member(const int* nb, int kk, int64_t id) {
@@ -88,7 +104,8 @@ __device__ __forceinline__ bool hash_has(const int* hs, int id) {
 }
 
 // Membership with the filter first (one shared load rules most ids out).
-__device__ __forceinline__ bool is_member_h(const EstSmem& sm, const int* hs, int64_t id) {
+template <class SMT>
+__device__ __forceinline__ bool is_member_h(const SMT& sm, const int* hs, int64_t id) {
   const uint32_t w = sm.filt[(id >> 5) & (kFiltWords - 1)];
   if (((w >> (id & 31)) & 1u) == 0u) return false;
   return hash_has(hs, (int)id);
@@ -165,8 +182,9 @@ __device__ void load_neighbours(const int32_t* __restrict__ row, int k, int64_t 
 
 // Inserts the neighbour row into the hash set hs and the filter: sm.kk
 // receives the number of distinct valid ids, sm.status = 1 when an id is >= n.
+template <class SMT>
 __device__ void load_neighbours_hash(const int32_t* __restrict__ row, int k, int64_t n,
-                                     EstSmem& sm, int* hs) {
+                                     SMT& sm, int* hs) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < kHashSlots; i += kNT) hs[i] = -1;
   for (int i = tid; i < kFiltWords; i += kNT) sm.filt[i] = 0u;
@@ -204,18 +222,24 @@ __device__ void load_neighbours_hash(const int32_t* __restrict__ row, int k, int
   __syncthreads();
 }
 
-// Fills sm.S[0..sm.cnt) with the next accepted sample indices (at most
-// `room`), starting at draw t0; sets sm.tnext to the first unused draw.
+// Fills S_out[0..sm.cnt) (sm.S when S_out is null) with the next accepted
+// sample indices (at most `room`), starting at draw t0; sets sm.tnext to the
+// first unused draw.
 // mode 0 rejects members of X_1; mode 1 accepts every draw.  Returns false
 // when the draw cap is reached.  A round covers kNT * kDraws consecutive
 // draws, thread i taking kDraws of them in a row, so the accepted draws are
 // ranked in draw order by a block prefix sum of the per-thread counts.
 constexpr int kDraws = 4;
-// Membership is tested on the hash set hs when given, else on sm.nb.
+// Membership is tested on the hash set hs when given, else on sm.nb (an
+// SMT without the sorted set always takes hs and S_out).
+template <class SMT>
 __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, int64_t cap,
-                           int room, int mode, const EstSmem& smc, EstSmem& sm,
-                           const int* hs = nullptr) {
+                           int room, int mode, const SMT& smc, SMT& sm,
+                           const int* hs = nullptr, int* S_out = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int* S;
+  if constexpr (SMT::kSorted) S = S_out != nullptr ? S_out : sm.S;
+  else S = S_out;
   int filled = 0;
   int64_t t = t0;
   bool ok = true;
@@ -232,9 +256,12 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
       ids[r] = 0;
       if (tb + r < cap) {
         ids[r] = (int)draw_index(seed, qid, (uint32_t)(tb + r), 0u, n);
-        if (mode == 1 ||
-            !(hs != nullptr ? is_member_h(smc, hs, ids[r]) : is_member_f(smc, smc.kk, ids[r])))
-          accm |= 1u << r;
+        bool member;
+        if constexpr (SMT::kSorted)
+          member = hs != nullptr ? is_member_h(smc, hs, ids[r]) : is_member_f(smc, smc.kk, ids[r]);
+        else
+          member = is_member_h(smc, hs, ids[r]);
+        if (mode == 1 || !member) accm |= 1u << r;
       }
     }
     const int mine = __popc(accm);
@@ -257,7 +284,7 @@ __device__ bool draw_chunk(uint64_t seed, uint64_t qid, uint64_t n, int64_t t0, 
     for (int r = 0; r < kDraws; ++r) {
       if ((accm >> r) & 1u) {
         if (rank < left) {
-          sm.S[filled + rank] = ids[r];
+          S[filled + rank] = ids[r];
           if (rank == left - 1) sm.tnext = tb + r + 1;
         }
         ++rank;
@@ -329,7 +356,9 @@ __device__ __forceinline__ void prefetch_next_rows(const float* __restrict__ X, 
 
 // Sum of kernel values over rows ids[0..cnt) of X, by groups of G lanes.
 // Returns this thread's partial (lane-in-group 0 holds the group sums).
-template <int G, bool L1>
+// kPf: request the next rows into L2 ahead of their loads (G = 32), for rows
+// that come from HBM; the phased estimator's rows are L2 hits already.
+template <int G, bool L1, bool kPf = true>
 __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __restrict__ ys,
                             const int* ids, int cnt, int kern, float inv) {
   const int tid = threadIdx.x;
@@ -347,7 +376,7 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
     int rid[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) rid[u] = base + u < cnt ? ids[base + u] : -1;
-    if (G == 32) prefetch_next_rows(X, dp, ids, cnt, wb + kNW * kUnroll);
+    if (G == 32 && kPf) prefetch_next_rows(X, dp, ids, cnt, wb + kNW * kUnroll);
     const float4* X4 = reinterpret_cast<const float4*>(X);
     float acc[kUnroll];
 #pragma unroll
@@ -399,6 +428,28 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
       v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
       const int row = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
       if ((lane & 3) == 0 && base + row < cnt) part += kernel_from_dist(kern, v1, inv);
+    } else if (G == 8 && !kPf) {
+      // (the phased gathers) reduce-scatter of the 8 rows over the group's 8
+      // lanes: three halving exchanges leave lane l of the group with the
+      // whole sum of row l (the same pairwise sums as group_sum, so the same
+      // distance bits), and the kernel is evaluated once per row on all lanes
+      float v4[4], v2[2], v1;
+      const bool h4 = lig & 4, h2 = lig & 2, h1 = lig & 1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? acc[i + 4] : acc[i], send = h4 ? acc[i] : acc[i + 4];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = h2 ? v4[i + 2] : v4[i], send = h2 ? v4[i] : v4[i + 2];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+      }
+      {
+        const float keep = h1 ? v2[1] : v2[0], send = h1 ? v2[0] : v2[1];
+        v1 = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+      }
+      if (base + lig < cnt) part += kernel_from_dist(kern, v1, inv);
     } else {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
@@ -410,11 +461,11 @@ __device__ float gather_sum(const float* __restrict__ X, int dp, const float* __
   return part;
 }
 
-template <int G>
+template <int G, bool kPf = true>
 __device__ float gather_sum_k(const float* X, int dp, const float* ys, const int* ids, int cnt,
                               int kern, float inv) {
-  return kern == KDE_KERN_LAPLACIAN ? gather_sum<G, true>(X, dp, ys, ids, cnt, kern, inv)
-                                    : gather_sum<G, false>(X, dp, ys, ids, cnt, kern, inv);
+  return kern == KDE_KERN_LAPLACIAN ? gather_sum<G, true, kPf>(X, dp, ys, ids, cnt, kern, inv)
+                                    : gather_sum<G, false, kPf>(X, dp, ys, ids, cnt, kern, inv);
 }
 
 __device__ float block_sum(float v, EstSmem& sm) {
@@ -559,6 +610,171 @@ __global__ void __launch_bounds__(kNT, 4) k_estimate(SampleArgs a) {
     if (sampled == false && a.samples)
       for (int i = 0; i < a.m; ++i) a.samples[q * a.m + i] = -1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Phased estimator.  The sum s2 over the sample does not depend on the order
+// of its terms, so the batch's draws are regrouped by the window of X they
+// fall in, and the windows are read one after another: a window of tens of
+// megabytes stays in L2 while every query's rows inside it are gathered, and
+// X comes from HBM about once per call instead of once per draw.
+// ---------------------------------------------------------------------------
+
+// Per query: X_1 as a hash set, the m accepted draws of Algorithm 1 (the same
+// Philox stream and rejection as k_estimate) into shared memory, then a
+// stable counting sort of them by window (window-major, then warp, then draw
+// order) written to ph.ids, with the run starts in ph.off and k' in ph.info.
+__global__ void __launch_bounds__(kNT) k_draw_phased(SampleArgs a, PhaseArgs ph) {
+  __shared__ PhaseSmem sm;
+  __shared__ int hs[kHashSlots];
+  extern __shared__ int dsm[];
+  int* drawn = dsm;          // [m] accepted draws in draw order
+  int* wc = dsm + a.m;       // [kNW x P] per-warp window counts, then run starts
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.active != nullptr && q >= *a.active) return;  // inactive row: no output
+  const uint64_t qid = a.qid_offset + (a.dev_qid != nullptr ? *a.dev_qid : 0ull) + (uint64_t)q;
+  const int P = ph.P;
+  int32_t* off = ph.off + q * (P + 1);
+  load_neighbours_hash(a.nbr + q * a.k, a.k, a.n, sm, hs);
+  if (sm.status) {
+    for (int p = tid; p <= P; p += kNT) off[p] = 0;
+    if (tid == 0) {
+      atomicOr(a.err, KDE_ERRBIT_BADNBR);
+      ph.info[q] = -1;
+    }
+    return;
+  }
+  const int kk = sm.kk;
+  if ((int64_t)kk == a.n) {  // X_1 is all of X: nothing is sampled
+    for (int p = tid; p <= P; p += kNT) off[p] = 0;
+    if (tid == 0) ph.info[q] = kk;
+    return;
+  }
+  const int64_t cap = 64 * (int64_t)a.m + 4096;
+  int64_t t0 = 0;
+  int got = 0;
+  while (got < a.m) {
+    const int room = min(kChunk, a.m - got);
+    if (!draw_chunk(a.seed, qid, (uint64_t)a.n, t0, cap, room, 0, sm, sm, hs, drawn + got)) {
+      for (int p = tid; p <= P; p += kNT) off[p] = 0;
+      if (tid == 0) {
+        atomicOr(a.err, KDE_ERRBIT_DRAWCAP);
+        ph.info[q] = -1;
+      }
+      return;
+    }
+    t0 = sm.tnext;
+    got += sm.cnt;
+    __syncthreads();
+  }
+  for (int i = tid; i < kNW * P; i += kNT) wc[i] = 0;
+  __syncthreads();
+  // warp w sorts draws [s0, s1) of the query; lanes holding the same window
+  // find one another with a match, the lowest of them counts for all
+  const int sh = ph.shift;  // window of row id: id >> sh
+  const int seg = (a.m + kNW - 1) / kNW;
+  const int s0 = min(a.m, warp * seg), s1 = min(a.m, s0 + seg);
+  for (int r = s0; r < s1; r += 32) {
+    const int i = r + lane;
+    const int b = i < s1 ? drawn[i] >> sh : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) wc[warp * P + b] += __popc(peers);
+  }
+  __syncthreads();
+  // exclusive scan in (window, warp) order: wc[w P + b] becomes the start of
+  // warp w's part of window b's run; off[b] the start of the run
+  if (warp == 0) {
+    int run = 0;
+    for (int f0 = 0; f0 < P * kNW; f0 += 32) {
+      const int f = f0 + lane;
+      const int b = f / kNW, w = f % kNW;
+      const int v = f < P * kNW ? wc[w * P + b] : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (f < P * kNW) {
+        wc[w * P + b] = run + incl - v;
+        if (w == 0) off[b] = run + incl - v;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) off[P] = run;
+  }
+  __syncthreads();
+  // scatter in draw order: a lane's place is its warp's cursor for the window
+  // plus the lanes below it with the same window
+  int32_t* dst = ph.ids + q * (int64_t)a.m;
+  for (int r = s0; r < s1; r += 32) {
+    const int i = r + lane;
+    const int id = i < s1 ? drawn[i] : 0;
+    const int b = i < s1 ? id >> sh : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int base = b >= 0 ? wc[warp * P + b] : 0;
+    __syncwarp();
+    if (b >= 0) {
+      dst[base + __popc(peers & ((1u << lane) - 1u))] = id;
+      if (lane == __ffs(peers) - 1) wc[warp * P + b] = base + __popc(peers);
+    }
+    __syncwarp();
+  }
+  if (tid == 0) ph.info[q] = kk;
+}
+
+// Block (p, q) of a phase-major grid (blockIdx = p nq + q): the sum of the
+// kernel values of query q's draws inside window p.
+template <int G>
+__global__ void __launch_bounds__(kNT, 4) k_gather_phase(SampleArgs a, PhaseArgs ph) {
+  extern __shared__ float4 ys4[];
+  __shared__ float red[kNW];
+  float* ys = reinterpret_cast<float*>(ys4);
+  const int p = (int)(blockIdx.x / (uint64_t)a.nq);
+  const int64_t q = (int64_t)(blockIdx.x % (uint64_t)a.nq);
+  const int tid = threadIdx.x;
+  if (a.active != nullptr && q >= *a.active) return;
+  // the run bounds and the query row are independent loads, issued together
+  // (a failed query's runs are all empty: the finish writes its NaN)
+  const int32_t* off = ph.off + q * (ph.P + 1);
+  const int lo = off[p], hi = off[p + 1];
+  for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
+  __syncthreads();
+  float s = 0.f;
+  if (hi > lo) {
+    float part = gather_sum_k<G, false>(a.X, a.dp, ys, ph.ids + q * (int64_t)a.m + lo, hi - lo,
+                                        a.kern, kernel_inv(a.kern, a.h));
+    part = warp_sum(part);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    for (int w = 0; w < kNW; ++w) s += red[w];
+  }
+  if (tid == 0) ph.part[(int64_t)p * a.nq + q] = s;
+}
+
+// out = (s1 + ((n - k') / m) s2) / n with s2 the window sums added in window
+// order (s1 / n when nothing is sampled, NaN for a failed query).
+__global__ void k_phase_finish(SampleArgs a, PhaseArgs ph) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nq) return;
+  if (a.active != nullptr && q >= *a.active) return;
+  const int kk = ph.info[q];
+  if (kk < 0) {
+    a.out[q] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const double n = (double)a.n;
+  const float s1 = a.s1_in[q];
+  double est;
+  if ((int64_t)kk == a.n) {
+    est = (double)s1 / n;
+  } else {
+    float s2 = 0.f;
+    for (int p = 0; p < ph.P; ++p) s2 += ph.part[(int64_t)p * a.nq + q];
+    est = ((double)s1 + (n - (double)kk) / (double)a.m * (double)s2) / n;
+  }
+  a.out[q] = (float)est;
 }
 
 // Permuted windows shared by many queries (the tiled path): per query, the
@@ -1042,6 +1258,45 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s) {
     case 16: launch_estimate_inst<16>(a, dyn, s); break;
     default: launch_estimate_inst<32>(a, dyn, s); break;
   }
+}
+
+PhasePlan phase_plan(int64_t n, int dp, int m, int64_t nq, int64_t window_bytes) {
+  PhasePlan pl;
+  if (window_bytes <= 0 || n <= 0 || m <= 0 || m > kPhasedMaxM || nq < kPhasedMinQueries)
+    return pl;
+  // W: the largest power of two whose rows fit the window (a shift, not a
+  // division, maps a row id to its window)
+  const int64_t row_bytes = (int64_t)dp * (int64_t)sizeof(float);
+  const int64_t rows = std::max<int64_t>(1, window_bytes / row_bytes);
+  int sh = 0;
+  while (sh < 30 && (int64_t(2) << sh) <= rows) ++sh;
+  const int64_t P = (n + (int64_t(1) << sh) - 1) >> sh;
+  // one window: every draw hits the same one, as in the per-query gathers
+  if (P < 2 || P > kMaxPhases || P * nq > INT32_MAX) return pl;
+  if ((int64_t)m < kMinPhaseRows * P) return pl;
+  pl.P = (int)P;
+  pl.shift = sh;
+  return pl;
+}
+
+template <int G>
+void launch_gather_phase(const SampleArgs& a, const PhaseArgs& ph, cudaStream_t s) {
+  const size_t dyn = sizeof(float) * a.dp;
+  if (dyn > 48 * 1024 - 64) set_dynamic_smem(reinterpret_cast<const void*>(&k_gather_phase<G>), dyn);
+  k_gather_phase<G><<<(unsigned)((int64_t)ph.P * a.nq), kNT, dyn, s>>>(a, ph);
+}
+
+void launch_estimate_phased(const SampleArgs& a, const PhaseArgs& ph, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  const size_t dyn = sizeof(int) * ((size_t)a.m + (size_t)kNW * ph.P);
+  set_dynamic_smem(reinterpret_cast<const void*>(&k_draw_phased), dyn);
+  k_draw_phased<<<(unsigned)a.nq, kNT, dyn, s>>>(a, ph);
+  // the rows come from L2 and the gathers are issue-bound: 8 lanes a row
+  // (four rows a warp instruction) reduce with a fifth of the shuffles and
+  // id loads of 32 lanes a row
+  if (group_lanes(a.dp) == 4) launch_gather_phase<4>(a, ph, s);
+  else launch_gather_phase<8>(a, ph, s);
+  k_phase_finish<<<(unsigned)((a.nq + 255) / 256), 256, 0, s>>>(a, ph);
 }
 
 void launch_window_prep(const SampleArgs& a, int32_t* drops, int dstride, int32_t* dcnt,

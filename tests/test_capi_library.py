@@ -76,6 +76,7 @@ def test_calls_reject_null_index(lib):
     assert lib.kde_exact(None, None, 0, None, None) == 1
     assert lib.kde_set_bandwidth(None, 1.0) == 1
     assert lib.kde_set_scan_tile(None, 1, 64) == 1
+    assert lib.kde_set_phase_window(None, 1 << 20) == 1
     lib.kde_free(None)
 
 
