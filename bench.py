@@ -86,6 +86,9 @@ def parse():
     p.add_argument("--profile-schedule", default="1280,4000,4", metavar="K,M,NPROBE",
                    help="the DEANN schedule --profile-case runs (BF16 scan); the default is "
                         "the one the tuner picks on this workload")
+    p.add_argument("--phase-window", type=int, default=-1, metavar="MIB",
+                   help="--profile-case: the estimator's phase window in MiB (0 = per-query "
+                        "gathers; default: the library's)")
     return p.parse_args()
 
 
@@ -1041,7 +1044,8 @@ def profile_case(args):
     with the split BF16 scan, DEANNP (tiled windows), the tensor-core exact
     KDE and the adjoint on the DEANN query's neighbours; one launch each of
     k_scan_tc<false>, k_scan_tc<true>, k_window_tile, k_exact_tc,
-    k_estimate_grad, two of k_select_neighbors and k_estimate."""
+    k_estimate_grad, two of k_select_neighbors, and two of k_estimate or, for
+    an X of several phase windows, of k_draw_phased and k_gather_phase."""
     import torch
     import paper_2107_02736_gb300 as pkg
     k, m, P = (int(v) for v in args.profile_schedule.split(","))
@@ -1049,6 +1053,8 @@ def profile_case(args):
     n = int(1_000_000 * args.scale)
     X, Y, _ = workloads.mixture_embed(n=n, nq=args.profile_case)
     index = pkg.KDEIndex(torch.from_numpy(X).to(dev), args.kernel, 12.85, nlist=1024, seed=1)
+    if args.phase_window >= 0:
+        index.set_phase_window(args.phase_window << 20)
     index.prepare_permuted()
     Yd = torch.from_numpy(Y).to(dev)
     a, nbr = index.query(Yd, k, m, nprobe=P, seed=1, precision=1, return_neighbors=True)

@@ -179,13 +179,16 @@ kde_status kde_set_scan_tile(kde_index* index, int32_t precision, int32_t tile);
 
 /* kde_set_phase_window -- the bytes of X one phase of kde_query's estimator
  * reads (Algorithm 1's sample sum s2 regrouped by where its rows lie).  When
- * X spans at least two such windows (at most 64), the batch has at least 256
- * queries, m <= 8192 and m >= 64 x the window count, kde_query draws every
+ * X is larger than the window and splits into at most 64 windows of a power
+ * of two of rows each (the most that fit the window), m <= 8192 and
+ * m >= 64 x the window count, kde_query draws every
  * query's sample first, sorts each query's draws stably by window, and then
  * gathers the rows window by window, so that the window being read stays in
  * L2 while all queries' rows in it are summed.  The draws, the rejection of
  * X_1 and the estimate are those of Algorithm 1 as in the per-query gathers;
- * only the order in which s2's terms are added differs (FP32 rounding).
+ * only the order in which s2's terms are added differs (FP32 rounding).  The
+ * choice does not depend on the batch size (for batches below 2^31 / windows
+ * queries), so a query gets the same bits in any batch.
  *   bytes  0 = off (per-query gathers always), else the window size; the
  *          default is 64 MiB (half the GPU's L2).
  * A view starts with its index's window.  Errors: EINVAL. */

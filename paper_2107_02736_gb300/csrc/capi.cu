@@ -253,7 +253,7 @@ struct CallBufs {
   int32_t* ph_ids = nullptr;     // nq x m
   int32_t* ph_off = nullptr;     // nq x (P + 1)
   int32_t* ph_info = nullptr;    // nq
-  float* ph_part = nullptr;      // P x nq
+  float* ph_part = nullptr;      // P x nq x kPhaseWarps
   // bandwidth fitting
   int32_t* fit_zid = nullptr;    // nq training point ids
   int32_t* fit_nbr = nullptr;    // nq x fit_k search neighbours
@@ -313,7 +313,7 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
       cb.ph_ids = b.take<int32_t>((size_t)nq * c.m);
       cb.ph_off = b.take<int32_t>((size_t)nq * (cb.ph.P + 1));
       cb.ph_info = b.take<int32_t>(nq);
-      cb.ph_part = b.take<float>((size_t)nq * cb.ph.P);
+      cb.ph_part = b.take<float>((size_t)nq * cb.ph.P * kPhaseWarps);
     }
   }
   if (c.fit_k >= 0) {
@@ -549,8 +549,8 @@ kde_status finish_call(kde_index* ix, bool host, cudaStream_t st) {
 
 // The estimator of a query call: per-query gathers (k_estimate); the phased
 // order (draws, window-by-window gathers, finish) when X is several L2-sized
-// windows and the batch is large; or, for permuted windows that many queries
-// of the batch share, the tiled window path (prep, tiles, finish).
+// windows; or, for permuted windows that many queries of the batch share, the
+// tiled window path (prep, tiles, finish).
 void run_estimate(kde_index* ix, const CallBufs& cb, const SampleArgs& a, cudaStream_t st) {
   if (a.mode == 0 && a.k > 0 && a.rs == 0 && a.loo == 0 && a.s1_in != nullptr &&
       a.out != nullptr && a.samples == nullptr && a.m > 0 && a.m <= kPhasedMaxM &&

@@ -342,7 +342,7 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s);
 constexpr int kMaxPhases = 64;       // more windows leave too few rows per run
 constexpr int kMinPhaseRows = 64;    // at least this many rows per run on average
 constexpr int kPhasedMaxM = 8192;    // the draws of a query sit in shared memory
-constexpr int64_t kPhasedMinQueries = 256;
+constexpr int kPhaseWarps = 8;        // warps of a gather block: one partial each
 struct PhasePlan {
   int P = 0;                 // windows; 0 = the per-query gathers instead
   int shift = 0;             // rows per window W = 2^shift (the last may be shorter)
@@ -354,7 +354,7 @@ struct PhaseArgs {
   int32_t* ids = nullptr;    // [nq x m] accepted draws, sorted stably by window
   int32_t* off = nullptr;    // [nq x (P + 1)] start of each window's run; off[P] = m
   int32_t* info = nullptr;   // [nq] k' of the query, or -1 when it failed
-  float* part = nullptr;     // [P x nq] per-window sums of kernel values
+  float* part = nullptr;     // [P x nq x kPhaseWarps] per-window, per-warp sums
 };
 // Needs a.mode == 0, a.k > 0, a.s1_in, a.out, no a.samples, not a.rs, and
 // 0 < a.m <= kPhasedMaxM.

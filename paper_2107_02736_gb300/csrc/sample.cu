@@ -724,37 +724,31 @@ __global__ void __launch_bounds__(kNT) k_draw_phased(SampleArgs a, PhaseArgs ph)
   if (tid == 0) ph.info[q] = kk;
 }
 
-// Block (p, q) of a phase-major grid (blockIdx = p nq + q): the sum of the
-// kernel values of query q's draws inside window p.
+// Block (p, q) of a phase-major grid (blockIdx = p nq + q): the sums of the
+// kernel values of query q's draws inside window p, one per warp.  No block
+// barrier: the query row is read straight from global memory (L1 keeps it)
+// and each warp writes its own partial.
+static_assert(kNW == kPhaseWarps, "one partial per warp of the phased gather");
 template <int G>
 __global__ void __launch_bounds__(kNT, 4) k_gather_phase(SampleArgs a, PhaseArgs ph) {
-  extern __shared__ float4 ys4[];
-  __shared__ float red[kNW];
-  float* ys = reinterpret_cast<float*>(ys4);
   const int p = (int)(blockIdx.x / (uint64_t)a.nq);
   const int64_t q = (int64_t)(blockIdx.x % (uint64_t)a.nq);
   const int tid = threadIdx.x;
   if (a.active != nullptr && q >= *a.active) return;
-  // the run bounds and the query row are independent loads, issued together
-  // (a failed query's runs are all empty: the finish writes its NaN)
+  // a failed query's runs are all empty: the finish writes its NaN
   const int32_t* off = ph.off + q * (ph.P + 1);
   const int lo = off[p], hi = off[p + 1];
-  for (int j = tid; j < a.dp; j += kNT) ys[j] = a.Y[q * a.dp + j];
-  __syncthreads();
-  float s = 0.f;
-  if (hi > lo) {
-    float part = gather_sum_k<G, false>(a.X, a.dp, ys, ph.ids + q * (int64_t)a.m + lo, hi - lo,
-                                        a.kern, kernel_inv(a.kern, a.h));
-    part = warp_sum(part);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
-    __syncthreads();
-    for (int w = 0; w < kNW; ++w) s += red[w];
-  }
-  if (tid == 0) ph.part[(int64_t)p * a.nq + q] = s;
+  float part = 0.f;
+  if (hi > lo)
+    part = gather_sum_k<G, false>(a.X, a.dp, a.Y + q * a.dp, ph.ids + q * (int64_t)a.m + lo,
+                                  hi - lo, a.kern, kernel_inv(a.kern, a.h));
+  part = warp_sum(part);
+  if ((tid & 31) == 0) ph.part[((int64_t)p * a.nq + q) * kNW + (tid >> 5)] = part;
 }
 
-// out = (s1 + ((n - k') / m) s2) / n with s2 the window sums added in window
-// order (s1 / n when nothing is sampled, NaN for a failed query).
+// out = (s1 + ((n - k') / m) s2) / n with s2 the warps' window sums added in
+// (window, warp) order (s1 / n when nothing is sampled, NaN for a failed
+// query).
 __global__ void k_phase_finish(SampleArgs a, PhaseArgs ph) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
@@ -771,7 +765,11 @@ __global__ void k_phase_finish(SampleArgs a, PhaseArgs ph) {
     est = (double)s1 / n;
   } else {
     float s2 = 0.f;
-    for (int p = 0; p < ph.P; ++p) s2 += ph.part[(int64_t)p * a.nq + q];
+    for (int p = 0; p < ph.P; ++p) {
+      const float* w = ph.part + ((int64_t)p * a.nq + q) * kNW;
+#pragma unroll
+      for (int i = 0; i < kNW; ++i) s2 += w[i];
+    }
     est = ((double)s1 + (n - (double)kk) / (double)a.m * (double)s2) / n;
   }
   a.out[q] = (float)est;
@@ -1262,11 +1260,13 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s) {
 
 PhasePlan phase_plan(int64_t n, int dp, int m, int64_t nq, int64_t window_bytes) {
   PhasePlan pl;
-  if (window_bytes <= 0 || n <= 0 || m <= 0 || m > kPhasedMaxM || nq < kPhasedMinQueries)
-    return pl;
+  // the plan depends on the index and on m, not on the batch size (short of
+  // the grid limit), so a query gets the same bits in any batch
+  if (window_bytes <= 0 || n <= 0 || m <= 0 || m > kPhasedMaxM) return pl;
   // W: the largest power of two whose rows fit the window (a shift, not a
   // division, maps a row id to its window)
   const int64_t row_bytes = (int64_t)dp * (int64_t)sizeof(float);
+  if (n * row_bytes <= window_bytes) return pl;  // X fits one window
   const int64_t rows = std::max<int64_t>(1, window_bytes / row_bytes);
   int sh = 0;
   while (sh < 30 && (int64_t(2) << sh) <= rows) ++sh;
@@ -1281,9 +1281,7 @@ PhasePlan phase_plan(int64_t n, int dp, int m, int64_t nq, int64_t window_bytes)
 
 template <int G>
 void launch_gather_phase(const SampleArgs& a, const PhaseArgs& ph, cudaStream_t s) {
-  const size_t dyn = sizeof(float) * a.dp;
-  if (dyn > 48 * 1024 - 64) set_dynamic_smem(reinterpret_cast<const void*>(&k_gather_phase<G>), dyn);
-  k_gather_phase<G><<<(unsigned)((int64_t)ph.P * a.nq), kNT, dyn, s>>>(a, ph);
+  k_gather_phase<G><<<(unsigned)((int64_t)ph.P * a.nq), kNT, 0, s>>>(a, ph);
 }
 
 void launch_estimate_phased(const SampleArgs& a, const PhaseArgs& ph, cudaStream_t s) {

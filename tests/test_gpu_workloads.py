@@ -248,23 +248,26 @@ def test_batch_server_tunes_the_scan_tile_before_capture(pkg):
 
 
 def test_graph_replays_with_the_phased_estimator(pkg):
-    """Graphs captured at capacities of 256 rows and more take the phased
-    estimator (forced here by a 4 MiB window on a 36 MB dataset: fifteen
-    windows of 2,048 rows), rows past the batch inactive; each served batch equals the
-    direct call of its size, which takes the same order (batches below 128
-    rows take the per-query gathers both ways)."""
+    """Graphs of every capacity take the phased estimator (forced here by a
+    4 MiB window on a 36 MB dataset: fifteen windows of 2,048 rows), rows
+    past the batch inactive; each served batch equals the direct call of its
+    size, and the whole set in one call (the windows do not depend on the
+    batch size)."""
     X, Y, _ = workloads.unit_powerlaw(n=30_000, nq=1_500, n_centres=100)
     index = pkg.KDEIndex(_dev(X), "exponential", 0.2, nlist=64, seed=5)
     index.set_phase_window(4 << 20)
     server = pkg.BatchServer(index, 100, 1000, nprobe=4, seed=11, precision=1, max_batch=1024)
     Yd = _dev(Y)
-    start = 0
+    start, parts = 0, []
     for b in (300, 17, 700, 260, 90):
         got = server(Yd[start:start + b]).clone()
         want = index.query(Yd[start:start + b], 100, 1000, nprobe=4, seed=11, precision=1,
                            qid_offset=start)
         assert torch.equal(got, want), b
+        parts.append(got)
         start += b
+    whole = index.query(Yd[:start], 100, 1000, nprobe=4, seed=11, precision=1)
+    assert torch.equal(torch.cat(parts), whole)
 
 def _data_small(n=3000, d=8, nq=40, seed=0):
     rng = np.random.default_rng(seed)
