@@ -230,7 +230,10 @@ kde_status kde_search(kde_index* index, const float* Y, int64_t nq, int32_t k, i
  *   nbr    NULL, or nq x k receiving the neighbour ids that were used (the
  *          set X_1, in no particular order; -1 pads).
  * With opts.dev_active_rows only the rows below the device count are served
- * (a CUDA graph captured at a fixed capacity serving a smaller batch). */
+ * (a CUDA graph captured at a fixed capacity serving a smaller batch).
+ * With k > 0 and sample_mode 0 on an X larger than the index's phase window
+ * (kde_set_phase_window) the sample sum runs in the phased order, whose
+ * scratch holds nq x m int32 sorted draws besides the search's. */
 kde_status kde_query(kde_index* index, const float* Y, int64_t nq, int32_t k, int32_t m,
                      int32_t nprobe, uint64_t seed, float* out, int32_t* nbr,
                      const kde_opts* opts);
