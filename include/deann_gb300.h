@@ -187,8 +187,9 @@ kde_status kde_set_scan_tile(kde_index* index, int32_t precision, int32_t tile);
  * L2 while all queries' rows in it are summed.  The draws, the rejection of
  * X_1 and the estimate are those of Algorithm 1 as in the per-query gathers;
  * only the order in which s2's terms are added differs (FP32 rounding).  The
- * choice does not depend on the batch size (for batches below 2^31 / windows
- * queries), so a query gets the same bits in any batch.
+ * choice does not depend on the batch size, so a query gets the same bits in
+ * any batch, up to nq x m = 2^30 draws a call (4 GiB of sorted draws in the
+ * index's scratch); larger batches take the per-query order.
  *   bytes  0 = off (per-query gathers always), else the window size; the
  *          default is 64 MiB (half the GPU's L2).
  * A view starts with its index's window.  Errors: EINVAL. */

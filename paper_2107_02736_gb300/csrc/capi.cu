@@ -307,7 +307,9 @@ void carve_call(Bump& b, const kde_index* ix, const CallShape& c, CallBufs& cb) 
       cb.win_part = b.take<double>((size_t)nq * cb.win.nslices);
     }
   }
-  if (c.search && c.k > 0 && c.m > 0) {
+  // the phased order's sorted draws are capped at kPhasedMaxDraws a call
+  // (larger batches take the per-query order)
+  if (c.search && c.k > 0 && c.m > 0 && (int64_t)c.nq * c.m <= kPhasedMaxDraws) {
     cb.ph = phase_plan(ix->n, ix->dp, c.m, c.nq, ix->phase_bytes);
     if (cb.ph.P > 0) {
       cb.ph_ids = b.take<int32_t>((size_t)nq * c.m);
@@ -1575,9 +1577,11 @@ kde_status kde_reserve(kde_index* ix, int64_t nq, int32_t k, int32_t m, int32_t 
   (void)opts;
   DeviceGuard g(ix->device);
   size_t need = 0;
-  for (int variant = 0; variant < 4; ++variant) {
+  // variant 4: the largest batch whose sample sum still runs in the phased
+  // order, whose sorted draws a smaller capture may need beyond nq's shapes
+  for (int variant = 0; variant < 5; ++variant) {
     CallShape c;
-    c.nq = nq;
+    c.nq = variant == 4 ? std::min<int64_t>(nq, kPhasedMaxDraws / std::max(m, 1)) : nq;
     c.k = k;
     c.m = m;
     c.P = std::max(1, nprobe);

@@ -342,6 +342,7 @@ void launch_estimate(const SampleArgs& a, cudaStream_t s);
 constexpr int kMaxPhases = 64;       // more windows leave too few rows per run
 constexpr int kMinPhaseRows = 64;    // at least this many rows per run on average
 constexpr int kPhasedMaxM = 8192;    // the draws of a query sit in shared memory
+constexpr int64_t kPhasedMaxDraws = int64_t(1) << 30;  // nq x m sorted draws: 4 GiB of scratch
 constexpr int kPhaseWarps = 8;        // warps of a gather block: one partial each
 struct PhasePlan {
   int P = 0;                 // windows; 0 = the per-query gathers instead
